@@ -1,0 +1,266 @@
+"""CPU oracle for local nucleus decomposition -- test infrastructure only.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its Python binding) never imports it, and it never imports them.
+
+The arithmetic lives in ``oracle.c`` (plain single-threaded C, compiled here
+with gcc); this module only marshals numpy arrays through ctypes.  The
+brute-force search of Lemma 1 is written in Python because it only runs on
+graphs with a handful of r-cliques.
+
+Sections cited: Def. 1 (r-/s-cliques, S-degree), Def. 2 (kappa_s), Lemma 1,
+Def. 3 (h-index), Def. 4 (update operator), Alg. 1 (peeling), Alg. 2 (SND),
+Alg. 3 (AND) with the notification of Section 4.3, Def. 5 (degree levels).
+"""
+from __future__ import annotations
+
+import ctypes
+import itertools
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB_PATH = os.path.join(_LIBDIR, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+ERRORS = {0: "ok", -1: "invalid input", -2: "out of memory",
+          -3: "an update raised tau (Thm. 1 violated)", -4: "unsupported (r,s)"}
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into a shared library with gcc (plain -O2)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        i64, i32, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p
+        lib.orc_create.argtypes = [i64, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(vp)]
+        lib.orc_create.restype = ctypes.c_int
+        lib.orc_free.argtypes = [vp]
+        lib.orc_num_r.argtypes = [vp]
+        lib.orc_num_r.restype = i64
+        lib.orc_num_s_incidences.argtypes = [vp]
+        lib.orc_num_s_incidences.restype = i64
+        lib.orc_q.argtypes = [vp]
+        lib.orc_r_tuples.argtypes = [vp, vp]
+        lib.orc_s_degree.argtypes = [vp, vp]
+        lib.orc_hindex.argtypes = [vp, i64]
+        lib.orc_hindex.restype = i32
+        lib.orc_peel.argtypes = [vp, vp]
+        lib.orc_snd.argtypes = [vp, vp, ctypes.c_int, i32, vp, vp, vp]
+        lib.orc_and.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int, i32, vp, vp, vp]
+        lib.orc_degree_levels.argtypes = [vp, vp]
+        lib.orc_degree_levels.restype = i32
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(st: int):
+    if st != 0:
+        raise RuntimeError(f"oracle: {ERRORS.get(st, st)}")
+
+
+def hindex(values) -> int:
+    """H(K), Def. 3: the largest h with at least h members of K that are >= h."""
+    a = np.ascontiguousarray(np.asarray(values, dtype=np.int32).copy())
+    return int(_load().orc_hindex(_ptr(a), a.size))
+
+
+class Graph:
+    """One graph and one (r, s) job, with the oracle's own enumeration.
+
+    ``row_ptr`` / ``col`` must be a simple, symmetric, sorted CSR.  With
+    ``incidence=True`` the oracle also lists, for every r-clique, the other
+    r-cliques of each s-clique that contains it (needed by SND and AND).
+    """
+
+    def __init__(self, row_ptr, col, r: int, s: int, incidence: bool = True):
+        lib = _load()
+        self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        self.col = np.ascontiguousarray(col, dtype=np.int32)
+        self.n = self.row_ptr.size - 1
+        self.r, self.s = r, s
+        h = ctypes.c_void_p()
+        _check(lib.orc_create(self.n, _ptr(self.row_ptr), _ptr(self.col), r, s, int(incidence),
+                              ctypes.byref(h)))
+        self._h = h
+        self._lib = lib
+        self.num_r = int(lib.orc_num_r(h))
+        self.q = int(lib.orc_q(h))
+        self.has_incidence = incidence
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.orc_free(h)
+            self._h = None
+
+    @property
+    def num_incidences(self) -> int:
+        return int(self._lib.orc_num_s_incidences(self._h))
+
+    def r_cliques(self) -> np.ndarray:
+        """Vertex tuples of the r-cliques in canonical (lexicographic) order."""
+        out = np.zeros((self.num_r, self.r), dtype=np.int32)
+        self._lib.orc_r_tuples(self._h, _ptr(out))
+        return out
+
+    def s_degree(self) -> np.ndarray:
+        """d_s(R), Def. 1, counted directly from the adjacency."""
+        out = np.zeros(self.num_r, dtype=np.int32)
+        _check(self._lib.orc_s_degree(self._h, _ptr(out)))
+        return out
+
+    def peel(self) -> np.ndarray:
+        """kappa_s by peeling, Alg. 1 (Batagelj-Zaversnik bins)."""
+        out = np.zeros(self.num_r, dtype=np.int32)
+        _check(self._lib.orc_peel(self._h, _ptr(out)))
+        return out
+
+    def snd(self, tau=None, max_sweeps: int = 1 << 30):
+        """SND, Alg. 2.  Starts from d_s (or from ``tau``) and runs until a pass
+        changes nothing or ``max_sweeps`` passes ran.
+
+        Returns (tau, sweeps, updating_sweeps, evaluations)."""
+        if not self.has_incidence:
+            raise RuntimeError("build the Graph with incidence=True")
+        t = np.zeros(self.num_r, dtype=np.int32) if tau is None else \
+            np.ascontiguousarray(np.asarray(tau, dtype=np.int32).copy())
+        sw, up, ev = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(self._lib.orc_snd(self._h, _ptr(t), int(tau is None), max_sweeps,
+                                 ctypes.byref(sw), ctypes.byref(up), ctypes.byref(ev)))
+        return t, sw.value, up.value, ev.value
+
+    def and_(self, notify: bool = True, order=None, tau=None, max_sweeps: int = 1 << 30):
+        """AND, Alg. 3, processed sequentially in ``order`` (default: id order).
+
+        Returns (tau, sweeps, updating_sweeps, evaluations)."""
+        if not self.has_incidence:
+            raise RuntimeError("build the Graph with incidence=True")
+        t = np.zeros(self.num_r, dtype=np.int32) if tau is None else \
+            np.ascontiguousarray(np.asarray(tau, dtype=np.int32).copy())
+        o = None
+        if order is not None:
+            o = np.ascontiguousarray(np.asarray(order, dtype=np.int64))
+            if sorted(o.tolist()) != list(range(self.num_r)):
+                raise ValueError("order must be a permutation of the r-clique ids")
+        sw, up, ev = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(self._lib.orc_and(self._h, _ptr(t), int(tau is None),
+                                 None if o is None else _ptr(o), int(notify), max_sweeps,
+                                 ctypes.byref(sw), ctypes.byref(up), ctypes.byref(ev)))
+        return t, sw.value, up.value, ev.value
+
+    def degree_levels(self):
+        """Degree levels, Def. 5.  Returns (number of levels, level of each R)."""
+        lv = np.zeros(self.num_r, dtype=np.int32)
+        k = int(self._lib.orc_degree_levels(self._h, _ptr(lv)))
+        if k < 0:
+            _check(k)
+        return k, lv
+
+
+def decompose(row_ptr, col, r: int, s: int) -> np.ndarray:
+    """kappa_s for every r-clique, canonical order (peeling, Alg. 1)."""
+    return Graph(row_ptr, col, r, s, incidence=False).peel()
+
+
+# ---------------------------------------------------------------------------
+# Brute force, Lemma 1: kappa_s(R) is the largest minimum S-degree over the
+# sub-complexes that contain R.  A sub-complex keeps a set X of r-cliques and
+# every s-clique whose r-cliques all lie in X (Def. 5's closure rule).
+# Pure Python; only for graphs with at most ~16 r-cliques.
+# ---------------------------------------------------------------------------
+
+def _adj_sets(row_ptr, col):
+    n = len(row_ptr) - 1
+    return [set(int(x) for x in col[row_ptr[u]:row_ptr[u + 1]]) for u in range(n)]
+
+
+def enumerate_cliques(row_ptr, col, k: int):
+    """All k-cliques as sorted tuples, by brute force over vertex subsets of
+    neighbourhoods (independent of the C enumeration)."""
+    adj = _adj_sets(row_ptr, col)
+    n = len(adj)
+    out = []
+    for combo in itertools.combinations(range(n), k):
+        if all(b in adj[a] for a, b in itertools.combinations(combo, 2)):
+            out.append(combo)
+    return out
+
+
+def brute_force_kappa(row_ptr, col, r: int, s: int, max_r: int = 16):
+    """kappa_s by Lemma 1 over every subset of r-cliques (exponential)."""
+    R = enumerate_cliques(row_ptr, col, r)
+    S = enumerate_cliques(row_ptr, col, s)
+    if len(R) > max_r:
+        raise ValueError("too many r-cliques for brute force")
+    rid = {t: i for i, t in enumerate(R)}
+    members = [[rid[sub] for sub in itertools.combinations(t, r)] for t in S]
+    best = [0] * len(R)
+    for mask in range(1, 1 << len(R)):
+        inside = [(mask >> i) & 1 for i in range(len(R))]
+        deg = [0] * len(R)
+        for mem in members:
+            if all(inside[i] for i in mem):
+                for i in mem:
+                    deg[i] += 1
+        delta = min(deg[i] for i in range(len(R)) if inside[i])
+        for i in range(len(R)):
+            if inside[i] and delta > best[i]:
+                best[i] = delta
+    return R, best
+
+
+def naive_kappa(row_ptr, col, r: int, s: int):
+    """kappa_s by repeated deletion: for each k, delete every r-clique with
+    fewer than k s-cliques left until stable; kappa(R) = largest k at which R
+    survives.  Pure Python, O(k * |R|^2)."""
+    R = enumerate_cliques(row_ptr, col, r)
+    S = enumerate_cliques(row_ptr, col, s)
+    rid = {t: i for i, t in enumerate(R)}
+    members = [[rid[sub] for sub in itertools.combinations(t, r)] for t in S]
+    kappa = [0] * len(R)
+    k = 1
+    while True:
+        alive = [True] * len(R)
+        changed = True
+        while changed:
+            changed = False
+            deg = [0] * len(R)
+            for mem in members:
+                if all(alive[i] for i in mem):
+                    for i in mem:
+                        deg[i] += 1
+            for i in range(len(R)):
+                if alive[i] and deg[i] < k:
+                    alive[i] = False
+                    changed = True
+        if not any(alive):
+            break
+        for i in range(len(R)):
+            if alive[i]:
+                kappa[i] = k
+        k += 1
+    return R, kappa

@@ -1,0 +1,259 @@
+"""Seeded synthetic graph generators and CSR normalisation.
+
+This module holds no part of the decomposition method: it only draws graphs
+and writes them as simple, symmetric, sorted CSR (row_ptr int64[n+1],
+col int32[2m]).  Both the CPU oracle tests and the CUDA path read graphs made
+here, so the two sides always see the same input.
+
+The paper measures on SNAP / Network Repository graphs (Section 5, Table 2).
+Those are replaced by synthetic graphs with the same character: power-law
+social graphs (Chung-Lu), skewed web-like graphs (R-MAT), Erdos-Renyi graphs,
+and planted cliques that create deep (3,4)-nuclei.
+
+Generator readings (the workloads leave these open):
+* Chung-Lu: weight w_i = (i + 1) ** (-1 / (gamma - 1)), scaled so that
+  sum(w) = n * mean_degree, each weight capped at sqrt(sum(w)); n*d/2
+  endpoint pairs are drawn independently with probability proportional to w;
+  self-loops and duplicates are dropped; vertex labels are then randomly
+  permuted so that ids carry no degree information.
+* R-MAT: the Graph500 recursive quadrant choice with (a, b, c, d) and no
+  noise; EF * 2**scale directed samples; symmetrised, deduplicated, loops
+  dropped, labels randomly permuted.
+* Erdos-Renyi: G(n, p) drawn exactly by sampling Binomial(n(n-1)/2, p)
+  distinct pairs.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "to_csr", "chung_lu", "rmat", "erdos_renyi", "plant_cliques",
+    "graph_from_edges", "toy_core_graph", "complete_graph", "cycle_graph",
+    "star_graph", "disjoint_union", "workload",
+]
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def to_csr(n: int, src, dst):
+    """Simple undirected CSR from an arbitrary directed pair list.
+
+    Drops self-loops, symmetrises, removes duplicates and sorts each row.
+    Returns (row_ptr int64[n+1], col int32[nnz]).
+    """
+    src = np.asarray(src, dtype=np.int64).ravel()
+    dst = np.asarray(dst, dtype=np.int64).ravel()
+    if src.size:
+        if src.min() < 0 or dst.min() < 0 or src.max() >= n or dst.max() >= n:
+            raise ValueError("vertex id out of range")
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
+    lo = np.minimum(src, dst)
+    hi = np.maximum(src, dst)
+    up = _sorted_unique(lo * np.int64(n) + hi)      # (lo, hi) pairs, sorted by lo then hi
+    dn = np.sort((up % n) * np.int64(n) + up // n)  # (hi, lo) pairs, sorted by hi then lo
+    up_u, up_v = up // n, up % n
+    dn_u, dn_v = dn // n, dn % n
+    cnt_up = np.bincount(up_u, minlength=n).astype(np.int64)
+    cnt_dn = np.bincount(dn_u, minlength=n).astype(np.int64)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(cnt_up + cnt_dn)
+    # a row is its smaller neighbours (all < u) followed by its larger ones (all > u)
+    start_up = np.zeros(n, np.int64)
+    start_up[1:] = np.cumsum(cnt_up)[:-1]
+    start_dn = np.zeros(n, np.int64)
+    start_dn[1:] = np.cumsum(cnt_dn)[:-1]
+    col = np.empty(int(row_ptr[-1]), dtype=np.int32)
+    i_dn = np.arange(dn.size, dtype=np.int64)
+    col[row_ptr[dn_u] + (i_dn - start_dn[dn_u])] = dn_v
+    i_up = np.arange(up.size, dtype=np.int64)
+    col[row_ptr[up_u] + cnt_dn[up_u] + (i_up - start_up[up_u])] = up_v
+    return row_ptr, col
+
+
+def _sorted_unique(a):
+    a = np.sort(a)
+    if a.size == 0:
+        return a
+    keep = np.empty(a.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(a[1:], a[:-1], out=keep[1:])
+    return a[keep]
+
+
+def _relabel(n: int, rng: np.random.Generator, src, dst):
+    perm = rng.permutation(n).astype(np.int64)
+    return perm[src], perm[dst]
+
+
+def chung_lu(n: int, gamma: float, mean_degree: float, seed: int):
+    """Chung-Lu power-law graph (expected degrees follow exponent gamma)."""
+    rng = _rng(seed)
+    w = (np.arange(n, dtype=np.float64) + 1.0) ** (-1.0 / (gamma - 1.0))
+    w *= n * mean_degree / w.sum()
+    cap = np.sqrt(w.sum())
+    w = np.minimum(w, cap)
+    p = w / w.sum()
+    m = int(round(n * mean_degree / 2.0))
+    cdf = np.cumsum(p)
+    cdf[-1] = 1.0
+    src = np.searchsorted(cdf, rng.random(m), side="right")
+    dst = np.searchsorted(cdf, rng.random(m), side="right")
+    src = np.minimum(src, n - 1)
+    dst = np.minimum(dst, n - 1)
+    src, dst = _relabel(n, rng, src, dst)
+    return src, dst
+
+
+def rmat(scale: int, edge_factor: int, abcd=(0.57, 0.19, 0.19, 0.05), seed: int = 0,
+         n_limit: int | None = None):
+    """R-MAT directed samples (Graph500 quadrant recursion, no noise).
+
+    Returns (n, src, dst).  With ``n_limit`` the vertex set is cut to the
+    first n_limit ids before relabelling and samples touching larger ids are
+    rejected (used for graph sizes that are not a power of two).
+    """
+    a, b, c, d = abcd
+    if abs(a + b + c + d - 1.0) > 1e-9:
+        raise ValueError("R-MAT probabilities must sum to 1")
+    rng = _rng(seed)
+    ne = edge_factor * (1 << scale)
+    src = np.zeros(ne, dtype=np.int64)
+    dst = np.zeros(ne, dtype=np.int64)
+    ab = a + b
+    abc = a + b + c
+    chunk = 1 << 22
+    for lo in range(0, ne, chunk):
+        hi = min(ne, lo + chunk)
+        s = np.zeros(hi - lo, dtype=np.int64)
+        t = np.zeros(hi - lo, dtype=np.int64)
+        for level in range(scale):
+            r = rng.random(hi - lo)
+            sbit = r >= ab
+            tbit = ((r >= a) & (r < ab)) | (r >= abc)
+            s |= sbit.astype(np.int64) << level
+            t |= tbit.astype(np.int64) << level
+        src[lo:hi] = s
+        dst[lo:hi] = t
+    n = 1 << scale
+    if n_limit is not None and n_limit < n:
+        keep = (src < n_limit) & (dst < n_limit)
+        src, dst = src[keep], dst[keep]
+        n = n_limit
+    src, dst = _relabel(n, rng, src, dst)
+    return n, src, dst
+
+
+def erdos_renyi(n: int, p: float, seed: int):
+    """G(n, p): each of the n(n-1)/2 pairs present independently with p."""
+    rng = _rng(seed)
+    total = n * (n - 1) // 2
+    m = int(rng.binomial(total, p)) if total else 0
+    picked = _sorted_unique(rng.integers(0, total, size=int(m * 1.1) + 16, dtype=np.int64))
+    while picked.size < m:
+        more = rng.integers(0, total, size=m - picked.size + 16, dtype=np.int64)
+        picked = _sorted_unique(np.concatenate([picked, more]))
+    picked = rng.permutation(picked)[:m]
+    # unrank pair index k -> (i, j), i < j, rows of length n-1-i
+    k = picked.astype(np.float64)
+    i = np.floor((2 * n - 1 - np.sqrt((2 * n - 1) ** 2 - 8 * k)) / 2).astype(np.int64)
+    row_start = i * (2 * n - i - 1) // 2
+    over = picked < row_start
+    i[over] -= 1
+    row_start = i * (2 * n - i - 1) // 2
+    under = picked >= row_start + (n - 1 - i)
+    i[under] += 1
+    row_start = i * (2 * n - i - 1) // 2
+    j = picked - row_start + i + 1
+    return i, j
+
+
+def plant_cliques(n: int, count: int, size_lo: int, size_hi: int, seed: int):
+    """Edges of `count` cliques, sizes uniform in [size_lo, size_hi], each on
+    a uniformly random vertex set."""
+    rng = _rng(seed)
+    src, dst = [], []
+    for _ in range(count):
+        k = int(rng.integers(size_lo, size_hi + 1))
+        vs = rng.choice(n, size=k, replace=False).astype(np.int64)
+        a, b = np.triu_indices(k, 1)
+        src.append(vs[a])
+        dst.append(vs[b])
+    if not src:
+        return np.zeros(0, np.int64), np.zeros(0, np.int64)
+    return np.concatenate(src), np.concatenate(dst)
+
+
+def graph_from_edges(n: int, edges):
+    e = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+    return to_csr(n, e[:, 0], e[:, 1])
+
+
+def toy_core_graph():
+    """The six-vertex k-core example traced in Section 4 (Figures 5 and 6).
+
+    Vertices a..f are 0..5; edges a-b, a-e, b-c, b-d, c-d, e-f.  The edge set
+    follows from the traces: b's neighbours are a, c, d; a's are e and b;
+    e notifies a and f.
+    """
+    a, b, c, d, e, f = range(6)
+    return graph_from_edges(6, [(a, b), (a, e), (b, c), (b, d), (c, d), (e, f)])
+
+
+def complete_graph(k: int):
+    a, b = np.triu_indices(k, 1)
+    return to_csr(k, a, b)
+
+
+def cycle_graph(k: int):
+    a = np.arange(k)
+    return to_csr(k, a, (a + 1) % k)
+
+
+def star_graph(leaves: int):
+    return to_csr(leaves + 1, np.zeros(leaves, np.int64), np.arange(1, leaves + 1))
+
+
+def disjoint_union(*graphs):
+    rps, cols, off = [np.zeros(1, np.int64)], [], 0
+    base = 0
+    for rp, col in graphs:
+        rps.append(rp[1:] + base)
+        cols.append(col.astype(np.int64) + off)
+        base += int(rp[-1])
+        off += rp.size - 1
+    return np.concatenate(rps).astype(np.int64), np.concatenate(cols).astype(np.int32)
+
+
+def workload(name: str):
+    """Named synthetic workloads, each with its (r, s) job.
+
+    Returns dict(name, r, s, row_ptr, col, recipe).
+    """
+    if name == "chunglu_n2000_g2.5_d10":
+        src, dst = chung_lu(2000, 2.5, 10.0, seed=1)
+        rp, col = to_csr(2000, src, dst)
+        return dict(name=name, r=1, s=2, row_ptr=rp, col=col,
+                    recipe="Chung-Lu n=2000 gamma=2.5 mean degree 10 seed 1; k-core (1,2)")
+    if name.startswith("rmat_s") and "_ef" in name:
+        # rmat_s{scale}_ef{ef}, e.g. rmat_s20_ef16
+        scale = int(name.split("_s")[1].split("_")[0])
+        ef = int(name.split("_ef")[1].split("_")[0])
+        n, src, dst = rmat(scale, ef, seed=2)
+        rp, col = to_csr(n, src, dst)
+        return dict(name=name, r=2, s=3, row_ptr=rp, col=col,
+                    recipe=f"R-MAT scale {scale} edge factor {ef} (0.57,0.19,0.19,0.05) seed 2, "
+                           "symmetrised, deduplicated, no loops; k-truss (2,3)")
+    if name.startswith("chunglu_n") and "_planted" in name:
+        # chunglu_n{n}_g2.1_d20_planted{count}
+        n = int(name.split("_n")[1].split("_")[0])
+        count = int(name.split("_planted")[1])
+        s1, d1 = chung_lu(n, 2.1, 20.0, seed=3)
+        s2, d2 = plant_cliques(n, count, 20, 60, seed=3 + 1000)
+        rp, col = to_csr(n, np.concatenate([s1, s2]), np.concatenate([d1, d2]))
+        return dict(name=name, r=3, s=4, row_ptr=rp, col=col,
+                    recipe=f"Chung-Lu n={n} gamma=2.1 mean degree 20 seed 3 plus {count} planted "
+                           "cliques of size U[20,60] on random vertex sets; (3,4)-nucleus")
+    raise KeyError(name)

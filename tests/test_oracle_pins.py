@@ -1,0 +1,335 @@
+"""Pins for the CPU oracle: each check ties it to something other than itself.
+
+* values the paper prints (worked examples in tests/golden/),
+* closed forms (cliques, cycles, stars, unions),
+* brute force on tiny graphs (Lemma 1 over all subsets; repeated deletion),
+* theorems (Thm. 1 monotonicity and lower bound, Thm. 3 level-by-level
+  convergence, AND never slower than SND),
+* a library routine (networkx core numbers) where it is installed.
+
+A plausible slip in the oracle -- a dropped s-clique, max instead of min in
+rho, an off-by-one in H, a wrong r-clique id -- fails at least one of these.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1704_00386_gb300 import graphs as G
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+RS = [(1, 2), (2, 3), (3, 4)]
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+def _random_graph(rng, n_lo, n_hi, m_hi):
+    n = int(rng.integers(n_lo, n_hi + 1))
+    e = rng.integers(0, n, size=(int(rng.integers(0, m_hi + 1)), 2))
+    return G.to_csr(n, e[:, 0], e[:, 1])
+
+
+# ---------------------------------------------------------------- h-index
+
+def test_hindex_paper_values():
+    for case in _gold("hindex_paper.json")["cases"]:
+        assert oracle.hindex(case["K"]) == case["H"], case["where"]
+
+
+def test_hindex_special_cases():
+    assert oracle.hindex([]) == 0                 # empty multiset
+    assert oracle.hindex([0, 0, 0]) == 0
+    assert oracle.hindex([5]) == 1
+    assert oracle.hindex([1, 1, 1, 1]) == 1       # duplicates count
+    assert oracle.hindex([4, 4, 4, 4]) == 4
+    assert oracle.hindex([100] * 7) == 7          # bounded by the size
+    assert oracle.hindex(list(range(1, 11))) == 5
+
+
+def test_hindex_brute_force_random():
+    rng = np.random.default_rng(7)
+    for _ in range(300):
+        k = list(rng.integers(0, 12, size=int(rng.integers(0, 12))))
+        # h qualifies iff at least h values are >= h; take the largest
+        best = max(h for h in range(len(k) + 1) if sum(v >= h for v in k) >= h)
+        assert oracle.hindex(k) == best
+
+
+# ---------------------------------------------------------- worked example
+
+def _toy():
+    return oracle.Graph(*G.toy_core_graph(), 1, 2)
+
+
+def test_toy_core_numbers_and_degrees():
+    gold = _gold("toy_core_fig5_fig6.json")
+    g = _toy()
+    assert list(g.s_degree()) == gold["degree"]
+    assert list(g.peel()) == gold["core_number"]
+
+
+def test_toy_snd_trace():
+    gold = _gold("toy_core_fig5_fig6.json")
+    g = _toy()
+    assert list(g.snd(max_sweeps=1)[0]) == gold["snd_tau1"]
+    assert list(g.snd(max_sweeps=2)[0]) == gold["snd_tau2"]
+    tau, sweeps, updating, evals = g.snd()
+    assert list(tau) == gold["core_number"]
+    assert updating == gold["snd_updating_iterations"]
+    assert sweeps == updating + 1            # tau_3 is computed and unchanged
+
+
+def test_toy_and_orders():
+    gold = _gold("toy_core_fig5_fig6.json")
+    names = gold["vertices"]
+    g = _toy()
+    order = [names.index(v) for v in gold["and_level_order"]]
+    tau, _, updating, _ = g.and_(notify=False, order=order)
+    assert list(tau) == gold["core_number"]
+    assert updating == gold["and_level_order_updating_iterations"]
+    tau, _, updating, _ = g.and_(notify=False)
+    assert updating == gold["and_abc_order_updating_iterations"]
+
+
+def test_toy_notification_counts():
+    gold = _gold("toy_core_fig5_fig6.json")
+    g = _toy()
+    tau, sweeps, updating, evals = g.and_(notify=True)
+    assert list(tau) == gold["core_number"]
+    assert evals == gold["and_notify_computations"]
+    assert sweeps == gold["and_notify_iterations"]
+    # without notification: the paper's 24 computations in 4 iterations count
+    # the initialisation tau_0 = d_s as one pass of 6 computations
+    tau, sweeps, updating, evals = g.and_(notify=False)
+    n = len(gold["vertices"])
+    assert evals + n == gold["and_no_notify_computations_incl_init"]
+    assert sweeps + 1 == gold["and_no_notify_iterations_incl_init"]
+
+
+def test_toy_degree_levels():
+    gold = _gold("toy_core_fig5_fig6.json")
+    g = _toy()
+    k, lv = g.degree_levels()
+    assert k == 4
+    assert {v: int(lv[i]) for i, v in enumerate(gold["vertices"])} == gold["degree_levels"]
+
+
+# ------------------------------------------------------------ closed forms
+
+@pytest.mark.parametrize("k", [3, 4, 5, 6, 7, 9])
+def test_complete_graph(k):
+    rp, col = G.complete_graph(k)
+    for (r, s) in RS:
+        if k < s:
+            continue
+        g = oracle.Graph(rp, col, r, s)
+        want = k - r            # each r-clique lies in C(k-r, s-r) = k-r s-cliques
+        assert (g.peel() == want).all()
+        assert (g.snd()[0] == want).all()
+        assert g.snd()[2] == 0  # already converged at tau_0 = d_s
+        assert g.num_r == len(list(itertools.combinations(range(k), r)))
+
+
+@pytest.mark.parametrize("k", [4, 5, 8, 13])
+def test_cycle(k):
+    rp, col = G.cycle_graph(k)
+    assert (oracle.Graph(rp, col, 1, 2).peel() == 2).all()
+    assert (oracle.Graph(rp, col, 2, 3).peel() == 0).all()
+    assert oracle.Graph(rp, col, 3, 4).num_r == 0
+
+
+@pytest.mark.parametrize("leaves", [1, 2, 7])
+def test_star(leaves):
+    rp, col = G.star_graph(leaves)
+    assert (oracle.Graph(rp, col, 1, 2).peel() == 1).all()
+    assert (oracle.Graph(rp, col, 2, 3).peel() == 0).all()
+
+
+def test_isolated_vertices_and_empty():
+    rp = np.zeros(6, np.int64)
+    col = np.zeros(0, np.int32)
+    g = oracle.Graph(rp, col, 1, 2)
+    assert (g.peel() == 0).all() and (g.snd()[0] == 0).all()
+    assert oracle.Graph(rp, col, 2, 3).num_r == 0
+    g0 = oracle.Graph(np.zeros(1, np.int64), col, 1, 2)
+    assert g0.num_r == 0 and g0.peel().size == 0
+
+
+def test_disjoint_union_decomposes_independently():
+    rng = np.random.default_rng(11)
+    parts = [_random_graph(rng, 5, 12, 30) for _ in range(3)]
+    rp, col = G.disjoint_union(*parts)
+    for (r, s) in RS:
+        whole = oracle.Graph(rp, col, r, s)
+        kw = whole.peel()
+        tw = [tuple(t) for t in whole.r_cliques()]
+        got = dict(zip(tw, kw.tolist()))
+        off = 0
+        for prp, pcol in parts:
+            g = oracle.Graph(prp, pcol, r, s)
+            for t, k in zip(g.r_cliques(), g.peel()):
+                assert got[tuple(int(x) + off for x in t)] == k
+            off += prp.size - 1
+
+
+def test_planted_clique_bounds():
+    k = 12
+    s1, d1 = G.erdos_renyi(120, 3 / 119, seed=21)
+    rng = np.random.default_rng(5)
+    vs = rng.choice(120, size=k, replace=False)
+    a, b = np.triu_indices(k, 1)
+    rp, col = G.to_csr(120, np.concatenate([s1, vs[a]]), np.concatenate([d1, vs[b]]))
+    inside = set(int(v) for v in vs)
+    for (r, s) in RS:
+        g = oracle.Graph(rp, col, r, s)
+        kap = g.peel()
+        for t, kk in zip(g.r_cliques(), kap):
+            if set(int(x) for x in t) <= inside:
+                assert kk >= k - r
+
+
+# ------------------------------------------------------------ brute force
+
+def test_brute_force_lemma1_all_rs():
+    rng = np.random.default_rng(3)
+    checked = {rs: 0 for rs in RS}
+    for rs in RS:
+        tries = 0
+        while checked[rs] < 25 and tries < 400:
+            tries += 1
+            rp, col = _random_graph(rng, 3, 8, 20)
+            g = oracle.Graph(rp, col, *rs)
+            if g.num_r > 13 or (rs != (1, 2) and g.num_r == 0):
+                continue
+            R, bf = oracle.brute_force_kappa(rp, col, *rs)
+            assert [tuple(int(x) for x in t) for t in g.r_cliques()] == R
+            assert list(g.peel()) == bf
+            assert list(g.snd()[0]) == bf
+            assert list(g.and_(notify=True)[0]) == bf
+            assert list(g.and_(notify=False)[0]) == bf
+            checked[rs] += 1
+    assert all(v >= 10 for v in checked.values()), checked
+
+
+def test_naive_deletion_matches_peeling():
+    rng = np.random.default_rng(4)
+    for rs in RS:
+        for _ in range(8):
+            rp, col = _random_graph(rng, 6, 16, 60)
+            g = oracle.Graph(rp, col, *rs)
+            R, kap = oracle.naive_kappa(rp, col, *rs)
+            assert [tuple(int(x) for x in t) for t in g.r_cliques()] == R
+            assert list(g.peel()) == kap
+
+
+def test_s_degree_matches_enumeration():
+    rng = np.random.default_rng(5)
+    for rs in RS:
+        for _ in range(6):
+            rp, col = _random_graph(rng, 5, 14, 50)
+            g = oracle.Graph(rp, col, *rs)
+            R = oracle.enumerate_cliques(rp, col, rs[0])
+            S = oracle.enumerate_cliques(rp, col, rs[1])
+            want = [sum(set(t) <= set(sc) for sc in S) for t in R]
+            assert list(g.s_degree()) == want
+            assert g.num_incidences == sum(want)
+
+
+# ---------------------------------------------------------------- theorems
+
+def _medium_graphs():
+    out = []
+    src, dst = G.chung_lu(400, 2.3, 8.0, seed=31)
+    out.append(G.to_csr(400, src, dst))
+    i, j = G.erdos_renyi(300, 10 / 299, seed=32)
+    out.append(G.to_csr(300, i, j))
+    n, s2, d2 = G.rmat(9, 8, seed=33)
+    out.append(G.to_csr(n, s2, d2))
+    return out
+
+
+@pytest.mark.parametrize("rs", RS)
+def test_theorems_on_medium_graphs(rs):
+    rng = np.random.default_rng(9)
+    for rp, col in _medium_graphs():
+        g = oracle.Graph(rp, col, *rs)
+        kap = g.peel()
+        ds = g.s_degree()
+        tau, sweeps, updating, _ = g.snd()
+        assert (tau == kap).all()
+        levels, lv = g.degree_levels()
+        # Thm. 3 / Lemma 2: level L_i has converged after i sweeps
+        assert updating <= max(levels - 1, 0)
+        prev = ds
+        for t in range(1, updating + 1):
+            cur = g.snd(max_sweeps=t)[0]
+            assert (cur <= prev).all()                 # Thm. 1, monotone
+            assert (cur >= kap).all()                  # Thm. 1, lower bound
+            assert (cur[lv <= t] == kap[lv <= t]).all()  # Thm. 3
+            prev = cur
+        # AND reaches the same fixed point, in no more updating sweeps
+        for notify in (False, True):
+            ta, _, up_a, _ = g.and_(notify=notify)
+            assert (ta == kap).all()
+            assert up_a <= updating
+        order = rng.permutation(g.num_r)
+        assert (g.and_(notify=True, order=order)[0] == kap).all()
+        # early-stopped AND is sandwiched: kappa <= tau_AND_k <= tau_SND_k
+        for k in (1, 2, 3):
+            ta = g.and_(notify=False, max_sweeps=k)[0]
+            ts = g.snd(max_sweeps=k)[0]
+            assert (kap <= ta).all() and (ta <= ts).all()
+
+
+def test_resume_from_intermediate_tau():
+    rp, col = _medium_graphs()[0]
+    g = oracle.Graph(rp, col, 2, 3)
+    full = g.snd()[0]
+    mid = g.snd(max_sweeps=2)[0]
+    assert (g.snd(tau=mid)[0] == full).all()
+    assert (g.and_(tau=mid)[0] == full).all()
+
+
+def test_cross_decomposition_bounds():
+    for rp, col in _medium_graphs():
+        g1, g2, g3 = (oracle.Graph(rp, col, r, s, incidence=False) for r, s in RS)
+        k1, k2, k3 = g1.peel(), g2.peel(), g3.peel()
+        e = g2.r_cliques()
+        # an edge in a k-truss (k triangles each) sits in a (k+1)-core
+        assert (k2 + 1 <= np.minimum(k1[e[:, 0]], k1[e[:, 1]])).all()
+        t = g3.r_cliques()
+        eid = {tuple(x): i for i, x in enumerate(e.tolist())}
+        for tri, kk in zip(t.tolist(), k3):
+            a, b, c = tri
+            m = min(k2[eid[(a, b)]], k2[eid[(a, c)]], k2[eid[(b, c)]])
+            assert kk + 1 <= m
+
+
+def test_networkx_core_number():
+    nx = pytest.importorskip("networkx")
+    for rp, col in _medium_graphs():
+        n = rp.size - 1
+        gx = nx.Graph()
+        gx.add_nodes_from(range(n))
+        for u in range(n):
+            for v in col[rp[u]:rp[u + 1]]:
+                gx.add_edge(u, int(v))
+        want = nx.core_number(gx)
+        got = oracle.Graph(rp, col, 1, 2, incidence=False).peel()
+        assert [want[u] for u in range(n)] == got.tolist()
+
+
+def test_rejects_invalid_csr():
+    rp = np.array([0, 1, 1], np.int64)
+    col = np.array([1], np.int32)           # not symmetric
+    with pytest.raises(RuntimeError):
+        oracle.Graph(rp, col, 1, 2)
+    rp2, col2 = G.toy_core_graph()
+    with pytest.raises(RuntimeError):
+        oracle.Graph(rp2, col2, 1, 3)        # unsupported (r, s)
