@@ -1,0 +1,157 @@
+/*
+ * nd.h -- C ABI of the GB300 local nucleus decomposition library (libnd).
+ *
+ * The library computes, for every r-clique R of a simple undirected graph,
+ * its kappa_s index (core number for (r,s) = (1,2), truss number for (2,3),
+ * (3,4)-nucleus number for (3,4)) by the iterated h-index update of
+ * Sariyuce, Seshadhri and Pinar, "Local Algorithms for Hierarchical Dense
+ * Subgraph Discovery" (PVLDB 12(1), 2019):
+ *   - the problem statement is the input/output of Alg. 1, Alg. 2, Alg. 3
+ *     (Input: graph G, integers r < s; Output: kappa_s of every r-clique);
+ *   - r-cliques, s-cliques and the S-degree d_s are Def. 1; kappa_s is Def. 2;
+ *   - the update operator U (rho(S,R) = min over the other r-cliques of S,
+ *     then the h-index H of Def. 3) is Def. 4;
+ *   - SND (synchronous, Jacobi-like) is Alg. 2, Section 4.1;
+ *   - AND (asynchronous, in place, Gauss-Seidel-like) is Alg. 3, Section 4.2,
+ *     and its notification mechanism is Section 4.3.
+ *
+ * Conventions shared by every call:
+ *   - Status codes are returned, never thrown; no call aborts the process.
+ *     nd_last_error() gives a message for the calling thread's last failure.
+ *   - Integers: vertex ids int32; r-clique ids fit uint32; offsets int64;
+ *     tau / kappa int32.  The arithmetic is exact integer throughout.
+ *   - Pointers flagged "host or device" are host memory when the call's
+ *     on_device argument is 0 and device memory (this GPU) when it is 1.
+ *     The caller owns every buffer it passes; the library owns the
+ *     nd_incidence handle and everything inside it until nd_free().
+ *   - Calls are stream-ordered on the given cudaStream_t (passed as void*;
+ *     NULL = the legacy default stream).  A call that returns results into
+ *     host memory synchronises that stream before returning; a call that
+ *     writes device memory returns once the work is enqueued, except where
+ *     it must read a count back (each such call says so).
+ *   - Canonical r-clique order: lexicographic order of the sorted vertex
+ *     tuple.  Vertex v for r = 1; edge (u,v), u < v, for r = 2; triangle
+ *     (u,v,w), u < v < w, for r = 3.  tau arrays are indexed in this order.
+ *   - Truss numbers follow the paper's convention (Section 2.1): an edge in
+ *     a k-truss lies in at least k triangles; the classic k-truss of Cohen
+ *     is kappa_3 + 2 (see nd_truss_classic).
+ */
+#ifndef ND_H
+#define ND_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ND_OK = 0,
+    ND_E_INVAL = 1,           /* bad argument or malformed graph (not simple, sorted, symmetric) */
+    ND_E_UNSUPPORTED_RS = 2,  /* (r,s) not one of (1,2), (2,3), (3,4) */
+    ND_E_NOMEM = 3,           /* a device or host allocation failed */
+    ND_E_CUDA = 4,            /* a CUDA runtime call failed (message in nd_last_error) */
+    ND_E_NOT_CONVERGED = 5,   /* the iteration cap was reached; tau is still a valid upper bound */
+    ND_E_TIMEOUT = 6,         /* a host-side wait exceeded its limit */
+    ND_E_TOO_LARGE = 7        /* more r-cliques than the 32-bit id space, or a size limit */
+} nd_status;
+
+typedef enum { ND_SND = 0, ND_AND = 1, ND_AND_NN = 2 } nd_mode;
+
+/* Simple undirected graph in CSR form: row_ptr[n+1] (int64), col[nnz]
+ * (int32), every row strictly increasing, no self-loops, symmetric
+ * (v in row u iff u in row v), so nnz = 2|E|.  Host or device per on_device. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    int on_device;
+} nd_csr;
+
+typedef struct nd_incidence nd_incidence; /* opaque; owned by the library */
+
+/* Build the r-clique -> s-clique incidence of g (Def. 1) on this GPU:
+ * degree split and canonical edge ids, then triangle enumeration for r = 2
+ * and r = 3 and 4-clique enumeration for r = 3, by sorted-list intersection
+ * (the paper finds s-cliques through vertex neighbourhoods, Section 4.1,
+ * "Time complexity"; here they are materialised once as CSR).
+ * For each r-clique R the incidence lists, per s-clique S containing R, the
+ * q = C(s,r) - 1 ids of the other r-cliques of S; row lengths are d_s(R).
+ * The graph is validated first; a malformed graph returns ND_E_INVAL and
+ * builds nothing.  Synchronises `stream` (sizes are read back to allocate).
+ * On success *out owns device memory until nd_free(*out). */
+nd_status nd_build_incidence(const nd_csr* g, int r, int s, void* stream, nd_incidence** out);
+
+/* Sizes of a built incidence: number of r-clique (N_R), number of
+ * (R, S) incidences (M = sum of d_s), and q.  Any output may be NULL. */
+nd_status nd_incidence_info(const nd_incidence* inc, int64_t* num_r, int64_t* num_incidences,
+                            int* q);
+
+/* Vertex tuples of the r-cliques in canonical order: num_r * r int32,
+ * host or device per on_device. */
+nd_status nd_r_cliques(const nd_incidence* inc, int32_t* verts_out, int on_device, void* stream);
+
+/* d_s(R) for every r-clique (tau_0 of Alg. 2 and Alg. 3): num_r int32. */
+nd_status nd_s_degree(const nd_incidence* inc, int32_t* ds_out, int on_device, void* stream);
+
+/* SND, Alg. 2: tau_0 = d_s, tau_{t+1} = U tau_t, until a pass changes no
+ * tau or max_iters passes ran.  tau_out: num_r int32 (host or device).
+ * *iters_out (may be NULL) = number of passes that changed at least one
+ * tau (the pass that detects convergence is not counted).  Synchronises
+ * `stream`.  Returns ND_E_NOT_CONVERGED if the cap was reached first. */
+nd_status nd_snd(nd_incidence* inc, int32_t* tau_out, int on_device, int32_t max_iters,
+                 int32_t* iters_out, void* stream);
+
+/* AND, Alg. 3: tau updated in place from the latest values.  notify = 1
+ * enables the notification mechanism of Section 4.3 (only r-cliques whose
+ * neighbours changed are recomputed); notify = 0 is "AND-nn".  Processing
+ * order inside a pass is not fixed (any order reaches the same kappa_s).
+ * *iters_out = passes that changed a tau; *evals_out = h-index evaluations
+ * performed over all passes (either may be NULL).  Synchronises `stream`. */
+nd_status nd_and(nd_incidence* inc, int32_t* tau_out, int on_device, int notify,
+                 int32_t max_iters, int32_t* iters_out, int64_t* evals_out, void* stream);
+
+/* Early-stopped iteration (Section 5.2.3's runtime/accuracy trade-off):
+ * run at most k passes of `mode` starting from tau_inout (tau_init_given = 1;
+ * any tau with kappa_s <= tau <= d_s is a valid start, Lemma 2) or from d_s
+ * (tau_init_given = 0), and write the result back into tau_inout.  Stops
+ * early if a pass changes nothing.  *updating_out = passes that changed a
+ * tau.  SND results are deterministic; AND results depend on the schedule
+ * but always satisfy kappa_s <= tau_AND_k <= tau_SND_k.  Synchronises. */
+nd_status nd_iterate_k(nd_incidence* inc, int mode, int32_t k, int32_t* tau_inout,
+                       int tau_init_given, int on_device, int32_t* updating_out, void* stream);
+
+/* Classic truss numbers (Cohen's k-2 convention) from kappa_3: out = in + 2
+ * for every edge.  Host or device per on_device. */
+nd_status nd_truss_classic(const int32_t* kappa3, int64_t num_edges, int32_t* out, int on_device,
+                           void* stream);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream.
+ * nd_prof_enable(1) starts recording (and clears the totals); with 0 it
+ * stops.  nd_prof_read synchronises and returns, for kernel index i, its
+ * name, launch count and total milliseconds; it returns ND_E_INVAL past the
+ * last kernel.  Profiling is off by default. */
+nd_status nd_prof_enable(int on);
+nd_status nd_prof_read(int i, const char** name, int64_t* launches, double* total_ms);
+
+/* Counters of the last nd_snd / nd_and / nd_iterate_k call on this handle,
+ * pass by pass: changed[i] = r-cliques whose tau changed in pass i,
+ * evaluated[i] = h-index evaluations in pass i (active r-cliques for AND).
+ * Fills at most cap entries and returns the number of passes in *passes. */
+nd_status nd_last_passes(const nd_incidence* inc, int64_t* changed, int64_t* evaluated,
+                         int32_t cap, int32_t* passes);
+
+/* Device memory held by the handle, in bytes. */
+nd_status nd_incidence_bytes(const nd_incidence* inc, int64_t* bytes);
+
+void nd_free(nd_incidence* inc);
+const char* nd_strerror(nd_status st);
+const char* nd_last_error(void);
+int nd_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ND_H */

@@ -1,0 +1,374 @@
+// C ABI of libnd (declared and documented in include/nd.h).
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <thread>
+
+#include "nd_internal.cuh"
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+void nd_set_error(const std::string& msg) { g_last_error = msg; }
+
+nd_status nd_cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    g_last_error = buf;
+    if (e == cudaErrorMemoryAllocation) return ND_E_NOMEM;
+    return ND_E_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// profiling: per-kernel CUDA events on the launching stream
+// ---------------------------------------------------------------------------
+namespace {
+struct ProfEntry {
+    std::string name;
+    int64_t launches = 0;
+    double ms = 0.0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfEntry> g_prof;
+
+int prof_id(const char* name) {
+    for (size_t i = 0; i < g_prof.size(); ++i)
+        if (g_prof[i].name == name) return (int)i;
+    g_prof.push_back(ProfEntry());
+    g_prof.back().name = name;
+    return (int)g_prof.size() - 1;
+}
+
+void prof_drain() {
+    for (auto& e : g_prof) {
+        for (auto& pr : e.pending) {
+            cudaEventSynchronize(pr.second);
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) e.ms += ms;
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        e.pending.clear();
+    }
+}
+}  // namespace
+
+nd_prof_scope::nd_prof_scope(const char* name, cudaStream_t s) : kid(-1), st(s), a(nullptr), b(nullptr), on(false) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return;
+    kid = prof_id(name);
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return;
+    cudaEventRecord(a, st);
+    on = true;
+}
+
+nd_prof_scope::~nd_prof_scope() {
+    if (!on) return;
+    cudaEventRecord(b, st);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof[kid].launches++;
+    g_prof[kid].pending.push_back({a, b});
+}
+
+// ---------------------------------------------------------------------------
+// device memory (stream-ordered; the pool keeps freed blocks for reuse)
+// ---------------------------------------------------------------------------
+nd_status nd_alloc(void** p, size_t bytes, cudaStream_t st, nd_incidence* owner) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        char buf[160];
+        snprintf(buf, sizeof(buf), "device allocation of %zu bytes failed", bytes);
+        nd_set_error(buf);
+        return ND_E_NOMEM;
+    }
+    if (owner) owner->bytes += (int64_t)bytes;
+    return ND_OK;
+}
+
+void nd_release(void* p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+
+static void keep_pool(int dev) {
+    static std::once_flag once[64];
+    if (dev < 0 || dev >= 64) return;
+    std::call_once(once[dev], [dev]() {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
+}
+
+static nd_status host_wait(cudaStream_t st) {
+    // bounded wait: poll the stream instead of blocking forever
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(st);
+        if (e == cudaSuccess) return ND_OK;
+        if (e != cudaErrorNotReady) return nd_cuda_fail(e, "cudaStreamQuery", __FILE__, __LINE__);
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(3600)) {
+            nd_set_error("stream did not finish within 3600 s");
+            return ND_E_TIMEOUT;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int nd_abi_version(void) { return 1; }
+
+const char* nd_strerror(nd_status st) {
+    switch (st) {
+        case ND_OK: return "ok";
+        case ND_E_INVAL: return "invalid argument or malformed graph";
+        case ND_E_UNSUPPORTED_RS: return "unsupported (r,s): use (1,2), (2,3) or (3,4)";
+        case ND_E_NOMEM: return "out of memory";
+        case ND_E_CUDA: return "CUDA runtime error";
+        case ND_E_NOT_CONVERGED: return "iteration cap reached before convergence";
+        case ND_E_TIMEOUT: return "timed out";
+        case ND_E_TOO_LARGE: return "problem exceeds the 32-bit id space";
+    }
+    return "unknown status";
+}
+
+const char* nd_last_error(void) { return g_last_error.c_str(); }
+
+void nd_free(nd_incidence* h) {
+    if (!h) return;
+    cudaStream_t st = 0;
+    cudaDeviceSynchronize();  // no kernel of any stream may still use the buffers
+    void* ptrs[] = {h->nlow, h->up_start, h->eid, h->e_u, h->e_v, h->tri_ptr, h->tri_w, h->tri_e,
+                    h->perm, h->tau[0], h->tau[1], h->front[0], h->front[1], h->counters};
+    for (void* p : ptrs) nd_release(p, st);
+    if (!h->inc_aliases_graph) {
+        nd_release(h->inc_ptr, st);
+        nd_release(h->inc, st);
+    }
+    nd_release(h->rp, st);
+    nd_release(h->col, st);
+    if (h->h_counters) cudaFreeHost(h->h_counters);
+    cudaStreamSynchronize(st);
+    delete h;
+}
+
+nd_status nd_build_incidence(const nd_csr* g, int r, int s, void* stream, nd_incidence** out) {
+    if (!out) { nd_set_error("out is NULL"); return ND_E_INVAL; }
+    *out = nullptr;
+    if (!g) { nd_set_error("graph is NULL"); return ND_E_INVAL; }
+    if (r < 1 || s <= r) { nd_set_error("need 1 <= r < s"); return ND_E_INVAL; }
+    if (!((r == 1 && s == 2) || (r == 2 && s == 3) || (r == 3 && s == 4))) {
+        nd_set_error("only (1,2), (2,3) and (3,4) are implemented");
+        return ND_E_UNSUPPORTED_RS;
+    }
+    if (g->n < 0 || g->nnz < 0 || !g->row_ptr || (g->nnz > 0 && !g->col)) {
+        nd_set_error("bad CSR header");
+        return ND_E_INVAL;
+    }
+    if (g->n >= INT32_MAX) { nd_set_error("more than 2^31-1 vertices"); return ND_E_TOO_LARGE; }
+    if (g->n == 0 && g->nnz != 0) { nd_set_error("nnz > 0 with no vertices"); return ND_E_INVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    ND_CUDA(cudaGetDevice(&dev));
+    keep_pool(dev);
+    nd_incidence* h = new (std::nothrow) nd_incidence();
+    if (!h) { nd_set_error("host allocation failed"); return ND_E_NOMEM; }
+    h->r = r;
+    h->s = s;
+    h->q = (r == 1) ? 1 : (r == 2 ? 2 : 3);
+    if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        h->sm_count = 152;
+    nd_status rc = nd_build_graph(h, g, st);
+    if (rc == ND_OK && r >= 2) rc = nd_build_edges(h, st);
+    if (rc == ND_OK) {
+        if (r == 1) {
+            h->num_r = h->n;
+            h->num_inc = h->nnz;
+            h->inc_ptr = h->rp;
+            h->inc = reinterpret_cast<uint32_t*>(h->col);
+            h->inc_aliases_graph = true;
+        } else if (r == 2) {
+            rc = nd_build_tri_incidence(h, st);
+        } else {
+            rc = nd_build_triangles(h, st);
+            if (rc == ND_OK) rc = nd_build_k4_incidence(h, st);
+        }
+    }
+    if (rc == ND_OK) rc = nd_build_buckets(h, st);
+    if (rc == ND_OK) rc = host_wait(st);
+    if (rc != ND_OK) {
+        std::string keep = g_last_error;
+        cudaStreamSynchronize(st);
+        nd_free(h);
+        g_last_error = keep;
+        return rc;
+    }
+    *out = h;
+    return ND_OK;
+}
+
+nd_status nd_incidence_info(const nd_incidence* h, int64_t* num_r, int64_t* num_inc, int* q) {
+    if (!h) { nd_set_error("handle is NULL"); return ND_E_INVAL; }
+    if (num_r) *num_r = h->num_r;
+    if (num_inc) *num_inc = h->num_inc;
+    if (q) *q = h->q;
+    return ND_OK;
+}
+
+nd_status nd_incidence_bytes(const nd_incidence* h, int64_t* bytes) {
+    if (!h || !bytes) { nd_set_error("NULL argument"); return ND_E_INVAL; }
+    *bytes = h->bytes;
+    return ND_OK;
+}
+
+static nd_status deliver(const int32_t* src_dev, int64_t count, int32_t* dst, int on_device, cudaStream_t st) {
+    if (count == 0) return ND_OK;
+    if (on_device) {
+        ND_CUDA(cudaMemcpyAsync(dst, src_dev, sizeof(int32_t) * count, cudaMemcpyDeviceToDevice, st));
+        return ND_OK;
+    }
+    ND_CUDA(cudaMemcpyAsync(dst, src_dev, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, st));
+    return host_wait(st);
+}
+
+nd_status nd_r_cliques(const nd_incidence* h, int32_t* out, int on_device, void* stream) {
+    if (!h || (!out && h->num_r > 0)) { nd_set_error("NULL argument"); return ND_E_INVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t count = h->num_r * h->r;
+    if (count == 0) return ND_OK;
+    if (on_device) return nd_write_r_cliques(h, out, st);
+    int32_t* tmp = nullptr;
+    ND_CUDA(cudaMallocAsync((void**)&tmp, sizeof(int32_t) * count, st));
+    nd_status s = nd_write_r_cliques(h, tmp, st);
+    if (s == ND_OK) s = deliver(tmp, count, out, 0, st);
+    cudaFreeAsync(tmp, st);
+    return s;
+}
+
+nd_status nd_s_degree(const nd_incidence* h, int32_t* out, int on_device, void* stream) {
+    if (!h || (!out && h->num_r > 0)) { nd_set_error("NULL argument"); return ND_E_INVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h->num_r == 0) return ND_OK;
+    if (on_device) return nd_init_tau(const_cast<nd_incidence*>(h), out, st);
+    int32_t* tmp = nullptr;
+    ND_CUDA(cudaMallocAsync((void**)&tmp, sizeof(int32_t) * h->num_r, st));
+    nd_status s = nd_init_tau(const_cast<nd_incidence*>(h), tmp, st);
+    if (s == ND_OK) s = deliver(tmp, h->num_r, out, 0, st);
+    cudaFreeAsync(tmp, st);
+    return s;
+}
+
+static nd_status run_and_deliver(nd_incidence* h, int mode, int32_t max_passes, const int32_t* tau_in,
+                                 int tau_in_on_device, int32_t* tau_out, int on_device,
+                                 int32_t* iters_out, int64_t* evals_out, bool require_convergence,
+                                 cudaStream_t st) {
+    if (!h) { nd_set_error("handle is NULL"); return ND_E_INVAL; }
+    if (!tau_out && h->num_r > 0) { nd_set_error("tau_out is NULL"); return ND_E_INVAL; }
+    if (mode != ND_SND && mode != ND_AND && mode != ND_AND_NN) { nd_set_error("bad mode"); return ND_E_INVAL; }
+    if (max_passes < 0) { nd_set_error("negative iteration cap"); return ND_E_INVAL; }
+    const int32_t* tin_dev = nullptr;
+    int32_t* staged = nullptr;
+    if (tau_in && h->num_r > 0) {
+        if (tau_in_on_device) {
+            tin_dev = tau_in;
+        } else {
+            ND_CUDA(cudaMallocAsync((void**)&staged, sizeof(int32_t) * h->num_r, st));
+            ND_CUDA(cudaMemcpyAsync(staged, tau_in, sizeof(int32_t) * h->num_r, cudaMemcpyHostToDevice, st));
+            tin_dev = staged;
+        }
+    }
+    int32_t* result = nullptr;
+    int32_t updating = 0;
+    int64_t evals = 0;
+    bool converged = false;
+    nd_status s = nd_run(h, mode, max_passes, tin_dev, &result, &updating, &evals, &converged, st);
+    if (staged) cudaFreeAsync(staged, st);
+    if (s != ND_OK) return s;
+    s = deliver(result, h->num_r, tau_out, on_device, st);
+    if (s != ND_OK) return s;
+    if (on_device) ND_TRY(host_wait(st));
+    if (iters_out) *iters_out = updating;
+    if (evals_out) *evals_out = evals;
+    if (require_convergence && !converged) {
+        nd_set_error("iteration cap reached before a pass without change");
+        return ND_E_NOT_CONVERGED;
+    }
+    return ND_OK;
+}
+
+nd_status nd_snd(nd_incidence* h, int32_t* tau_out, int on_device, int32_t max_iters,
+                 int32_t* iters_out, void* stream) {
+    return run_and_deliver(h, ND_SND, max_iters, nullptr, 0, tau_out, on_device, iters_out, nullptr, true,
+                           (cudaStream_t)stream);
+}
+
+nd_status nd_and(nd_incidence* h, int32_t* tau_out, int on_device, int notify, int32_t max_iters,
+                 int32_t* iters_out, int64_t* evals_out, void* stream) {
+    return run_and_deliver(h, notify ? ND_AND : ND_AND_NN, max_iters, nullptr, 0, tau_out, on_device,
+                           iters_out, evals_out, true, (cudaStream_t)stream);
+}
+
+nd_status nd_iterate_k(nd_incidence* h, int mode, int32_t k, int32_t* tau_inout, int tau_init_given,
+                       int on_device, int32_t* updating_out, void* stream) {
+    if (k < 0) { nd_set_error("negative k"); return ND_E_INVAL; }
+    return run_and_deliver(h, mode, k, tau_init_given ? tau_inout : nullptr, on_device, tau_inout,
+                           on_device, updating_out, nullptr, false, (cudaStream_t)stream);
+}
+
+nd_status nd_truss_classic(const int32_t* kappa3, int64_t num_edges, int32_t* out, int on_device,
+                           void* stream) {
+    if (num_edges < 0 || (num_edges > 0 && (!kappa3 || !out))) { nd_set_error("bad arguments"); return ND_E_INVAL; }
+    if (!on_device) {
+        for (int64_t i = 0; i < num_edges; ++i) out[i] = kappa3[i] + 2;
+        return ND_OK;
+    }
+    return nd_classic_truss(kappa3, num_edges, out, (cudaStream_t)stream);
+}
+
+nd_status nd_last_passes(const nd_incidence* h, int64_t* changed, int64_t* evaluated, int32_t cap,
+                         int32_t* passes) {
+    if (!h || !passes) { nd_set_error("NULL argument"); return ND_E_INVAL; }
+    const int32_t n = (int32_t)h->last_changed.size();
+    *passes = n;
+    for (int32_t i = 0; i < n && i < cap; ++i) {
+        if (changed) changed[i] = h->last_changed[i];
+        if (evaluated) evaluated[i] = h->last_evals[i];
+    }
+    return ND_OK;
+}
+
+nd_status nd_prof_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_drain();
+    if (on) {
+        for (auto& e : g_prof) { e.launches = 0; e.ms = 0.0; }
+    }
+    g_prof_on = (on != 0);
+    return ND_OK;
+}
+
+nd_status nd_prof_read(int i, const char** name, int64_t* launches, double* total_ms) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_drain();
+    if (i < 0 || i >= (int)g_prof.size()) return ND_E_INVAL;
+    if (name) *name = g_prof[i].name.c_str();
+    if (launches) *launches = g_prof[i].launches;
+    if (total_ms) *total_ms = g_prof[i].ms;
+    return ND_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,524 @@
+// Incidence construction: r-clique -> s-clique incidence as CSR (Def. 1).
+//
+// The paper discovers the s-cliques of an r-clique through the
+// neighbourhoods of its vertices (Section 4.1, "Time complexity": all
+// (s-r)-tuples of a neighbourhood), and recomputes them on every pass.  Here
+// they are found once, by sorted-list intersection, and stored:
+//   (1,2)  the CSR itself is the incidence (q = 1);
+//   (2,3)  edge (u,v): w in N(u) /\ N(v) -> the pair (id(u,w), id(v,w));
+//   (3,4)  triangle (u,v,w): x in N(u) /\ N(v) /\ N(w) -> the ids of the
+//          triangles {u,v,x}, {u,w,x}, {v,w,x}.
+// Every step is a count pass, an exclusive scan and a fill pass over the same
+// enumeration, so rows come out in canonical order with no atomics.
+// Intersections: one warp per r-clique; the lanes walk the shortest list in
+// order and binary-search each element in the other list(s) (read-only path).
+#include "nd_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ int64_t lower_bound_i32(const int32_t* __restrict__ a, int64_t lo,
+                                                   int64_t hi, int32_t x) {
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (__ldg(a + mid) < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    return (1u << (threadIdx.x & 31)) - 1u;
+}
+
+__device__ __forceinline__ int64_t warp_id_global() {
+    return ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+}
+
+__device__ __forceinline__ int64_t warp_count_global() {
+    return ((int64_t)gridDim.x * blockDim.x) >> 5;
+}
+
+// ---- validation and degree split (one warp per vertex) -------------------
+// A row must lie inside [0, nnz], be strictly increasing, hold ids in [0, n)
+// other than its own, and every entry v of row u needs u in row v.  Writes
+// nlow[u] = #neighbours < u and upcnt[u] = #neighbours > u.  Reads only
+// inside the bounds it has checked, so a malformed graph cannot fault.
+__global__ void k_validate_split(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
+                                 const int32_t* __restrict__ col, int32_t* __restrict__ nlow,
+                                 int64_t* __restrict__ upcnt, int* __restrict__ err) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t u = warp_id_global(); u < n; u += warp_count_global()) {
+        int64_t b = rp[u], e = rp[u + 1];
+        bool bad = (b < 0) || (e < b) || (e > nnz) || (u == 0 && b != 0) || (u == n - 1 && e != nnz);
+        if (bad) {
+            if (lane == 0) { atomicOr(err, 1); nlow[u] = 0; upcnt[u] = 0; }
+            continue;
+        }
+        int low = 0;
+        bool rowbad = false;
+        for (int64_t p = b + lane; p < e; p += 32) {
+            int32_t v = col[p];
+            if (v < 0 || v >= n || v == u) { rowbad = true; continue; }
+            if (p > b && col[p - 1] >= v) rowbad = true;
+            low += (v < u);
+            int64_t vb = rp[v], ve = rp[v + 1];
+            if (vb < 0 || ve < vb || ve > nnz) { rowbad = true; continue; }
+            int64_t pos = lower_bound_i32(col, vb, ve, (int32_t)u);
+            if (pos >= ve || col[pos] != (int32_t)u) rowbad = true;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) low += __shfl_xor_sync(kFull, low, o);
+        rowbad = __any_sync(kFull, rowbad);
+        if (lane == 0) {
+            nlow[u] = low;
+            upcnt[u] = (e - b) - low;
+            if (rowbad) atomicOr(err, 2);
+        }
+    }
+}
+
+// ---- canonical edge ids (one warp per vertex) ------------------------------
+// Edge (u,v), u < v, gets id up_start[u] + (rank of v among u's larger
+// neighbours): lexicographic order.  eid[p] is the id of the edge at CSR
+// position p, for both directions.
+__global__ void k_edge_ids(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                           const int32_t* __restrict__ nlow, const int64_t* __restrict__ up_start,
+                           uint32_t* __restrict__ eid, int32_t* __restrict__ e_u,
+                           int32_t* __restrict__ e_v) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t u = warp_id_global(); u < n; u += warp_count_global()) {
+        const int64_t b = rp[u], e = rp[u + 1];
+        const int64_t first_up = b + nlow[u];
+        const int64_t base = up_start[u];
+        for (int64_t p = b + lane; p < e; p += 32) {
+            int32_t v = col[p];
+            if (p >= first_up) {
+                int64_t id = base + (p - first_up);
+                eid[p] = (uint32_t)id;
+                e_u[id] = (int32_t)u;
+                e_v[id] = v;
+            } else {
+                int64_t vfirst = rp[v] + nlow[v];
+                int64_t pos = lower_bound_i32(col, vfirst, rp[v + 1], (int32_t)u);
+                eid[p] = (uint32_t)(up_start[v] + (pos - vfirst));
+            }
+        }
+    }
+}
+
+// ---- (2,3): triangles of every edge (one warp per edge) --------------------
+// COUNT: ptr[e] = d_3(e).  FILL: writes (eid(u,w), eid(v,w)) for each common
+// neighbour w, in increasing w, at ptr[e] (already scanned).
+template <bool FILL>
+__global__ void k_edge_triangles(int64_t m, const int64_t* __restrict__ rp,
+                                 const int32_t* __restrict__ col, const uint32_t* __restrict__ eid,
+                                 const int32_t* __restrict__ e_u, const int32_t* __restrict__ e_v,
+                                 int64_t* __restrict__ ptr, uint2* __restrict__ inc) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t e = warp_id_global(); e < m; e += warp_count_global()) {
+        const int32_t u = e_u[e], v = e_v[e];
+        int64_t ab = rp[u], ae = rp[u + 1], bb = rp[v], be = rp[v + 1];
+        if (ae - ab > be - bb) { int64_t t = ab; ab = bb; bb = t; t = ae; ae = be; be = t; }
+        int64_t out = FILL ? ptr[e] : 0;
+        int64_t cnt = 0;
+        int64_t lo = bb;  // elements of the short list increase, so searches can start here
+        for (int64_t base = ab; base < ae; base += 32) {
+            int64_t p = base + lane;
+            bool found = false;
+            int64_t pb = 0;
+            int32_t x = 0;
+            if (p < ae) {
+                x = __ldg(col + p);
+                pb = lower_bound_i32(col, lo, be, x);
+                found = (pb < be) && (__ldg(col + pb) == x);
+            }
+            unsigned bal = __ballot_sync(kFull, found);
+            if (FILL && found) {
+                int64_t slot = out + cnt + __popc(bal & lanemask_lt());
+                inc[slot] = make_uint2(__ldg(eid + p), __ldg(eid + pb));
+            }
+            cnt += __popc(bal);
+            // next chunk starts after this chunk's last element: its position in B bounds the rest
+            int64_t last_pb = __shfl_sync(kFull, pb, 31);
+            bool full_chunk = (base + 32 <= ae);
+            if (full_chunk) lo = last_pb;
+        }
+        if (!FILL && lane == 0) ptr[e] = cnt;
+    }
+}
+
+// ---- (3,4) step 1: canonical triangle list (one warp per edge) -------------
+// Edge (u,v), u<v, owns the triangles (u,v,w) with w > v: w in the parts of
+// N(u) and N(v) above v.  COUNT: ptr[e] = number owned.  FILL: tri_w, tri_e.
+template <bool FILL>
+__global__ void k_triangle_list(int64_t m, const int64_t* __restrict__ rp,
+                                const int32_t* __restrict__ col, const int32_t* __restrict__ nlow,
+                                const int64_t* __restrict__ up_start, const int32_t* __restrict__ e_u,
+                                const int32_t* __restrict__ e_v, int64_t* __restrict__ ptr,
+                                int32_t* __restrict__ tri_w, uint32_t* __restrict__ tri_e) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t e = warp_id_global(); e < m; e += warp_count_global()) {
+        const int32_t u = e_u[e], v = e_v[e];
+        // position of v in row u follows from the edge id; entries after it are > v
+        int64_t ab = rp[u] + nlow[u] + (e - up_start[u]) + 1, ae = rp[u + 1];
+        int64_t bb = rp[v] + nlow[v], be = rp[v + 1];
+        if (ae - ab > be - bb) { int64_t t = ab; ab = bb; bb = t; t = ae; ae = be; be = t; }
+        int64_t out = FILL ? ptr[e] : 0;
+        int64_t cnt = 0;
+        int64_t lo = bb;
+        for (int64_t base = ab; base < ae; base += 32) {
+            int64_t p = base + lane;
+            bool found = false;
+            int64_t pb = 0;
+            int32_t x = 0;
+            if (p < ae) {
+                x = __ldg(col + p);
+                pb = lower_bound_i32(col, lo, be, x);
+                found = (pb < be) && (__ldg(col + pb) == x);
+            }
+            unsigned bal = __ballot_sync(kFull, found);
+            if (FILL && found) {
+                int64_t slot = out + cnt + __popc(bal & lanemask_lt());
+                tri_w[slot] = x;
+                tri_e[slot] = (uint32_t)e;
+            }
+            cnt += __popc(bal);
+            int64_t last_pb = __shfl_sync(kFull, pb, 31);
+            if (base + 32 <= ae) lo = last_pb;
+        }
+        if (!FILL && lane == 0) ptr[e] = cnt;
+    }
+}
+
+// id of triangle {a, b, x} where a < b are two vertices of the current
+// triangle, pa / pb the positions of x in rows a / b and e_ab the id of edge
+// (a,b).  Sorted, the triangle's smallest edge is (x,a) if x < a, (a,x) if
+// a < x < b, and (a,b) if x > b; its third vertex is b, b, x.
+__device__ __forceinline__ uint32_t tri_lookup(int32_t a, int32_t b, int32_t x, int64_t pa,
+                                               uint32_t e_ab, const uint32_t* __restrict__ eid,
+                                               const int64_t* __restrict__ tri_ptr,
+                                               const int32_t* __restrict__ tri_w, bool* ok) {
+    uint32_t edge;
+    int32_t third;
+    if (x < b) { edge = __ldg(eid + pa); third = b; }
+    else { edge = e_ab; third = x; }
+    (void)a;
+    int64_t lo = __ldg(tri_ptr + edge), hi = __ldg(tri_ptr + edge + 1);
+    int64_t pos = lower_bound_i32(tri_w, lo, hi, third);
+    if (pos >= hi || __ldg(tri_w + pos) != third) { *ok = false; return 0; }
+    return (uint32_t)pos;
+}
+
+// ---- (3,4) step 2: 4-cliques of every triangle (one warp per triangle) -----
+template <bool FILL>
+__global__ void k_triangle_k4(int64_t T, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                              const uint32_t* __restrict__ eid, const int32_t* __restrict__ e_u,
+                              const int32_t* __restrict__ e_v, const int64_t* __restrict__ tri_ptr,
+                              const int32_t* __restrict__ tri_w, const uint32_t* __restrict__ tri_e,
+                              int64_t* __restrict__ ptr, uint32_t* __restrict__ inc,
+                              int* __restrict__ err) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t t = warp_id_global(); t < T; t += warp_count_global()) {
+        const uint32_t e = tri_e[t];
+        const int32_t vtx[3] = {e_u[e], e_v[e], tri_w[t]};  // u < v < w
+        int64_t rb[3], re[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) { rb[i] = rp[vtx[i]]; re[i] = rp[vtx[i] + 1]; }
+        int A = 0;
+        if (re[1] - rb[1] < re[A] - rb[A]) A = 1;
+        if (re[2] - rb[2] < re[A] - rb[A]) A = 2;
+        const int B1 = (A == 0) ? 1 : 0, B2 = (A == 2) ? 1 : 2;
+        uint32_t e_uw = 0, e_vw = 0;
+        if (FILL) {  // ids of edges (u,w) and (v,w): positions of w in rows u and v
+            int64_t p1 = lower_bound_i32(col, rb[0], re[0], vtx[2]);
+            int64_t p2 = lower_bound_i32(col, rb[1], re[1], vtx[2]);
+            e_uw = __ldg(eid + p1);
+            e_vw = __ldg(eid + p2);
+        }
+        int64_t out = FILL ? ptr[t] : 0;
+        int64_t cnt = 0;
+        bool ok = true;
+        for (int64_t base = rb[A]; base < re[A]; base += 32) {
+            int64_t p = base + lane;
+            bool found = false;
+            int64_t pos[3] = {0, 0, 0};
+            int32_t x = 0;
+            if (p < re[A]) {
+                x = __ldg(col + p);
+                pos[A] = p;
+                pos[B1] = lower_bound_i32(col, rb[B1], re[B1], x);
+                if (pos[B1] < re[B1] && __ldg(col + pos[B1]) == x) {
+                    pos[B2] = lower_bound_i32(col, rb[B2], re[B2], x);
+                    found = (pos[B2] < re[B2]) && (__ldg(col + pos[B2]) == x);
+                }
+            }
+            unsigned bal = __ballot_sync(kFull, found);
+            if (FILL && found) {
+                int64_t slot = out + cnt + __popc(bal & lanemask_lt());
+                uint32_t* dst = inc + 3 * slot;
+                dst[0] = tri_lookup(vtx[0], vtx[1], x, pos[0], e, eid, tri_ptr, tri_w, &ok);
+                dst[1] = tri_lookup(vtx[0], vtx[2], x, pos[0], e_uw, eid, tri_ptr, tri_w, &ok);
+                dst[2] = tri_lookup(vtx[1], vtx[2], x, pos[1], e_vw, eid, tri_ptr, tri_w, &ok);
+            }
+            cnt += __popc(bal);
+        }
+        if (FILL && !ok) atomicOr(err, 4);
+        if (!FILL && lane == 0) ptr[t] = cnt;
+    }
+}
+
+// ---- degree buckets --------------------------------------------------------
+__device__ __forceinline__ int bucket_of(int64_t d) {
+    return d == 0 ? -1 : (d <= 8 ? 0 : (d <= 64 ? 1 : (d <= 1024 ? 2 : 3)));
+}
+
+__global__ void k_bucket_flags(int64_t N, const int64_t* __restrict__ inc_ptr, int b,
+                               int64_t* __restrict__ flags, unsigned long long* __restrict__ inc_sum) {
+    unsigned long long local = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t d = inc_ptr[i + 1] - inc_ptr[i];
+        bool in = bucket_of(d) == b;
+        flags[i] = in;
+        if (in) local += (unsigned long long)d;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(kFull, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(inc_sum, local);
+}
+
+__global__ void k_bucket_scatter(int64_t N, const int64_t* __restrict__ inc_ptr, int b,
+                                 const int64_t* __restrict__ pos, uint32_t* __restrict__ perm) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t d = inc_ptr[i + 1] - inc_ptr[i];
+        if (bucket_of(d) == b) perm[pos[i]] = (uint32_t)i;
+    }
+}
+
+__global__ void k_r_cliques(int r, int64_t N, const int32_t* __restrict__ e_u,
+                            const int32_t* __restrict__ e_v, const int32_t* __restrict__ tri_w,
+                            const uint32_t* __restrict__ tri_e, int32_t* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (r == 1) {
+            out[i] = (int32_t)i;
+        } else if (r == 2) {
+            out[2 * i] = e_u[i];
+            out[2 * i + 1] = e_v[i];
+        } else {
+            uint32_t e = tri_e[i];
+            out[3 * i] = e_u[e];
+            out[3 * i + 1] = e_v[e];
+            out[3 * i + 2] = tri_w[i];
+        }
+    }
+}
+
+int grid_cap(const nd_incidence* h) { return (h->sm_count > 0 ? h->sm_count : 152) * 8; }
+
+nd_status read_flag(int* dflag, int* hval, cudaStream_t st) {
+    ND_CUDA(cudaMemcpyAsync(hval, dflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ND_CUDA(cudaStreamSynchronize(st));
+    return ND_OK;
+}
+
+nd_status read_i64(const int64_t* d, int64_t* hv, cudaStream_t st) {
+    ND_CUDA(cudaMemcpyAsync(hv, d, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    ND_CUDA(cudaStreamSynchronize(st));
+    return ND_OK;
+}
+
+}  // namespace
+
+// Copy the caller's CSR into owned device buffers, validate it, split each
+// row at its own vertex and derive the canonical edge numbering offsets.
+nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st) {
+    h->n = g->n;
+    h->nnz = g->nnz;
+    ND_TRY(nd_alloc((void**)&h->rp, sizeof(int64_t) * (g->n + 1), st, h));
+    ND_TRY(nd_alloc((void**)&h->col, sizeof(int32_t) * (g->nnz > 0 ? g->nnz : 1), st, h));
+    cudaMemcpyKind kind = g->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    ND_CUDA(cudaMemcpyAsync(h->rp, g->row_ptr, sizeof(int64_t) * (g->n + 1), kind, st));
+    if (g->nnz > 0) ND_CUDA(cudaMemcpyAsync(h->col, g->col, sizeof(int32_t) * g->nnz, kind, st));
+    ND_TRY(nd_alloc((void**)&h->nlow, sizeof(int32_t) * (g->n > 0 ? g->n : 1), st, h));
+    ND_TRY(nd_alloc((void**)&h->up_start, sizeof(int64_t) * (g->n + 1), st, h));
+    int* derr = nullptr;
+    ND_CUDA(cudaMallocAsync((void**)&derr, sizeof(int), st));
+    ND_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
+    ND_CUDA(cudaMemsetAsync(h->up_start, 0, sizeof(int64_t) * (g->n + 1), st));
+    if (g->n > 0) {
+        nd_prof_scope ps("validate_split", st);
+        int blocks = nd_blocks_for(g->n * 32, kThreads, grid_cap(h) * 4);
+        k_validate_split<<<blocks, kThreads, 0, st>>>(g->n, g->nnz, h->rp, h->col, h->nlow,
+                                                      h->up_start, derr);
+        ND_CUDA(cudaGetLastError());
+    }
+    int herr = 0;
+    nd_status s = read_flag(derr, &herr, st);
+    cudaFreeAsync(derr, st);
+    if (s != ND_OK) return s;
+    if (herr) {
+        nd_set_error(herr & 1 ? "row_ptr is not a valid offset array"
+                              : "col is not simple, sorted and symmetric");
+        return ND_E_INVAL;
+    }
+    ND_TRY(nd_scan_i64(h->up_start, g->n, st));
+    int64_t m = 0;
+    ND_TRY(read_i64(h->up_start + g->n, &m, st));
+    if (2 * m != g->nnz) {
+        nd_set_error("edge count is inconsistent with nnz");
+        return ND_E_INVAL;
+    }
+    h->m = m;
+    return ND_OK;
+}
+
+nd_status nd_build_edges(nd_incidence* h, cudaStream_t st) {
+    if (h->m >= (int64_t)UINT32_MAX) { nd_set_error("more than 2^32-1 edges"); return ND_E_TOO_LARGE; }
+    ND_TRY(nd_alloc((void**)&h->eid, sizeof(uint32_t) * (h->nnz > 0 ? h->nnz : 1), st, h));
+    ND_TRY(nd_alloc((void**)&h->e_u, sizeof(int32_t) * (h->m > 0 ? h->m : 1), st, h));
+    ND_TRY(nd_alloc((void**)&h->e_v, sizeof(int32_t) * (h->m > 0 ? h->m : 1), st, h));
+    if (h->n > 0 && h->nnz > 0) {
+        nd_prof_scope ps("edge_ids", st);
+        int blocks = nd_blocks_for(h->n * 32, kThreads, grid_cap(h) * 4);
+        k_edge_ids<<<blocks, kThreads, 0, st>>>(h->n, h->rp, h->col, h->nlow, h->up_start, h->eid,
+                                                h->e_u, h->e_v);
+        ND_CUDA(cudaGetLastError());
+    }
+    return ND_OK;
+}
+
+nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
+    h->num_r = h->m;
+    ND_TRY(nd_alloc((void**)&h->inc_ptr, sizeof(int64_t) * (h->m + 1), st, h));
+    ND_CUDA(cudaMemsetAsync(h->inc_ptr, 0, sizeof(int64_t) * (h->m + 1), st));
+    int blocks = nd_blocks_for(h->m * 32, kThreads, grid_cap(h) * 4);
+    if (h->m > 0) {
+        nd_prof_scope ps("tri_count", st);
+        k_edge_triangles<false><<<blocks, kThreads, 0, st>>>(h->m, h->rp, h->col, h->eid, h->e_u,
+                                                             h->e_v, h->inc_ptr, nullptr);
+        ND_CUDA(cudaGetLastError());
+    }
+    ND_TRY(nd_scan_i64(h->inc_ptr, h->m, st));
+    ND_TRY(read_i64(h->inc_ptr + h->m, &h->num_inc, st));
+    ND_TRY(nd_alloc((void**)&h->inc, sizeof(uint32_t) * 2 * (h->num_inc > 0 ? h->num_inc : 1), st, h));
+    if (h->num_inc > 0) {
+        nd_prof_scope ps("tri_fill", st);
+        k_edge_triangles<true><<<blocks, kThreads, 0, st>>>(h->m, h->rp, h->col, h->eid, h->e_u,
+                                                            h->e_v, h->inc_ptr, (uint2*)h->inc);
+        ND_CUDA(cudaGetLastError());
+    }
+    return ND_OK;
+}
+
+nd_status nd_build_triangles(nd_incidence* h, cudaStream_t st) {
+    ND_TRY(nd_alloc((void**)&h->tri_ptr, sizeof(int64_t) * (h->m + 1), st, h));
+    ND_CUDA(cudaMemsetAsync(h->tri_ptr, 0, sizeof(int64_t) * (h->m + 1), st));
+    int blocks = nd_blocks_for(h->m * 32, kThreads, grid_cap(h) * 4);
+    if (h->m > 0) {
+        nd_prof_scope ps("tri_list_count", st);
+        k_triangle_list<false><<<blocks, kThreads, 0, st>>>(h->m, h->rp, h->col, h->nlow, h->up_start,
+                                                            h->e_u, h->e_v, h->tri_ptr, nullptr,
+                                                            nullptr);
+        ND_CUDA(cudaGetLastError());
+    }
+    ND_TRY(nd_scan_i64(h->tri_ptr, h->m, st));
+    ND_TRY(read_i64(h->tri_ptr + h->m, &h->num_tri, st));
+    if (h->num_tri >= (int64_t)UINT32_MAX) { nd_set_error("more than 2^32-1 triangles"); return ND_E_TOO_LARGE; }
+    ND_TRY(nd_alloc((void**)&h->tri_w, sizeof(int32_t) * (h->num_tri > 0 ? h->num_tri : 1), st, h));
+    ND_TRY(nd_alloc((void**)&h->tri_e, sizeof(uint32_t) * (h->num_tri > 0 ? h->num_tri : 1), st, h));
+    if (h->num_tri > 0) {
+        nd_prof_scope ps("tri_list_fill", st);
+        k_triangle_list<true><<<blocks, kThreads, 0, st>>>(h->m, h->rp, h->col, h->nlow, h->up_start,
+                                                           h->e_u, h->e_v, h->tri_ptr, h->tri_w,
+                                                           h->tri_e);
+        ND_CUDA(cudaGetLastError());
+    }
+    return ND_OK;
+}
+
+nd_status nd_build_k4_incidence(nd_incidence* h, cudaStream_t st) {
+    const int64_t T = h->num_tri;
+    h->num_r = T;
+    ND_TRY(nd_alloc((void**)&h->inc_ptr, sizeof(int64_t) * (T + 1), st, h));
+    ND_CUDA(cudaMemsetAsync(h->inc_ptr, 0, sizeof(int64_t) * (T + 1), st));
+    int blocks = nd_blocks_for(T * 32, kThreads, grid_cap(h) * 4);
+    int* derr = nullptr;
+    ND_CUDA(cudaMallocAsync((void**)&derr, sizeof(int), st));
+    ND_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
+    if (T > 0) {
+        nd_prof_scope ps("k4_count", st);
+        k_triangle_k4<false><<<blocks, kThreads, 0, st>>>(T, h->rp, h->col, h->eid, h->e_u, h->e_v,
+                                                          h->tri_ptr, h->tri_w, h->tri_e, h->inc_ptr,
+                                                          nullptr, derr);
+        ND_CUDA(cudaGetLastError());
+    }
+    ND_TRY(nd_scan_i64(h->inc_ptr, T, st));
+    ND_TRY(read_i64(h->inc_ptr + T, &h->num_inc, st));
+    ND_TRY(nd_alloc((void**)&h->inc, sizeof(uint32_t) * 3 * (h->num_inc > 0 ? h->num_inc : 1), st, h));
+    if (h->num_inc > 0) {
+        nd_prof_scope ps("k4_fill", st);
+        k_triangle_k4<true><<<blocks, kThreads, 0, st>>>(T, h->rp, h->col, h->eid, h->e_u, h->e_v,
+                                                         h->tri_ptr, h->tri_w, h->tri_e, h->inc_ptr,
+                                                         h->inc, derr);
+        ND_CUDA(cudaGetLastError());
+    }
+    int herr = 0;
+    nd_status s = read_flag(derr, &herr, st);
+    cudaFreeAsync(derr, st);
+    if (s != ND_OK) return s;
+    if (herr) { nd_set_error("internal: a triangle of a 4-clique was not found"); return ND_E_INVAL; }
+    return ND_OK;
+}
+
+nd_status nd_build_buckets(nd_incidence* h, cudaStream_t st) {
+    const int64_t N = h->num_r;
+    int64_t* flags = nullptr;
+    unsigned long long* sums = nullptr;
+    ND_CUDA(cudaMallocAsync((void**)&flags, sizeof(int64_t) * (N + 1), st));
+    ND_CUDA(cudaMallocAsync((void**)&sums, sizeof(unsigned long long) * ND_NB, st));
+    ND_CUDA(cudaMemsetAsync(sums, 0, sizeof(unsigned long long) * ND_NB, st));
+    ND_TRY(nd_alloc((void**)&h->perm, sizeof(uint32_t) * (N > 0 ? N : 1), st, h));
+    int blocks = nd_blocks_for(N, kThreads, grid_cap(h) * 2);
+    int64_t lo = 0;
+    for (int b = 0; b < ND_NB; ++b) {
+        h->bucket_lo[b] = lo;
+        if (N == 0) continue;
+        ND_CUDA(cudaMemsetAsync(flags + N, 0, sizeof(int64_t), st));
+        {
+            nd_prof_scope ps("buckets", st);
+            k_bucket_flags<<<blocks, kThreads, 0, st>>>(N, h->inc_ptr, b, flags, sums + b);
+            ND_CUDA(cudaGetLastError());
+        }
+        ND_TRY(nd_scan_i64(flags, N, st));
+        {
+            nd_prof_scope ps("buckets", st);
+            k_bucket_scatter<<<blocks, kThreads, 0, st>>>(N, h->inc_ptr, b, flags, h->perm + lo);
+            ND_CUDA(cudaGetLastError());
+        }
+        int64_t cnt = 0;
+        ND_TRY(read_i64(flags + N, &cnt, st));
+        lo += cnt;
+    }
+    h->bucket_lo[ND_NB] = lo;
+    unsigned long long hs[ND_NB] = {0, 0, 0, 0};
+    ND_CUDA(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    ND_CUDA(cudaStreamSynchronize(st));
+    for (int b = 0; b < ND_NB; ++b) h->bucket_inc[b] = (int64_t)hs[b];
+    h->num_zero = N - lo;
+    cudaFreeAsync(flags, st);
+    cudaFreeAsync(sums, st);
+    return ND_OK;
+}
+
+nd_status nd_write_r_cliques(const nd_incidence* h, int32_t* out_dev, cudaStream_t st) {
+    if (h->num_r == 0) return ND_OK;
+    int blocks = nd_blocks_for(h->num_r, kThreads, grid_cap(h) * 2);
+    nd_prof_scope ps("r_cliques", st);
+    k_r_cliques<<<blocks, kThreads, 0, st>>>(h->r, h->num_r, h->e_u, h->e_v, h->tri_w, h->tri_e, out_dev);
+    ND_CUDA(cudaGetLastError());
+    return ND_OK;
+}

@@ -1,0 +1,115 @@
+// Internal declarations shared by the libnd translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "nd.h"
+
+// ----------------------------------------------------------------------------
+// error handling: every CUDA call is checked; failures become ND_E_CUDA with a
+// thread-local message, never an abort.
+// ----------------------------------------------------------------------------
+void nd_set_error(const std::string& msg);
+nd_status nd_cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define ND_CUDA(call)                                                         \
+    do {                                                                      \
+        cudaError_t nd_e_ = (call);                                           \
+        if (nd_e_ != cudaSuccess) return nd_cuda_fail(nd_e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define ND_TRY(expr)                                                          \
+    do {                                                                      \
+        nd_status nd_s_ = (expr);                                             \
+        if (nd_s_ != ND_OK) return nd_s_;                                     \
+    } while (0)
+
+// ----------------------------------------------------------------------------
+// per-kernel timing (CUDA events on the launching stream), see nd_prof_*
+// ----------------------------------------------------------------------------
+struct nd_prof_scope {
+    int kid;
+    cudaStream_t st;
+    cudaEvent_t a, b;
+    bool on;
+    nd_prof_scope(const char* name, cudaStream_t s);
+    ~nd_prof_scope();
+};
+
+// ----------------------------------------------------------------------------
+// degree buckets for the h-index sweeps: r-cliques are grouped by d_s so that
+// each group of lanes that evaluates one r-clique is sized to its work.
+// ----------------------------------------------------------------------------
+enum { ND_NB = 4 };  // bucket 0: d_s in [1,8], 1: [9,64], 2: [65,1024], 3: > 1024
+
+struct nd_incidence {
+    int r = 0, s = 0, q = 0;
+    int64_t n = 0, nnz = 0, m = 0;  // m = number of edges (nnz / 2)
+    int64_t num_r = 0, num_inc = 0, num_tri = 0;
+    int sm_count = 0;
+    // graph on the device (owned copies)
+    int64_t* rp = nullptr;
+    int32_t* col = nullptr;
+    int32_t* nlow = nullptr;       // [n] number of neighbours smaller than u
+    int64_t* up_start = nullptr;   // [n+1] first edge id owned by u (edges u<v)
+    uint32_t* eid = nullptr;       // [nnz] edge id of every CSR entry
+    int32_t* e_u = nullptr;        // [m] canonical edges (u<v), lexicographic
+    int32_t* e_v = nullptr;
+    int64_t* tri_ptr = nullptr;    // [m+1] triangles (u<v<w) grouped by edge (u,v)
+    int32_t* tri_w = nullptr;      // [T] third vertex w, ascending inside a group
+    uint32_t* tri_e = nullptr;     // [T] owning edge (u,v)
+    // incidence (r-clique -> other r-cliques of each s-clique)
+    int64_t* inc_ptr = nullptr;    // [num_r+1]
+    uint32_t* inc = nullptr;       // [num_inc*q]
+    bool inc_aliases_graph = false;  // r = 1: inc_ptr/inc are rp/col
+    // degree-bucketed processing order
+    uint32_t* perm = nullptr;      // [num_r_active]
+    int64_t bucket_lo[ND_NB + 1] = {0, 0, 0, 0, 0};
+    int64_t bucket_inc[ND_NB] = {0, 0, 0, 0};
+    int64_t num_zero = 0;          // r-cliques with d_s = 0 (kappa = 0, never updated)
+    // iteration state
+    int32_t* tau[2] = {nullptr, nullptr};
+    uint32_t* front[2] = {nullptr, nullptr};
+    unsigned long long* counters = nullptr;  // ring of per-pass counters
+    unsigned long long* h_counters = nullptr;  // pinned host mirror
+    std::vector<int64_t> last_changed, last_evals;
+    int64_t bytes = 0;
+};
+
+enum { ND_RING = 256 };  // per-pass counter slots (2 x u64 each)
+
+// device memory helpers (stream-ordered)
+nd_status nd_alloc(void** p, size_t bytes, cudaStream_t st, nd_incidence* owner);
+void nd_release(void* p, cudaStream_t st);
+
+// exclusive scan of data[0..count] in place (count+1 entries; data[count]
+// becomes the total).  Uses stream-ordered scratch.
+nd_status nd_scan_i64(int64_t* data, int64_t count, cudaStream_t st);
+
+// build steps (nd_build.cu)
+nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st);
+nd_status nd_build_edges(nd_incidence* h, cudaStream_t st);
+nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st);
+nd_status nd_build_triangles(nd_incidence* h, cudaStream_t st);
+nd_status nd_build_k4_incidence(nd_incidence* h, cudaStream_t st);
+nd_status nd_build_buckets(nd_incidence* h, cudaStream_t st);
+nd_status nd_write_r_cliques(const nd_incidence* h, int32_t* out_dev, cudaStream_t st);
+
+// iteration (nd_hindex.cu)
+nd_status nd_init_tau(nd_incidence* h, int32_t* tau, cudaStream_t st);
+nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* tau_in_dev,
+                 int32_t** tau_result, int32_t* updating, int64_t* evals, bool* converged,
+                 cudaStream_t st);
+nd_status nd_classic_truss(const int32_t* in, int64_t n, int32_t* out, cudaStream_t st);
+
+// launch geometry
+static inline int nd_blocks_for(int64_t work_items, int per_block, int cap) {
+    int64_t b = (work_items + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}

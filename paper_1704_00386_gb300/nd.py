@@ -1,0 +1,280 @@
+"""Thin ctypes binding of libnd (include/nd.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library.  There is no CPU
+fallback: if the library is missing or cannot be loaded this module raises.
+
+Arrays may be numpy arrays (host memory; on_device = 0) or CUDA torch tensors
+(device memory; on_device = 1).  Results come back in the same kind of
+memory as the input graph: numpy for a host graph, torch CUDA tensors for a
+device graph.  Calls run on torch's current CUDA stream unless a stream is
+given.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+ND_OK, ND_E_INVAL, ND_E_UNSUPPORTED_RS, ND_E_NOMEM, ND_E_CUDA, ND_E_NOT_CONVERGED, \
+    ND_E_TIMEOUT, ND_E_TOO_LARGE = range(8)
+ND_SND, ND_AND, ND_AND_NN = 0, 1, 2
+MODES = {"snd": ND_SND, "and": ND_AND, "and_nn": ND_AND_NN}
+
+SYMBOLS = ["nd_build_incidence", "nd_incidence_info", "nd_r_cliques", "nd_s_degree", "nd_snd",
+           "nd_and", "nd_iterate_k", "nd_truss_classic", "nd_prof_enable", "nd_prof_read",
+           "nd_last_passes", "nd_incidence_bytes", "nd_free", "nd_strerror", "nd_last_error",
+           "nd_abi_version"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class NDError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status} ({msg})")
+        self.status = status
+
+
+class _CSR(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("on_device", ctypes.c_int)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libnd (building it in-tree with nvcc if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and (not os.path.exists(path) or _build._stale()):
+            _build.build()
+        if not os.path.exists(path):
+            raise ImportError(f"libnd is not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        i32, i64, vp, ci = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int
+        P = ctypes.POINTER
+        lib.nd_build_incidence.argtypes = [P(_CSR), ci, ci, vp, P(vp)]
+        lib.nd_incidence_info.argtypes = [vp, P(i64), P(i64), P(ci)]
+        lib.nd_r_cliques.argtypes = [vp, vp, ci, vp]
+        lib.nd_s_degree.argtypes = [vp, vp, ci, vp]
+        lib.nd_snd.argtypes = [vp, vp, ci, i32, P(i32), vp]
+        lib.nd_and.argtypes = [vp, vp, ci, ci, i32, P(i32), P(i64), vp]
+        lib.nd_iterate_k.argtypes = [vp, ci, i32, vp, ci, ci, P(i32), vp]
+        lib.nd_truss_classic.argtypes = [vp, i64, vp, ci, vp]
+        lib.nd_prof_enable.argtypes = [ci]
+        lib.nd_prof_read.argtypes = [ci, P(ctypes.c_char_p), P(i64), P(ctypes.c_double)]
+        lib.nd_last_passes.argtypes = [vp, vp, vp, i32, P(i32)]
+        lib.nd_incidence_bytes.argtypes = [vp, P(i64)]
+        lib.nd_free.argtypes = [vp]
+        lib.nd_free.restype = None
+        lib.nd_strerror.argtypes = [ci]
+        lib.nd_strerror.restype = ctypes.c_char_p
+        lib.nd_last_error.restype = ctypes.c_char_p
+        for name in SYMBOLS:
+            f = getattr(lib, name)
+            if f.restype is ctypes.c_int:  # default restype: nd_status
+                f.restype = ci
+        _lib = lib
+        return lib
+
+
+def _check(st: int, where: str):
+    if st != ND_OK:
+        lib = load()
+        raise NDError(st, where, f"{lib.nd_strerror(st).decode()}: {lib.nd_last_error().decode()}")
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _stream_ptr(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    import torch
+    if torch.cuda.is_available():
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _ptr(x):
+    if _is_torch(x):
+        return ctypes.c_void_p(x.data_ptr())
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def _empty(n, like_device: bool, device=None, dtype="int32"):
+    if like_device:
+        import torch
+        return torch.empty(n, dtype=getattr(torch, dtype), device=device)
+    return np.empty(n, dtype=dtype)
+
+
+class Incidence:
+    """A built r-clique -> s-clique incidence (library-owned device memory)."""
+
+    def __init__(self, handle, r, s, on_device, device, stream):
+        self._h = handle
+        self.r, self.s = r, s
+        self.on_device = on_device
+        self.device = device
+        self._stream = stream
+        n_r, n_inc, q = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        _check(load().nd_incidence_info(self._h, ctypes.byref(n_r), ctypes.byref(n_inc),
+                                        ctypes.byref(q)), "nd_incidence_info")
+        self.num_r, self.num_incidences, self.q = n_r.value, n_inc.value, q.value
+
+    # -- lifetime
+    def free(self):
+        if self._h is not None and self._h.value:
+            load().nd_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def _alloc(self, n, dtype="int32"):
+        return _empty(n, self.on_device, self.device, dtype)
+
+    def _sp(self, stream):
+        return _stream_ptr(stream if stream is not None else self._stream)
+
+    # -- calls (same names as the C ABI)
+    def incidence_info(self):
+        return self.num_r, self.num_incidences, self.q
+
+    def incidence_bytes(self) -> int:
+        b = ctypes.c_int64()
+        _check(load().nd_incidence_bytes(self._h, ctypes.byref(b)), "nd_incidence_bytes")
+        return b.value
+
+    def r_cliques(self, stream=None):
+        out = self._alloc(self.num_r * self.r)
+        _check(load().nd_r_cliques(self._h, _ptr(out), int(self.on_device), self._sp(stream)),
+               "nd_r_cliques")
+        return out.reshape(self.num_r, self.r)
+
+    def s_degree(self, stream=None):
+        out = self._alloc(self.num_r)
+        _check(load().nd_s_degree(self._h, _ptr(out), int(self.on_device), self._sp(stream)),
+               "nd_s_degree")
+        return out
+
+    def snd(self, max_iters: int = 1 << 30, out=None, stream=None):
+        """SND (Alg. 2) to convergence.  Returns (tau, updating passes)."""
+        tau = self._alloc(self.num_r) if out is None else out
+        it = ctypes.c_int32()
+        _check(load().nd_snd(self._h, _ptr(tau), int(self.on_device), int(max_iters),
+                             ctypes.byref(it), self._sp(stream)), "nd_snd")
+        return tau, it.value
+
+    def and_(self, notify: bool = True, max_iters: int = 1 << 30, out=None, stream=None):
+        """AND (Alg. 3) to convergence.  Returns (tau, updating passes, evaluations)."""
+        tau = self._alloc(self.num_r) if out is None else out
+        it, ev = ctypes.c_int32(), ctypes.c_int64()
+        _check(load().nd_and(self._h, _ptr(tau), int(self.on_device), int(bool(notify)),
+                             int(max_iters), ctypes.byref(it), ctypes.byref(ev), self._sp(stream)),
+               "nd_and")
+        return tau, it.value, ev.value
+
+    def iterate_k(self, mode: str, k: int, tau=None, stream=None):
+        """At most k passes of mode ('snd', 'and', 'and_nn') from tau (or d_s).
+        Returns (tau, updating passes); tau is a new array."""
+        if tau is None:
+            buf = self._alloc(self.num_r)
+            given = 0
+        else:
+            if _is_torch(tau) != bool(self.on_device):
+                raise ValueError("tau must live where the graph lives")
+            buf = tau.clone() if _is_torch(tau) else np.array(tau, dtype=np.int32, copy=True)
+            given = 1
+        up = ctypes.c_int32()
+        _check(load().nd_iterate_k(self._h, MODES[mode], int(k), _ptr(buf), given,
+                                   int(self.on_device), ctypes.byref(up), self._sp(stream)),
+               "nd_iterate_k")
+        return buf, up.value
+
+    def last_passes(self):
+        """(changed, evaluated) per pass of the last iteration call."""
+        lib = load()
+        n = ctypes.c_int32()
+        _check(lib.nd_last_passes(self._h, None, None, 0, ctypes.byref(n)), "nd_last_passes")
+        ch = np.zeros(max(n.value, 1), np.int64)
+        ev = np.zeros(max(n.value, 1), np.int64)
+        _check(lib.nd_last_passes(self._h, _ptr(ch), _ptr(ev), n.value, ctypes.byref(n)),
+               "nd_last_passes")
+        return ch[:n.value], ev[:n.value]
+
+
+def build_incidence(row_ptr, col, r: int, s: int, stream=None) -> Incidence:
+    """nd_build_incidence on a CSR given as numpy arrays (host) or CUDA tensors."""
+    lib = load()
+    on_device = _is_torch(row_ptr)
+    if on_device != _is_torch(col):
+        raise ValueError("row_ptr and col must both be host arrays or both CUDA tensors")
+    device = None
+    if on_device:
+        import torch
+        if not (row_ptr.is_cuda and col.is_cuda):
+            raise ValueError("torch tensors must be on a CUDA device")
+        row_ptr = row_ptr.to(torch.int64).contiguous()
+        col = col.to(torch.int32).contiguous()
+        device = row_ptr.device
+        n, nnz = row_ptr.numel() - 1, col.numel()
+    else:
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        n, nnz = row_ptr.size - 1, col.size
+    csr = _CSR(n, nnz, _ptr(row_ptr).value, _ptr(col).value if nnz else None, int(on_device))
+    h = ctypes.c_void_p()
+    _check(lib.nd_build_incidence(ctypes.byref(csr), int(r), int(s), _stream_ptr(stream),
+                                  ctypes.byref(h)), "nd_build_incidence")
+    return Incidence(h, r, s, on_device, device, stream)
+
+
+def truss_classic(kappa3, stream=None):
+    """Classic (k-2 convention) truss numbers: kappa_3 + 2 (nd_truss_classic)."""
+    on_device = _is_torch(kappa3)
+    out = _empty(len(kappa3), on_device, kappa3.device if on_device else None)
+    src = kappa3 if on_device else np.ascontiguousarray(kappa3, dtype=np.int32)
+    _check(load().nd_truss_classic(_ptr(src), len(kappa3), _ptr(out), int(on_device),
+                                   _stream_ptr(stream)), "nd_truss_classic")
+    return out
+
+
+def prof_enable(on: bool = True):
+    _check(load().nd_prof_enable(int(on)), "nd_prof_enable")
+
+
+def prof_read() -> dict:
+    """{kernel name: (launches, total ms)} recorded since prof_enable(True)."""
+    lib = load()
+    out = {}
+    i = 0
+    while True:
+        name, n, ms = ctypes.c_char_p(), ctypes.c_int64(), ctypes.c_double()
+        if lib.nd_prof_read(i, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms)) != ND_OK:
+            break
+        out[name.value.decode()] = (n.value, ms.value)
+        i += 1
+    return out
+
+
+def strerror(status: int) -> str:
+    return load().nd_strerror(int(status)).decode()
+
+
+def abi_version() -> int:
+    return int(load().nd_abi_version())

@@ -1,0 +1,67 @@
+"""CPU-side checks of the C ABI: the library builds, loads, and exports every
+function include/nd.h declares; host-only calls work without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1704_00386_gb300 import nd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fname in os.listdir(os.path.join(ROOT, "include")):
+        if fname.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fname)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(nd_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = nd.load()
+    declared = _declared()
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(nd.SYMBOLS) == set(declared)
+
+
+def test_host_only_calls():
+    assert nd.abi_version() == 1
+    assert nd.strerror(nd.ND_OK) == "ok"
+    assert "unsupported" in nd.strerror(nd.ND_E_UNSUPPORTED_RS)
+    lib = nd.load()
+    assert isinstance(lib.nd_last_error(), bytes)
+
+
+def test_classic_truss_host_path():
+    import numpy as np
+    k = np.array([0, 1, 5], np.int32)
+    assert nd.truss_classic(k).tolist() == [2, 3, 7]
+
+
+def test_rejects_bad_arguments_before_touching_the_gpu():
+    import numpy as np
+    rp = np.array([0, 1, 2], np.int64)
+    col = np.array([1, 0], np.int32)
+    with pytest.raises(nd.NDError) as e:
+        nd.build_incidence(rp, col, 1, 3)
+    assert e.value.status == nd.ND_E_UNSUPPORTED_RS
+    with pytest.raises(nd.NDError) as e:
+        nd.build_incidence(rp, col, 2, 2)
+    assert e.value.status == nd.ND_E_INVAL
+    lib = nd.load()
+    out = ctypes.c_void_p()
+    assert lib.nd_build_incidence(None, 1, 2, None, ctypes.byref(out)) == nd.ND_E_INVAL
+
+
+def test_binding_has_no_cpu_fallback():
+    src = open(os.path.join(ROOT, "paper_1704_00386_gb300", "nd.py")).read()
+    assert "oracle" not in src
+    for f in os.listdir(os.path.join(ROOT, "paper_1704_00386_gb300")):
+        if f.endswith(".py"):
+            assert "import oracle" not in open(os.path.join(ROOT, "paper_1704_00386_gb300", f)).read()

@@ -1,0 +1,189 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integers throughout, so every comparison is bit-exact: r-clique tuples, d_s,
+kappa_s from SND / AND / AND-nn, the SND iterates tau_k (deterministic,
+Alg. 2) and iteration counts.  AND iterates are schedule-dependent and are
+checked against the bounds kappa <= tau_AND_k <= tau_SND_k.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1704_00386_gb300 import graphs as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RS = [(1, 2), (2, 3), (3, 4)]
+
+
+@pytest.fixture(scope="module")
+def nd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_00386_gb300 import nd as _nd
+    _nd.load()
+    return _nd
+
+
+def _cases():
+    out = {}
+    out["toy"] = G.toy_core_graph()
+    out["k7"] = G.complete_graph(7)
+    s, d = G.chung_lu(600, 2.3, 9.0, seed=101)
+    out["chunglu600"] = G.to_csr(600, s, d)
+    i, j = G.erdos_renyi(500, 12 / 499, seed=102)
+    out["er500"] = G.to_csr(500, i, j)
+    n, s, d = G.rmat(10, 8, seed=103)
+    out["rmat10"] = G.to_csr(n, s, d)
+    # planted cliques over a sparse background: deep (3,4) nuclei, wide tails
+    s1, d1 = G.chung_lu(800, 2.1, 6.0, seed=104)
+    s2, d2 = G.plant_cliques(800, 6, 8, 22, seed=105)
+    out["planted800"] = G.to_csr(800, np.concatenate([s1, s2]), np.concatenate([d1, d2]))
+    # an edge in > 1024 triangles (streaming bucket for (2,3)) and a vertex of
+    # degree > 1024 (streaming bucket for (1,2)), with a clique among the fan
+    fan = 1300
+    src = [0] * fan + [1] * fan + [0]
+    dst = list(range(2, fan + 2)) + list(range(2, fan + 2)) + [1]
+    a, b = np.triu_indices(40, 1)
+    src += list(a + 2)
+    dst += list(b + 2)
+    out["book1300"] = G.to_csr(fan + 2, src, dst)
+    return out
+
+
+CASES = _cases()
+
+
+def _run_all(nd, rp, col, r, s):
+    inc = nd.build_incidence(rp, col, r, s)
+    g = oracle.Graph(rp, col, r, s)
+    return inc, g
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("rs", RS)
+def test_small_graphs_bit_exact(nd, name, rs):
+    rp, col = CASES[name]
+    inc, g = _run_all(nd, rp, col, *rs)
+    assert inc.num_r == g.num_r
+    assert inc.q == g.q
+    assert inc.num_incidences == g.num_incidences
+    if g.num_r == 0:
+        return
+    np.testing.assert_array_equal(inc.r_cliques(), g.r_cliques())
+    np.testing.assert_array_equal(inc.s_degree(), g.s_degree())
+    kap = g.peel()
+    tau, iters = inc.snd()
+    np.testing.assert_array_equal(tau, kap)
+    assert iters == g.snd()[2]  # SND is deterministic: same number of updating passes
+    for notify in (True, False):
+        t2, it2, ev2 = inc.and_(notify=notify)
+        np.testing.assert_array_equal(t2, kap)
+        assert it2 <= iters
+        assert ev2 >= g.num_r
+    for k in (1, 2, 3):
+        tk, _ = inc.iterate_k("snd", k)
+        np.testing.assert_array_equal(tk, g.snd(max_sweeps=k)[0])
+        ta, _ = inc.iterate_k("and", k)
+        assert (kap <= ta).all() and (ta <= tk).all()
+        tn, _ = inc.iterate_k("and_nn", k)
+        assert (kap <= tn).all() and (tn <= tk).all()
+
+
+def test_toy_traces(nd):
+    rp, col = G.toy_core_graph()
+    inc = nd.build_incidence(rp, col, 1, 2)
+    assert inc.iterate_k("snd", 1)[0].tolist() == [2, 2, 2, 2, 1, 1]
+    assert inc.iterate_k("snd", 2)[0].tolist() == [1, 2, 2, 2, 1, 1]
+    tau, iters = inc.snd()
+    assert tau.tolist() == [1, 2, 2, 2, 1, 1] and iters == 2
+    ch, ev = inc.last_passes()
+    assert ch.tolist() == [2, 1, 0] and ev.tolist() == [6, 6, 6]
+
+
+def test_device_tensors_and_host_arrays_agree(nd):
+    rp, col = CASES["planted800"]
+    for r, s in RS:
+        host = nd.build_incidence(rp, col, r, s)
+        dev = nd.build_incidence(torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda(), r, s)
+        th, _ = host.snd()
+        td, _ = dev.snd()
+        assert isinstance(td, torch.Tensor) and td.is_cuda
+        np.testing.assert_array_equal(th, td.cpu().numpy())
+        ta, _, _ = dev.and_()
+        np.testing.assert_array_equal(th, ta.cpu().numpy())
+        np.testing.assert_array_equal(host.r_cliques(), dev.r_cliques().cpu().numpy())
+
+
+def test_resume_from_saved_tau(nd):
+    rp, col = CASES["rmat10"]
+    inc = nd.build_incidence(rp, col, 2, 3)
+    full, _ = inc.snd()
+    mid, _ = inc.iterate_k("snd", 2)
+    resumed, _ = inc.iterate_k("snd", 1 << 20, tau=mid)
+    np.testing.assert_array_equal(resumed, full)
+    resumed_and, _ = inc.iterate_k("and", 1 << 20, tau=mid)
+    np.testing.assert_array_equal(resumed_and, full)
+
+
+def test_iteration_cap_reports_not_converged(nd):
+    rp, col = CASES["rmat10"]
+    inc = nd.build_incidence(rp, col, 2, 3)
+    _, iters = inc.snd()
+    assert iters >= 2
+    with pytest.raises(nd.NDError) as e:
+        inc.snd(max_iters=1)
+    assert e.value.status == nd.ND_E_NOT_CONVERGED
+
+
+def test_empty_and_degenerate_graphs(nd):
+    empty_rp, empty_col = np.zeros(1, np.int64), np.zeros(0, np.int32)
+    for r, s in RS:
+        inc = nd.build_incidence(empty_rp, empty_col, r, s)
+        assert inc.num_r == 0
+        assert inc.snd()[0].size == 0
+    iso = np.zeros(9, np.int64)
+    inc = nd.build_incidence(iso, empty_col, 1, 2)
+    assert inc.snd()[0].tolist() == [0] * 8
+    assert inc.and_()[0].tolist() == [0] * 8
+    rp, col = G.cycle_graph(9)
+    assert (nd.build_incidence(rp, col, 1, 2).snd()[0] == 2).all()
+    assert (nd.build_incidence(rp, col, 2, 3).snd()[0] == 0).all()
+    assert nd.build_incidence(rp, col, 3, 4).num_r == 0
+    rp, col = G.star_graph(3000)  # hub of degree 3000: streaming bucket
+    assert (nd.build_incidence(rp, col, 1, 2).and_()[0] == 1).all()
+
+
+def test_closed_form_cliques(nd):
+    for k in (4, 9, 33, 70):
+        rp, col = G.complete_graph(k)
+        for r, s in RS:
+            inc = nd.build_incidence(rp, col, r, s)
+            assert (inc.snd()[0] == k - r).all()
+            assert (inc.and_()[0] == k - r).all()
+
+
+@pytest.mark.parametrize("bad", ["unsorted", "asymmetric", "selfloop", "range", "rowptr"])
+def test_malformed_graph_rejected(nd, bad):
+    rp, col = G.toy_core_graph()
+    rp = rp.copy()
+    col = col.copy()
+    if bad == "unsorted":
+        col[2], col[3] = col[3], col[2]
+    elif bad == "asymmetric":
+        col[0] = 2                  # a lists c, but c does not list a
+    elif bad == "selfloop":
+        col[0] = 0
+    elif bad == "range":
+        col[0] = 99
+    elif bad == "rowptr":
+        rp[3] = 100
+    with pytest.raises(nd.NDError) as e:
+        nd.build_incidence(rp, col, 1, 2)
+    assert e.value.status == nd.ND_E_INVAL
+
+
+def test_classic_truss_device(nd):
+    k = torch.tensor([0, 3, 7], dtype=torch.int32, device="cuda")
+    assert nd.truss_classic(k).cpu().tolist() == [2, 5, 9]
