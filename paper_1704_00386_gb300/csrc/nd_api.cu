@@ -153,7 +153,7 @@ void nd_free(nd_incidence* h) {
     cudaStream_t st = 0;
     cudaDeviceSynchronize();  // no kernel of any stream may still use the buffers
     void* ptrs[] = {h->nlow, h->up_start, h->eid, h->e_u, h->e_v, h->tri_ptr, h->tri_w, h->tri_e,
-                    h->perm, h->tau[0], h->tau[1], h->front[0], h->front[1], h->counters};
+                    h->items, h->tau[0], h->tau[1], h->front[0], h->front[1], h->counters};
     for (void* p : ptrs) nd_release(p, st);
     if (!h->inc_aliases_graph) {
         nd_release(h->inc_ptr, st);

@@ -271,7 +271,7 @@ __global__ void k_triangle_k4(int64_t T, const int64_t* __restrict__ rp, const i
 
 // ---- degree buckets --------------------------------------------------------
 __device__ __forceinline__ int bucket_of(int64_t d) {
-    return d == 0 ? -1 : (d <= 8 ? 0 : (d <= 64 ? 1 : (d <= 1024 ? 2 : 3)));
+    return d == 0 ? -1 : (d <= 8 ? 0 : (d <= 64 ? 1 : (d <= 2048 ? 2 : 3)));
 }
 
 __global__ void k_bucket_flags(int64_t N, const int64_t* __restrict__ inc_ptr, int b,
@@ -290,11 +290,17 @@ __global__ void k_bucket_flags(int64_t N, const int64_t* __restrict__ inc_ptr, i
 }
 
 __global__ void k_bucket_scatter(int64_t N, const int64_t* __restrict__ inc_ptr, int b,
-                                 const int64_t* __restrict__ pos, uint32_t* __restrict__ perm) {
+                                 const int64_t* __restrict__ pos, nd_item* __restrict__ items) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         int64_t d = inc_ptr[i + 1] - inc_ptr[i];
-        if (bucket_of(d) == b) perm[pos[i]] = (uint32_t)i;
+        if (bucket_of(d) == b) {
+            nd_item it;
+            it.jb = inc_ptr[i];
+            it.R = (uint32_t)i;
+            it.d = (uint32_t)d;
+            items[pos[i]] = it;
+        }
     }
 }
 
@@ -481,7 +487,7 @@ nd_status nd_build_buckets(nd_incidence* h, cudaStream_t st) {
     ND_CUDA(cudaMallocAsync((void**)&flags, sizeof(int64_t) * (N + 1), st));
     ND_CUDA(cudaMallocAsync((void**)&sums, sizeof(unsigned long long) * ND_NB, st));
     ND_CUDA(cudaMemsetAsync(sums, 0, sizeof(unsigned long long) * ND_NB, st));
-    ND_TRY(nd_alloc((void**)&h->perm, sizeof(uint32_t) * (N > 0 ? N : 1), st, h));
+    ND_TRY(nd_alloc((void**)&h->items, sizeof(nd_item) * (N > 0 ? N : 1), st, h));
     int blocks = nd_blocks_for(N, kThreads, grid_cap(h) * 2);
     int64_t lo = 0;
     for (int b = 0; b < ND_NB; ++b) {
@@ -496,7 +502,7 @@ nd_status nd_build_buckets(nd_incidence* h, cudaStream_t st) {
         ND_TRY(nd_scan_i64(flags, N, st));
         {
             nd_prof_scope ps("buckets", st);
-            k_bucket_scatter<<<blocks, kThreads, 0, st>>>(N, h->inc_ptr, b, flags, h->perm + lo);
+            k_bucket_scatter<<<blocks, kThreads, 0, st>>>(N, h->inc_ptr, b, flags, h->items + lo);
             ND_CUDA(cudaGetLastError());
         }
         int64_t cnt = 0;

@@ -1,9 +1,10 @@
 // The iterated h-index update (Def. 4) as GPU passes: SND (Alg. 2) and AND
 // with or without notification (Alg. 3, Section 4.3).
 //
-// One pass = one launch.  Blocks are dispatched to four degree buckets of
-// r-cliques (d_s in [1,8], [9,64], [65,1024], >1024) and each r-clique is
-// evaluated by a group of 4, 8, 32 or 32 lanes.  A group:
+// One pass = one launch of a persistent grid.  R-cliques are grouped into
+// four degree buckets (d_s in [1,8], [9,64], [65,2048], >2048) and evaluated
+// by a group of 4 or 8 lanes, a warp, or a whole CTA; blocks take chunks of
+// r-cliques from a per-pass counter, longest rows first.  A group of 4 or 8:
 //   1. streams the r-clique's incidence row (coalesced, q ids per s-clique),
 //      gathers the q tau values of each s-clique and keeps
 //      rho = min(...) in registers (Def. 4, step 1);
@@ -13,6 +14,11 @@
 //   3. otherwise H lies in [count, tau(R)) and is found by binary search on
 //      h over the register-resident rho values, testing
 //      #{rho >= h} >= h (Def. 3).  No histogram, no sort.
+// A warp or a CTA (longer rows) streams its row instead: one pass counts
+// rho >= tau(R); if that fails, each further pass bins rho into at most 256
+// shared-memory counters over the interval [lo, hi) that holds H, and the
+// suffix sums at the bin edges cut the interval 256-fold, so H is exact after
+// 1-2 more streaming passes whatever the row length.
 // The paper's linear-time hashmap h-index (Section 4.4) is replaced by this
 // tau-bounded count; both compute Def. 3 exactly.
 //
@@ -33,17 +39,24 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Work of one pass is a list of chunks, longest rows first (bucket 3, 2, 1,
+// 0); persistent blocks take chunks from a per-pass counter until none are
+// left, so every SM stays busy to the end of the pass.
+// processing order of the buckets, and r-cliques per chunk by bucket
+__host__ __device__ constexpr int bucket_at(int o) { return ND_NB - 1 - o; }
+__host__ __device__ constexpr int chunk_r(int b) { return b == 0 ? 256 : (b == 1 ? 64 : (b == 2 ? 8 : 1)); }
+
 struct SweepParams {
     const int64_t* __restrict__ inc_ptr;
     const uint32_t* __restrict__ inc;
     const int32_t* tin;   // SND: tau of the previous pass; AND: same array as tout
     int32_t* tout;
-    const uint32_t* __restrict__ perm;
-    int64_t lo[ND_NB], hi[ND_NB];
-    int blk[ND_NB + 1];
+    const nd_item* __restrict__ items;
+    int64_t lo[ND_NB], hi[ND_NB];  // bucket ranges in items
+    int64_t chunk_end[ND_NB];      // cumulative chunk counts, in processing order
     const uint32_t* cur;  // AND + notification: frontier read in this pass
     uint32_t* next;       // and the frontier written for the next pass
-    unsigned long long* ctr;         // this pass: [0] changed, [1] evaluated
+    unsigned long long* ctr;         // this pass: [0] changed, [1] evaluated, [2] next chunk
     const unsigned long long* prev;  // previous pass (null on the first)
 };
 
@@ -56,114 +69,303 @@ __device__ __forceinline__ int32_t ld_tau(const int32_t* p) {
 // rho(S,R) for the s-clique at incidence j: min of the other r-cliques' tau
 template <int Q, bool RO>
 __device__ __forceinline__ int32_t rho_at(const uint32_t* __restrict__ inc, const int32_t* tau, int64_t j) {
+    // the incidence ids are read once per pass: evict-first, so that they do
+    // not push the gathered tau values out of L2
     if (Q == 1) {
-        return ld_tau<RO>(tau + __ldg(inc + j));
+        return ld_tau<RO>(tau + __ldcs(inc + j));
     } else if (Q == 2) {
-        uint2 id = __ldg(reinterpret_cast<const uint2*>(inc) + j);
+        uint2 id = __ldcs(reinterpret_cast<const uint2*>(inc) + j);
         return min(ld_tau<RO>(tau + id.x), ld_tau<RO>(tau + id.y));
     } else {
         const uint32_t* p = inc + 3 * j;
-        uint32_t a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+        uint32_t a = __ldcs(p), b = __ldcs(p + 1), c = __ldcs(p + 2);
         return min(min(ld_tau<RO>(tau + a), ld_tau<RO>(tau + b)), ld_tau<RO>(tau + c));
     }
 }
 
-// H({rho_j}) clipped to t, for one r-clique, by a group of G lanes.
-// C > 0: the row fits in G*C registers.  C == 0: stream the row per probe.
+// H({rho_j}) clipped to t, for one r-clique, by a group of G lanes; the row
+// (at most G*C <= 1024 incidences, so t <= 1024) is held in registers as
+// min(rho, t), two 16-bit values per register.
 template <int Q, int G, int C, bool RO>
 __device__ __forceinline__ int32_t group_hindex(const cg::thread_block_tile<G>& g,
                                                 const uint32_t* __restrict__ inc, const int32_t* tau,
                                                 int64_t jb, int64_t je, int32_t t) {
+    static_assert(C % 2 == 0, "values are packed in pairs");
     const int lane = g.thread_rank();
     if (t <= 0) return 0;
-    if (C > 0) {
-        int32_t rho[C > 0 ? C : 1];
-        int cnt = 0;
+    uint32_t pk[C / 2];
+    int cnt = 0;
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-            int64_t j = jb + lane + (int64_t)c * G;
-            rho[c] = (j < je) ? rho_at<Q, RO>(inc, tau, j) : -1;
-            cnt += (rho[c] >= t);
-        }
-        cnt = cg::reduce(g, cnt, cg::plus<int>());
-        if (cnt >= t) return t;
-        int lo = cnt, hi = t;  // #{rho >= lo} >= lo holds; at hi it fails
-        while (hi - lo > 1) {
-            int mid = lo + ((hi - lo) >> 1);
-            int c2 = 0;
-#pragma unroll
-            for (int c = 0; c < C; ++c) c2 += (rho[c] >= mid);
-            c2 = cg::reduce(g, c2, cg::plus<int>());
-            if (c2 >= mid) lo = mid; else hi = mid;
-        }
-        return lo;
-    } else {
-        int cnt = 0;
-        for (int64_t j = jb + lane; j < je; j += G) cnt += (rho_at<Q, RO>(inc, tau, j) >= t);
-        cnt = cg::reduce(g, cnt, cg::plus<int>());
-        if (cnt >= t) return t;
-        int lo = cnt, hi = t;
-        while (hi - lo > 1) {
-            int mid = lo + ((hi - lo) >> 1);
-            int c2 = 0;
-            for (int64_t j = jb + lane; j < je; j += G) c2 += (rho_at<Q, RO>(inc, tau, j) >= mid);
-            c2 = cg::reduce(g, c2, cg::plus<int>());
-            if (c2 >= mid) lo = mid; else hi = mid;
-        }
-        return lo;
+    for (int c = 0; c < C; c += 2) {
+        const int64_t j0 = jb + lane + (int64_t)c * G, j1 = j0 + G;
+        const int32_t r0 = (j0 < je) ? rho_at<Q, RO>(inc, tau, j0) : 0;
+        const int32_t r1 = (j1 < je) ? rho_at<Q, RO>(inc, tau, j1) : 0;
+        cnt += (r0 >= t) + (r1 >= t);
+        pk[c / 2] = (uint32_t)min(r0, t) | ((uint32_t)min(r1, t) << 16);
     }
+    cnt = cg::reduce(g, cnt, cg::plus<int>());
+    if (cnt >= t) return t;
+    int lo = cnt, hi = t;  // #{rho >= lo} >= lo holds; at hi it fails
+    while (hi - lo > 1) {
+        const int mid = lo + ((hi - lo) >> 1);
+        int c2 = 0;
+#pragma unroll
+        for (int c = 0; c < C / 2; ++c)
+            c2 += ((int)(pk[c] & 0xffffu) >= mid) + ((int)(pk[c] >> 16) >= mid);
+        c2 = cg::reduce(g, c2, cg::plus<int>());
+        if (c2 >= mid) lo = mid; else hi = mid;
+    }
+    return lo;
 }
 
-template <int Q, int G, int C, bool AND, bool NOTIFY>
-__device__ __forceinline__ void run_bucket(const SweepParams& P, int b, unsigned long long& changed,
-                                           unsigned long long& evals) {
-    auto g = cg::tiled_partition<G>(cg::this_thread_block());
-    const int64_t groups_per_block = kThreads / G;
-    const int64_t nblk = P.blk[b + 1] - P.blk[b];
-    const int64_t gid = (int64_t)(blockIdx.x - P.blk[b]) * groups_per_block + g.meta_group_rank();
-    const int64_t stride = nblk * groups_per_block;
-    const int lane = g.thread_rank();
-    for (int64_t i = P.lo[b] + gid; i < P.hi[b]; i += stride) {
-        const uint32_t R = __ldg(P.perm + i);
-        if (AND && NOTIFY) {
-            if (!((__ldg(P.cur + (R >> 5)) >> (R & 31)) & 1u)) continue;
-        }
-        const int32_t t = ld_tau<!AND>(P.tin + R);
-        const int64_t jb = __ldg(P.inc_ptr + R), je = __ldg(P.inc_ptr + R + 1);
-        const int32_t h = group_hindex<Q, G, C, !AND>(g, P.inc, P.tin, jb, je, t);
-        if (lane == 0) {
-            evals++;
-            if (h != t) changed++;
-            if (!AND || h != t) P.tout[R] = h;
-        }
-        if (AND && NOTIFY && h != t) {
-            // notify every neighbour whose tau could still depend on R: h <= tau(R')
-            for (int64_t j = jb + lane; j < je; j += G) {
+// Bin selection of one k-ary search step, by one full warp.  bins[0..255]
+// count rho in [lo + b*width, lo + (b+1)*width), bins[256] counts rho >= hi.
+// #{rho >= lo + b*width} is the suffix sum from b; the answer H lies in
+// [k, next edge) for the largest bin edge k whose suffix is >= k (bin 0
+// always qualifies, because #{rho >= lo} >= lo).  Each lane owns 8 bins.
+__device__ __forceinline__ void select_bin(const unsigned* bins, int lo, int hi, int width, int nb,
+                                           int* nlo, int* nhi) {
+    const int lane = threadIdx.x & 31;
+    unsigned own = 0;
 #pragma unroll
-                for (int k = 0; k < Q; ++k) {
-                    uint32_t Rp = __ldg(P.inc + Q * j + k);
-                    if (h <= ld_tau<false>(P.tin + Rp)) {
-                        uint32_t bit = 1u << (Rp & 31);
-                        uint32_t* w = P.next + (Rp >> 5);
-                        if (!(*(volatile uint32_t*)w & bit)) atomicOr(w, bit);
-                    }
-                }
+    for (int k = 0; k < 8; ++k) own += bins[8 * lane + k];
+    unsigned incl = own;  // inclusive prefix over lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+    int64_t run = (int64_t)bins[256] + (total - incl);  // rho at or above this lane's bins
+    int best = -1;
+#pragma unroll
+    for (int k = 7; k >= 0; --k) {
+        const int b = 8 * lane + k;
+        run += bins[b];
+        if (best < 0 && run >= (int64_t)lo + (int64_t)b * width) best = b;
+    }
+    const unsigned hit = __ballot_sync(0xffffffffu, best >= 0);
+    const int b = __shfl_sync(0xffffffffu, best, 31 - __clz(hit));
+    *nlo = lo + b * width;
+    const int e = (b + 1 < nb) ? lo + (b + 1) * width : hi;
+    *nhi = e < hi ? e : hi;
+}
+
+__device__ __forceinline__ void kary_bin(unsigned* bins, int32_t r, int lo, int hi, int width) {
+    if (r >= lo) atomicAdd(&bins[r >= hi ? 256 : (r - lo) / width], 1u);
+}
+
+// H({rho_j}) clipped to t by one warp, streaming the row: one pass counts
+// rho >= t; if that fails, k-ary search with 256 shared-memory bins per
+// streaming pass (at most 2 passes for t <= 65536).
+template <int Q, bool RO>
+__device__ __forceinline__ int32_t warp_hindex(const uint32_t* __restrict__ inc, const int32_t* tau,
+                                               int64_t jb, int64_t je, int32_t t, unsigned* bins) {
+    const int lane = threadIdx.x & 31;
+    if (t <= 0) return 0;
+    int cnt = 0;
+#pragma unroll 4
+    for (int64_t j = jb + lane; j < je; j += 32) cnt += (rho_at<Q, RO>(inc, tau, j) >= t);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (cnt >= t) return t;
+    int lo = cnt, hi = t;
+    while (hi - lo > 1) {
+        const int span = hi - lo;
+        const int nb = span < 256 ? span : 256;
+        const int width = (span + nb - 1) / nb;
+        for (int i = lane; i <= 256; i += 32) bins[i] = 0;
+        __syncwarp();
+        for (int64_t j = jb + lane; j < je; j += 32) kary_bin(bins, rho_at<Q, RO>(inc, tau, j), lo, hi, width);
+        __syncwarp();
+        int nlo, nhi;
+        select_bin(bins, lo, hi, width, nb, &nlo, &nhi);
+        lo = nlo;
+        hi = nhi;
+        __syncwarp();
+    }
+    return lo;
+}
+
+// The same by the whole CTA (the longest rows); warp 0 selects the bin.
+template <int Q, bool RO>
+__device__ __forceinline__ int32_t cta_hindex(const uint32_t* __restrict__ inc, const int32_t* tau,
+                                              int64_t jb, int64_t je, int32_t t,
+                                              unsigned* bins /* 257 */, int* bounds /* 2 */) {
+    if (t <= 0) return 0;
+    int cnt = 0;
+#pragma unroll 4
+    for (int64_t j = jb + threadIdx.x; j < je; j += kThreads) cnt += (rho_at<Q, RO>(inc, tau, j) >= t);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0) bins[threadIdx.x >> 5] = (unsigned)cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tot = 0;
+        for (int w = 0; w < kThreads / 32; ++w) tot += bins[w];
+        bounds[0] = (int)tot;
+    }
+    __syncthreads();
+    cnt = bounds[0];
+    __syncthreads();
+    if (cnt >= t) return t;
+    int lo = cnt, hi = t;  // #{rho >= lo} >= lo holds; at hi it fails
+    while (hi - lo > 1) {
+        const int span = hi - lo;
+        const int nb = span < 256 ? span : 256;
+        const int width = (span + nb - 1) / nb;
+        for (int i = threadIdx.x; i <= 256; i += kThreads) bins[i] = 0;
+        __syncthreads();
+        for (int64_t j = jb + threadIdx.x; j < je; j += kThreads)
+            kary_bin(bins, rho_at<Q, RO>(inc, tau, j), lo, hi, width);
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int nlo, nhi;
+            select_bin(bins, lo, hi, width, nb, &nlo, &nhi);
+            if (threadIdx.x == 0) { bounds[0] = nlo; bounds[1] = nhi; }
+        }
+        __syncthreads();
+        lo = bounds[0];
+        hi = bounds[1];
+        __syncthreads();
+    }
+    return lo;
+}
+
+// notify every neighbour whose tau could still depend on R (Alg. 3, orange
+// lines): set its next-frontier bit if h <= tau(R')
+template <int Q>
+__device__ __forceinline__ void notify_row(const SweepParams& P, int64_t jb, int64_t je, int32_t h,
+                                           int first, int step) {
+    for (int64_t j = jb + first; j < je; j += step) {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            uint32_t Rp = __ldg(P.inc + Q * j + k);
+            if (h <= ld_tau<false>(P.tin + Rp)) {
+                uint32_t bit = 1u << (Rp & 31);
+                uint32_t* w = P.next + (Rp >> 5);
+                if (!(*(volatile uint32_t*)w & bit)) atomicOr(w, bit);
             }
         }
     }
 }
 
+__device__ __forceinline__ nd_item load_item(const nd_item* __restrict__ items, int64_t i) {
+    longlong2 v = __ldg(reinterpret_cast<const longlong2*>(items) + i);
+    nd_item it;
+    it.jb = v.x;
+    it.R = (uint32_t)(unsigned long long)v.y;
+    it.d = (uint32_t)((unsigned long long)v.y >> 32);
+    return it;
+}
+
+// work items [first, last): one r-clique per group of G lanes; the next
+// item is loaded before the current one is evaluated
+template <int Q, int G, int C, bool AND, bool NOTIFY>
+__device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, int64_t last,
+                                           unsigned long long& changed, unsigned long long& evals) {
+    auto g = cg::tiled_partition<G>(cg::this_thread_block());
+    const int lane = g.thread_rank();
+    int64_t i = first + g.meta_group_rank();
+    nd_item it;
+    if (i < last) it = load_item(P.items, i);
+    while (i < last) {
+        const int64_t ni = i + kThreads / G;
+        nd_item nx;
+        if (ni < last) nx = load_item(P.items, ni);
+        const uint32_t R = it.R;
+        const int64_t jb = it.jb, je = it.jb + it.d;
+        bool active = true;
+        if (AND && NOTIFY) active = (__ldg(P.cur + (R >> 5)) >> (R & 31)) & 1u;
+        if (active) {
+            const int32_t t = ld_tau<!AND>(P.tin + R);
+            const int32_t h = group_hindex<Q, G, C, !AND>(g, P.inc, P.tin, jb, je, t);
+            if (lane == 0) {
+                evals++;
+                if (h != t) changed++;
+                if (!AND || h != t) P.tout[R] = h;
+            }
+            if (AND && NOTIFY && h != t) notify_row<Q>(P, jb, je, h, lane, G);
+        }
+        it = nx;
+        i = ni;
+    }
+}
+
+// work items [first, last): one r-clique per warp, streamed (rows of 65-2048)
 template <int Q, bool AND, bool NOTIFY>
-__global__ void __launch_bounds__(kThreads) k_pass(SweepParams P) {
+__device__ __forceinline__ void run_warps(const SweepParams& P, int64_t first, int64_t last,
+                                          unsigned* bins, unsigned long long& changed,
+                                          unsigned long long& evals) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = first + (threadIdx.x >> 5); i < last; i += kThreads / 32) {
+        const nd_item it = load_item(P.items, i);
+        const uint32_t R = it.R;
+        if (AND && NOTIFY) {
+            if (!((__ldg(P.cur + (R >> 5)) >> (R & 31)) & 1u)) continue;
+        }
+        const int32_t t = ld_tau<!AND>(P.tin + R);
+        const int64_t jb = it.jb, je = it.jb + it.d;
+        const int32_t h = warp_hindex<Q, !AND>(P.inc, P.tin, jb, je, t, bins);
+        if (lane == 0) {
+            evals++;
+            if (h != t) changed++;
+            if (!AND || h != t) P.tout[R] = h;
+        }
+        if (AND && NOTIFY && h != t) notify_row<Q>(P, jb, je, h, lane, 32);
+    }
+}
+
+// one r-clique per CTA (rows longer than 2048 incidences)
+template <int Q, bool AND, bool NOTIFY>
+__device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int64_t last,
+                                        unsigned* bins, int* bounds, unsigned long long& changed,
+                                        unsigned long long& evals) {
+    for (int64_t i = first; i < last; ++i) {
+        const nd_item it = load_item(P.items, i);
+        const uint32_t R = it.R;
+        if (AND && NOTIFY) {
+            if (!((__ldg(P.cur + (R >> 5)) >> (R & 31)) & 1u)) continue;
+        }
+        const int32_t t = ld_tau<!AND>(P.tin + R);
+        const int64_t jb = it.jb, je = it.jb + it.d;
+        const int32_t h = cta_hindex<Q, !AND>(P.inc, P.tin, jb, je, t, bins, bounds);
+        if (threadIdx.x == 0) {
+            evals++;
+            if (h != t) changed++;
+            if (!AND || h != t) P.tout[R] = h;
+        }
+        if (AND && NOTIFY && h != t) notify_row<Q>(P, jb, je, h, threadIdx.x, kThreads);
+        __syncthreads();
+    }
+}
+
+template <int Q, bool AND, bool NOTIFY>
+__global__ void __launch_bounds__(kThreads, 5) k_pass(SweepParams P) {
     if (P.prev != nullptr && *(volatile const unsigned long long*)P.prev == 0ull) return;  // converged
+    __shared__ unsigned bins[kThreads / 32][260];  // k-ary search bins, one set per warp
+    __shared__ int bounds[2];
+    __shared__ unsigned long long s_chunk;
     unsigned long long changed = 0, evals = 0;
-    int b = 0;
-    while (b < ND_NB - 1 && (int)blockIdx.x >= P.blk[b + 1]) ++b;
-    switch (b) {
-        case 0: run_bucket<Q, 4, 2, AND, NOTIFY>(P, 0, changed, evals); break;
-        case 1: run_bucket<Q, 8, 8, AND, NOTIFY>(P, 1, changed, evals); break;
-        case 2: run_bucket<Q, 32, 32, AND, NOTIFY>(P, 2, changed, evals); break;
-        default: run_bucket<Q, 32, 0, AND, NOTIFY>(P, 3, changed, evals); break;
+    const int64_t total = P.chunk_end[ND_NB - 1];
+    for (;;) {
+        if (threadIdx.x == 0) s_chunk = atomicAdd(P.ctr + 2, 1ull);
+        __syncthreads();
+        const int64_t c = (int64_t)s_chunk;
+        __syncthreads();
+        if (c >= total) break;
+        int o = 0;
+        while (c >= P.chunk_end[o]) ++o;
+        const int b = bucket_at(o);
+        const int64_t k = c - (o ? P.chunk_end[o - 1] : 0);
+        const int64_t first = P.lo[b] + k * chunk_r(b);
+        const int64_t last = min(first + (int64_t)chunk_r(b), P.hi[b]);
+        switch (b) {
+            case 0: run_groups<Q, 4, 2, AND, NOTIFY>(P, first, last, changed, evals); break;
+            case 1: run_groups<Q, 8, 8, AND, NOTIFY>(P, first, last, changed, evals); break;
+            case 2: run_warps<Q, AND, NOTIFY>(P, first, last, bins[threadIdx.x >> 5], changed, evals); break;
+            default: run_cta<Q, AND, NOTIFY>(P, first, last, bins[0], bounds, changed, evals); break;
+        }
     }
     __shared__ unsigned long long s_ch[kThreads / 32], s_ev[kThreads / 32];
 #pragma unroll
@@ -216,27 +418,27 @@ pass_fn pick(int q, int mode) {
     return mode == ND_SND ? k_pass<3, false, false> : (mode == ND_AND ? k_pass<3, true, true> : k_pass<3, true, false>);
 }
 
-// blocks per bucket in proportion to its incidences (its share of the work),
-// never more than its groups need, at least one if it is non-empty
-void plan_blocks(const nd_incidence* h, SweepParams& P) {
-    const int group[ND_NB] = {4, 8, 32, 32};
-    const int64_t total_blocks = (int64_t)(h->sm_count > 0 ? h->sm_count : 152) * 8;
-    int64_t tot_inc = 0;
-    for (int b = 0; b < ND_NB; ++b) tot_inc += h->bucket_inc[b];
-    int acc = 0;
-    for (int b = 0; b < ND_NB; ++b) {
-        P.blk[b] = acc;
-        int64_t cnt = h->bucket_lo[b + 1] - h->bucket_lo[b];
+// chunk table of a pass (see bucket_at / chunk_r)
+void plan_chunks(const nd_incidence* h, SweepParams& P) {
+    int64_t acc = 0;
+    for (int o = 0; o < ND_NB; ++o) {
+        const int b = bucket_at(o);
         P.lo[b] = h->bucket_lo[b];
         P.hi[b] = h->bucket_lo[b + 1];
-        if (cnt == 0) continue;
-        int64_t need = (cnt * group[b] + kThreads - 1) / kThreads;
-        int64_t share = tot_inc > 0 ? (total_blocks * h->bucket_inc[b] + tot_inc - 1) / tot_inc : 1;
-        int64_t nb = share < need ? share : need;
-        if (nb < 1) nb = 1;
-        acc += (int)nb;
+        acc += (P.hi[b] - P.lo[b] + chunk_r(b) - 1) / chunk_r(b);
+        P.chunk_end[o] = acc;
     }
-    P.blk[ND_NB] = acc;
+}
+
+// persistent grid: as many blocks as fit on the GPU at once (never more than
+// there are chunks)
+int pass_grid(const nd_incidence* h, const void* fn, int64_t chunks) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    int64_t g = (int64_t)per_sm * (h->sm_count > 0 ? h->sm_count : 152);
+    if (g > chunks) g = chunks;
+    return (int)(g < 1 ? 1 : g);
 }
 
 nd_status ensure_state(nd_incidence* h, bool and_mode, cudaStream_t st) {
@@ -249,8 +451,8 @@ nd_status ensure_state(nd_incidence* h, bool and_mode, cudaStream_t st) {
         ND_TRY(nd_alloc((void**)&h->front[1], sizeof(uint32_t) * words, st, h));
     }
     if (!h->counters) {
-        ND_TRY(nd_alloc((void**)&h->counters, sizeof(unsigned long long) * 2 * ND_RING, st, h));
-        ND_CUDA(cudaMallocHost((void**)&h->h_counters, sizeof(unsigned long long) * 2 * ND_RING));
+        ND_TRY(nd_alloc((void**)&h->counters, sizeof(unsigned long long) * ND_SLOT * ND_RING, st, h));
+        ND_CUDA(cudaMallocHost((void**)&h->h_counters, sizeof(unsigned long long) * ND_SLOT * ND_RING));
     }
     return ND_OK;
 }
@@ -317,10 +519,10 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
     SweepParams P;
     P.inc_ptr = h->inc_ptr;
     P.inc = h->inc;
-    P.perm = h->perm;
-    plan_blocks(h, P);
-    const int grid = P.blk[ND_NB];
+    P.items = h->items;
+    plan_chunks(h, P);
     pass_fn fn = pick(h->q, mode);
+    const int grid = P.chunk_end[ND_NB - 1] > 0 ? pass_grid(h, (const void*)fn, P.chunk_end[ND_NB - 1]) : 0;
     const int kBatch = 16;
     int32_t pass = 0;
     bool done = false;
@@ -331,11 +533,11 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
         int nb = kBatch;
         if (nb > max_passes - pass) nb = max_passes - pass;
         if (slot0 + nb > ND_RING) nb = ND_RING - slot0;
-        ND_CUDA(cudaMemsetAsync(h->counters + 2 * slot0, 0, sizeof(unsigned long long) * 2 * nb, st));
+        ND_CUDA(cudaMemsetAsync(h->counters + ND_SLOT * slot0, 0, sizeof(unsigned long long) * ND_SLOT * nb, st));
         for (int k = 0; k < nb; ++k, ++pass) {
             const int slot = pass % ND_RING;
-            P.ctr = h->counters + 2 * slot;
-            P.prev = (pass == 0) ? nullptr : h->counters + 2 * ((pass - 1) % ND_RING);
+            P.ctr = h->counters + ND_SLOT * slot;
+            P.prev = (pass == 0) ? nullptr : h->counters + ND_SLOT * ((pass - 1) % ND_RING);
             if (and_mode) {
                 P.tin = h->tau[0];
                 P.tout = h->tau[0];
@@ -356,13 +558,13 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
                 ND_CUDA(cudaGetLastError());
             }
         }
-        ND_CUDA(cudaMemcpyAsync(h->h_counters + 2 * slot0, h->counters + 2 * slot0,
-                                sizeof(unsigned long long) * 2 * nb, cudaMemcpyDeviceToHost, st));
+        ND_CUDA(cudaMemcpyAsync(h->h_counters + ND_SLOT * slot0, h->counters + ND_SLOT * slot0,
+                                sizeof(unsigned long long) * ND_SLOT * nb, cudaMemcpyDeviceToHost, st));
         ND_CUDA(cudaStreamSynchronize(st));
         for (int k = 0; k < nb; ++k) {
             const int32_t p = start + k;
-            unsigned long long ch = h->h_counters[2 * (slot0 + k)];
-            unsigned long long ev = h->h_counters[2 * (slot0 + k) + 1];
+            unsigned long long ch = h->h_counters[ND_SLOT * (slot0 + k)];
+            unsigned long long ev = h->h_counters[ND_SLOT * (slot0 + k) + 1];
             // r-cliques with d_s = 0 are never launched: tau = H(empty) = 0 = d_s.
             // They count as evaluated in every SND / AND-nn pass and in the first
             // AND pass, as in the paper's sequential loops.

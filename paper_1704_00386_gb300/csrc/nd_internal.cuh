@@ -44,7 +44,15 @@ struct nd_prof_scope {
 // degree buckets for the h-index sweeps: r-cliques are grouped by d_s so that
 // each group of lanes that evaluates one r-clique is sized to its work.
 // ----------------------------------------------------------------------------
-enum { ND_NB = 4 };  // bucket 0: d_s in [1,8], 1: [9,64], 2: [65,1024], 3: > 1024
+enum { ND_NB = 4 };  // bucket 0: d_s in [1,8], 1: [9,64], 2: [65,2048], 3: > 2048
+
+// one unit of h-index work: the r-clique and its incidence row, so that a
+// pass reaches the row with one 16-byte load instead of two dependent ones
+struct __align__(16) nd_item {
+    int64_t jb;   // first incidence of the row
+    uint32_t R;   // r-clique id
+    uint32_t d;   // row length d_s(R)
+};
 
 struct nd_incidence {
     int r = 0, s = 0, q = 0;
@@ -67,7 +75,7 @@ struct nd_incidence {
     uint32_t* inc = nullptr;       // [num_inc*q]
     bool inc_aliases_graph = false;  // r = 1: inc_ptr/inc are rp/col
     // degree-bucketed processing order
-    uint32_t* perm = nullptr;      // [num_r_active]
+    nd_item* items = nullptr;      // [num_r - num_zero], bucket by bucket
     int64_t bucket_lo[ND_NB + 1] = {0, 0, 0, 0, 0};
     int64_t bucket_inc[ND_NB] = {0, 0, 0, 0};
     int64_t num_zero = 0;          // r-cliques with d_s = 0 (kappa = 0, never updated)
@@ -80,7 +88,7 @@ struct nd_incidence {
     int64_t bytes = 0;
 };
 
-enum { ND_RING = 256 };  // per-pass counter slots (2 x u64 each)
+enum { ND_RING = 256, ND_SLOT = 4 };  // per-pass counter slots of ND_SLOT u64 each
 
 // device memory helpers (stream-ordered)
 nd_status nd_alloc(void** p, size_t bytes, cudaStream_t st, nd_incidence* owner);

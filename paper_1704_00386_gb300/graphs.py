@@ -29,7 +29,7 @@ import numpy as np
 __all__ = [
     "to_csr", "chung_lu", "rmat", "erdos_renyi", "plant_cliques",
     "graph_from_edges", "toy_core_graph", "complete_graph", "cycle_graph",
-    "star_graph", "disjoint_union", "workload",
+    "star_graph", "disjoint_union", "hub_graph", "workload",
 ]
 
 
@@ -184,6 +184,28 @@ def plant_cliques(n: int, count: int, size_lo: int, size_hi: int, seed: int):
     if not src:
         return np.zeros(0, np.int64), np.zeros(0, np.int64)
     return np.concatenate(src), np.concatenate(dst)
+
+
+def hub_graph(n: int = 3000, hubs: int = 6, seed: int = 107):
+    """Sparse Erdos-Renyi background (mean degree 6), `hubs` mutually adjacent
+    hub vertices each joined to 70-85% of the others, and 5 planted cliques
+    of size 20-40: long incidence rows for every (r,s) (hub degrees, hub-hub
+    edge triangles and hub-triple 4-cliques all exceed 1024)."""
+    rng = _rng(seed)
+    i, j = erdos_renyi(n, 6.0 / (n - 1), seed=seed)
+    src, dst = [i], [j]
+    for h in range(hubs):
+        k = int(rng.integers(int(0.7 * n), int(0.85 * n)))
+        nb = rng.choice(np.arange(hubs, n), size=k, replace=False)
+        src.append(np.full(k, h, dtype=np.int64))
+        dst.append(nb.astype(np.int64))
+    a, b = np.triu_indices(hubs, 1)
+    src.append(a)
+    dst.append(b)
+    s2, d2 = plant_cliques(n, 5, 20, 40, seed=seed + 1)
+    src.append(s2)
+    dst.append(d2)
+    return to_csr(n, np.concatenate(src), np.concatenate(dst))
 
 
 def graph_from_edges(n: int, edges):

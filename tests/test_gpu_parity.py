@@ -40,8 +40,8 @@ def _cases():
     s1, d1 = G.chung_lu(800, 2.1, 6.0, seed=104)
     s2, d2 = G.plant_cliques(800, 6, 8, 22, seed=105)
     out["planted800"] = G.to_csr(800, np.concatenate([s1, s2]), np.concatenate([d1, d2]))
-    # an edge in > 1024 triangles (streaming bucket for (2,3)) and a vertex of
-    # degree > 1024 (streaming bucket for (1,2)), with a clique among the fan
+    # an edge in > 1024 triangles (CTA bucket for (2,3)) and a vertex of
+    # degree > 1024 (CTA bucket for (1,2)), with a clique among the fan
     fan = 1300
     src = [0] * fan + [1] * fan + [0]
     dst = list(range(2, fan + 2)) + list(range(2, fan + 2)) + [1]
@@ -49,6 +49,7 @@ def _cases():
     src += list(a + 2)
     dst += list(b + 2)
     out["book1300"] = G.to_csr(fan + 2, src, dst)
+    out["hubs3000"] = G.hub_graph(3000, 6, seed=107)
     return out
 
 
@@ -151,7 +152,7 @@ def test_empty_and_degenerate_graphs(nd):
     assert (nd.build_incidence(rp, col, 1, 2).snd()[0] == 2).all()
     assert (nd.build_incidence(rp, col, 2, 3).snd()[0] == 0).all()
     assert nd.build_incidence(rp, col, 3, 4).num_r == 0
-    rp, col = G.star_graph(3000)  # hub of degree 3000: streaming bucket
+    rp, col = G.star_graph(3000)  # hub of degree 3000: CTA bucket
     assert (nd.build_incidence(rp, col, 1, 2).and_()[0] == 1).all()
 
 
