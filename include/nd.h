@@ -83,6 +83,19 @@ typedef struct nd_incidence nd_incidence; /* opaque; owned by the library */
  * On success *out owns device memory until nd_free(*out). */
 nd_status nd_build_incidence(const nd_csr* g, int r, int s, void* stream, nd_incidence** out);
 
+/* Batched build: the incidence of many independent graphs at once, as the
+ * incidence of their disjoint union (graph i's vertex ids are shifted past
+ * those of graphs 0..i-1).  kappa_s of a disjoint union is kappa_s of each
+ * part (Lemma 1: a subgraph around R only gains from R's own component), so
+ * every later call (nd_snd, nd_and, nd_iterate_k, ...) processes all graphs
+ * in one launch per pass.  In the union's canonical order the r-cliques of
+ * graph i are the contiguous slice [r_offsets[i], r_offsets[i+1]), in graph
+ * i's own canonical order.  graphs[count]: all on the host or all on the
+ * device; each must be a valid CSR whose ids stay inside its own range.
+ * r_offsets: host int64[count+1] (may be NULL).  Synchronises `stream`. */
+nd_status nd_build_incidence_batch(const nd_csr* graphs, int count, int r, int s, void* stream,
+                                   nd_incidence** out, int64_t* r_offsets);
+
 /* Sizes of a built incidence: number of r-clique (N_R), number of
  * (R, S) incidences (M = sum of d_s), and q.  Any output may be NULL. */
 nd_status nd_incidence_info(const nd_incidence* inc, int64_t* num_r, int64_t* num_incidences,

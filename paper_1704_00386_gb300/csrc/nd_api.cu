@@ -110,20 +110,24 @@ static void keep_pool(int dev) {
     });
 }
 
-static nd_status host_wait(cudaStream_t st) {
-    // bounded wait: poll the stream instead of blocking forever
+// bounded wait: poll the stream instead of blocking forever
+nd_status nd_wait(cudaStream_t st, double seconds) {
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
         cudaError_t e = cudaStreamQuery(st);
         if (e == cudaSuccess) return ND_OK;
         if (e != cudaErrorNotReady) return nd_cuda_fail(e, "cudaStreamQuery", __FILE__, __LINE__);
-        if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(3600)) {
-            nd_set_error("stream did not finish within 3600 s");
+        if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > seconds) {
+            char buf[96];
+            snprintf(buf, sizeof(buf), "stream did not finish within %.0f s", seconds);
+            nd_set_error(buf);
             return ND_E_TIMEOUT;
         }
         std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
 }
+
+static nd_status host_wait(cudaStream_t st) { return nd_wait(st, 1800.0); }
 
 // ---------------------------------------------------------------------------
 // C ABI
@@ -150,8 +154,10 @@ const char* nd_last_error(void) { return g_last_error.c_str(); }
 
 void nd_free(nd_incidence* h) {
     if (!h) return;
-    cudaStream_t st = 0;
-    cudaDeviceSynchronize();  // no kernel of any stream may still use the buffers
+    // every call on a handle is ordered on its stream; wait for the latest
+    // one, then release on it (other streams keep running)
+    cudaStream_t st = h->last_stream;
+    cudaStreamSynchronize(st);
     void* ptrs[] = {h->nlow, h->up_start, h->eid, h->e_u, h->e_v, h->tri_ptr, h->tri_w, h->tri_e,
                     h->items, h->tau[0], h->tau[1], h->front[0], h->front[1], h->counters};
     for (void* p : ptrs) nd_release(p, st);
@@ -166,22 +172,28 @@ void nd_free(nd_incidence* h) {
     delete h;
 }
 
-nd_status nd_build_incidence(const nd_csr* g, int r, int s, void* stream, nd_incidence** out) {
-    if (!out) { nd_set_error("out is NULL"); return ND_E_INVAL; }
-    *out = nullptr;
-    if (!g) { nd_set_error("graph is NULL"); return ND_E_INVAL; }
+static nd_status check_rs(int r, int s) {
     if (r < 1 || s <= r) { nd_set_error("need 1 <= r < s"); return ND_E_INVAL; }
     if (!((r == 1 && s == 2) || (r == 2 && s == 3) || (r == 3 && s == 4))) {
         nd_set_error("only (1,2), (2,3) and (3,4) are implemented");
         return ND_E_UNSUPPORTED_RS;
     }
+    return ND_OK;
+}
+
+static nd_status check_csr(const nd_csr* g) {
+    if (!g) { nd_set_error("graph is NULL"); return ND_E_INVAL; }
     if (g->n < 0 || g->nnz < 0 || !g->row_ptr || (g->nnz > 0 && !g->col)) {
         nd_set_error("bad CSR header");
         return ND_E_INVAL;
     }
     if (g->n >= INT32_MAX) { nd_set_error("more than 2^31-1 vertices"); return ND_E_TOO_LARGE; }
     if (g->n == 0 && g->nnz != 0) { nd_set_error("nnz > 0 with no vertices"); return ND_E_INVAL; }
-    cudaStream_t st = (cudaStream_t)stream;
+    return ND_OK;
+}
+
+// the whole build on one (validated-header) CSR
+static nd_status build_common(const nd_csr* g, int r, int s, cudaStream_t st, nd_incidence** out) {
     int dev = 0;
     ND_CUDA(cudaGetDevice(&dev));
     keep_pool(dev);
@@ -192,6 +204,7 @@ nd_status nd_build_incidence(const nd_csr* g, int r, int s, void* stream, nd_inc
     h->q = (r == 1) ? 1 : (r == 2 ? 2 : 3);
     if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         h->sm_count = 152;
+    h->last_stream = st;
     nd_status rc = nd_build_graph(h, g, st);
     if (rc == ND_OK && r >= 2) rc = nd_build_edges(h, st);
     if (rc == ND_OK) {
@@ -221,6 +234,78 @@ nd_status nd_build_incidence(const nd_csr* g, int r, int s, void* stream, nd_inc
     return ND_OK;
 }
 
+nd_status nd_build_incidence(const nd_csr* g, int r, int s, void* stream, nd_incidence** out) {
+    if (!out) { nd_set_error("out is NULL"); return ND_E_INVAL; }
+    *out = nullptr;
+    ND_TRY(check_rs(r, s));
+    ND_TRY(check_csr(g));
+    return build_common(g, r, s, (cudaStream_t)stream, out);
+}
+
+nd_status nd_build_incidence_batch(const nd_csr* graphs, int count, int r, int s, void* stream,
+                                   nd_incidence** out, int64_t* r_offsets) {
+    if (!out) { nd_set_error("out is NULL"); return ND_E_INVAL; }
+    *out = nullptr;
+    ND_TRY(check_rs(r, s));
+    if (count < 0 || (count > 0 && !graphs)) { nd_set_error("bad graph list"); return ND_E_INVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int64_t> voff(count + 1, 0);
+    std::vector<nd_union_part> parts(count);
+    int64_t n = 0, nnz = 0;
+    const int on_device = count > 0 ? graphs[0].on_device : 1;
+    for (int i = 0; i < count; ++i) {
+        ND_TRY(check_csr(&graphs[i]));
+        if (graphs[i].on_device != on_device) {
+            nd_set_error("all graphs of a batch must be on the host or all on the device");
+            return ND_E_INVAL;
+        }
+        parts[i] = {graphs[i].row_ptr, graphs[i].col, graphs[i].n, graphs[i].nnz, n, nnz};
+        n += graphs[i].n;
+        nnz += graphs[i].nnz;
+        voff[i + 1] = n;
+    }
+    if (n >= INT32_MAX) { nd_set_error("batch has more than 2^31-1 vertices"); return ND_E_TOO_LARGE; }
+    int64_t* urp = nullptr;
+    int32_t* ucol = nullptr;
+    nd_status rc = ND_OK;
+    if (on_device) {
+        ND_CUDA(cudaMallocAsync((void**)&urp, sizeof(int64_t) * (n + 1), st));
+        ND_CUDA(cudaMallocAsync((void**)&ucol, sizeof(int32_t) * (nnz > 0 ? nnz : 1), st));
+        rc = nd_union_device(parts.data(), count, n, nnz, urp, ucol, st);
+    } else {
+        // host graphs: assemble the union on the host and copy it once
+        std::vector<int64_t> hrp(n + 1);
+        std::vector<int32_t> hcol(nnz > 0 ? nnz : 1);
+        for (int i = 0; i < count && rc == ND_OK; ++i) {
+            const nd_union_part& p = parts[i];
+            if (p.rp[0] != 0 || p.rp[p.n] != p.nnz) { nd_set_error("a graph of the batch has an invalid row_ptr"); rc = ND_E_INVAL; break; }
+            for (int64_t u = 0; u < p.n; ++u) hrp[p.n_off + u] = p.nnz_off + p.rp[u];
+            for (int64_t j = 0; j < p.nnz; ++j) {
+                const int32_t v = p.col[j];
+                if (v < 0 || v >= p.n) { nd_set_error("a graph of the batch has a neighbour id outside its own vertex range"); rc = ND_E_INVAL; break; }
+                hcol[p.nnz_off + j] = v + (int32_t)p.n_off;
+            }
+        }
+        hrp[n] = nnz;
+        if (rc == ND_OK) {
+            nd_csr u{n, nnz, hrp.data(), hcol.data(), 0};
+            rc = build_common(&u, r, s, st, out);
+        }
+        if (rc == ND_OK && r_offsets) rc = nd_batch_offsets(*out, voff.data(), count, r_offsets, st);
+        if (rc != ND_OK && *out) { nd_free(*out); *out = nullptr; }
+        return rc;
+    }
+    if (rc == ND_OK) {
+        nd_csr u{n, nnz, urp, ucol, 1};
+        rc = build_common(&u, r, s, st, out);
+    }
+    cudaFreeAsync(urp, st);
+    cudaFreeAsync(ucol, st);
+    if (rc == ND_OK && r_offsets) rc = nd_batch_offsets(*out, voff.data(), count, r_offsets, st);
+    if (rc != ND_OK && *out) { nd_free(*out); *out = nullptr; }
+    return rc;
+}
+
 nd_status nd_incidence_info(const nd_incidence* h, int64_t* num_r, int64_t* num_inc, int* q) {
     if (!h) { nd_set_error("handle is NULL"); return ND_E_INVAL; }
     if (num_r) *num_r = h->num_r;
@@ -248,6 +333,7 @@ static nd_status deliver(const int32_t* src_dev, int64_t count, int32_t* dst, in
 nd_status nd_r_cliques(const nd_incidence* h, int32_t* out, int on_device, void* stream) {
     if (!h || (!out && h->num_r > 0)) { nd_set_error("NULL argument"); return ND_E_INVAL; }
     cudaStream_t st = (cudaStream_t)stream;
+    const_cast<nd_incidence*>(h)->last_stream = st;
     const int64_t count = h->num_r * h->r;
     if (count == 0) return ND_OK;
     if (on_device) return nd_write_r_cliques(h, out, st);
@@ -262,6 +348,7 @@ nd_status nd_r_cliques(const nd_incidence* h, int32_t* out, int on_device, void*
 nd_status nd_s_degree(const nd_incidence* h, int32_t* out, int on_device, void* stream) {
     if (!h || (!out && h->num_r > 0)) { nd_set_error("NULL argument"); return ND_E_INVAL; }
     cudaStream_t st = (cudaStream_t)stream;
+    const_cast<nd_incidence*>(h)->last_stream = st;
     if (h->num_r == 0) return ND_OK;
     if (on_device) return nd_init_tau(const_cast<nd_incidence*>(h), out, st);
     int32_t* tmp = nullptr;
@@ -280,6 +367,7 @@ static nd_status run_and_deliver(nd_incidence* h, int mode, int32_t max_passes, 
     if (!tau_out && h->num_r > 0) { nd_set_error("tau_out is NULL"); return ND_E_INVAL; }
     if (mode != ND_SND && mode != ND_AND && mode != ND_AND_NN) { nd_set_error("bad mode"); return ND_E_INVAL; }
     if (max_passes < 0) { nd_set_error("negative iteration cap"); return ND_E_INVAL; }
+    h->last_stream = st;
     const int32_t* tin_dev = nullptr;
     int32_t* staged = nullptr;
     if (tau_in && h->num_r > 0) {

@@ -323,6 +323,34 @@ __global__ void k_r_cliques(int r, int64_t N, const int32_t* __restrict__ e_u,
     }
 }
 
+// ---- batches: the disjoint union of many graphs (one block per graph) ------
+// Vertex ids of graph i are shifted by n_off; its CSR slots by nnz_off.  A
+// graph whose offsets or ids fall outside its own range is reported.
+__global__ void k_union(const nd_union_part* __restrict__ parts, int count, int64_t* __restrict__ urp,
+                        int32_t* __restrict__ ucol, int* __restrict__ err) {
+    for (int gi = blockIdx.x; gi < count; gi += gridDim.x) {
+        const nd_union_part p = parts[gi];
+        if (threadIdx.x == 0 && (p.rp[0] != 0 || p.rp[p.n] != p.nnz)) atomicOr(err, 1);
+        for (int64_t i = threadIdx.x; i < p.n; i += blockDim.x) {
+            int64_t x = p.rp[i];
+            if (x < 0 || x > p.nnz) { atomicOr(err, 1); x = 0; }
+            urp[p.n_off + i] = p.nnz_off + x;
+        }
+        for (int64_t j = threadIdx.x; j < p.nnz; j += blockDim.x) {
+            int32_t v = p.col[j];
+            if (v < 0 || v >= p.n) { atomicOr(err, 2); v = 0; }
+            ucol[p.nnz_off + j] = v + (int32_t)p.n_off;
+        }
+    }
+}
+
+// out[i] = src[idx[i]] for the r-clique offsets of a batch
+__global__ void k_gather_i64(const int64_t* __restrict__ src, const int64_t* __restrict__ idx, int count,
+                             int64_t* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        out[i] = src[idx[i]];
+}
+
 int grid_cap(const nd_incidence* h) { return (h->sm_count > 0 ? h->sm_count : 152) * 8; }
 
 nd_status read_flag(int* dflag, int* hval, cudaStream_t st) {
@@ -526,5 +554,62 @@ nd_status nd_write_r_cliques(const nd_incidence* h, int32_t* out_dev, cudaStream
     nd_prof_scope ps("r_cliques", st);
     k_r_cliques<<<blocks, kThreads, 0, st>>>(h->r, h->num_r, h->e_u, h->e_v, h->tri_w, h->tri_e, out_dev);
     ND_CUDA(cudaGetLastError());
+    return ND_OK;
+}
+
+nd_status nd_union_device(const nd_union_part* parts_host, int count, int64_t n, int64_t nnz, int64_t* urp,
+                          int32_t* ucol, cudaStream_t st) {
+    nd_union_part* dparts = nullptr;
+    int* derr = nullptr;
+    ND_CUDA(cudaMallocAsync((void**)&dparts, sizeof(nd_union_part) * (count > 0 ? count : 1), st));
+    ND_CUDA(cudaMallocAsync((void**)&derr, sizeof(int), st));
+    ND_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
+    ND_CUDA(cudaMemcpyAsync(dparts, parts_host, sizeof(nd_union_part) * count, cudaMemcpyHostToDevice, st));
+    if (count > 0) {
+        nd_prof_scope ps("union", st);
+        k_union<<<count < 152 * 16 ? count : 152 * 16, kThreads, 0, st>>>(dparts, count, urp, ucol, derr);
+        ND_CUDA(cudaGetLastError());
+    }
+    ND_CUDA(cudaMemcpyAsync(urp + n, &nnz, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    int herr = 0;
+    nd_status s = read_flag(derr, &herr, st);
+    cudaFreeAsync(dparts, st);
+    cudaFreeAsync(derr, st);
+    if (s != ND_OK) return s;
+    if (herr) {
+        nd_set_error(herr & 1 ? "a graph of the batch has an invalid row_ptr"
+                              : "a graph of the batch has a neighbour id outside its own vertex range");
+        return ND_E_INVAL;
+    }
+    return ND_OK;
+}
+
+// r-clique offsets of the graphs of a batch: the union's canonical order
+// lists graph 0's r-cliques first, then graph 1's, and so on.
+nd_status nd_batch_offsets(const nd_incidence* h, const int64_t* vertex_off /* count+1, host */, int count,
+                           int64_t* r_off /* count+1, host */, cudaStream_t st) {
+    if (h->r == 1) {
+        for (int i = 0; i <= count; ++i) r_off[i] = vertex_off[i];
+        return ND_OK;
+    }
+    int64_t* didx = nullptr;
+    int64_t* dout = nullptr;
+    ND_CUDA(cudaMallocAsync((void**)&didx, sizeof(int64_t) * (count + 1), st));
+    ND_CUDA(cudaMallocAsync((void**)&dout, sizeof(int64_t) * (count + 1), st));
+    ND_CUDA(cudaMemcpyAsync(didx, vertex_off, sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
+    // edges owned by vertices below the graph's first vertex
+    k_gather_i64<<<nd_blocks_for(count + 1, kThreads, 64), kThreads, 0, st>>>(h->up_start, didx, count + 1, dout);
+    ND_CUDA(cudaGetLastError());
+    if (h->r == 3) {
+        // triangles owned by those edges
+        k_gather_i64<<<nd_blocks_for(count + 1, kThreads, 64), kThreads, 0, st>>>(h->tri_ptr, dout, count + 1, didx);
+        ND_CUDA(cudaGetLastError());
+        ND_CUDA(cudaMemcpyAsync(r_off, didx, sizeof(int64_t) * (count + 1), cudaMemcpyDeviceToHost, st));
+    } else {
+        ND_CUDA(cudaMemcpyAsync(r_off, dout, sizeof(int64_t) * (count + 1), cudaMemcpyDeviceToHost, st));
+    }
+    ND_CUDA(cudaStreamSynchronize(st));
+    cudaFreeAsync(didx, st);
+    cudaFreeAsync(dout, st);
     return ND_OK;
 }

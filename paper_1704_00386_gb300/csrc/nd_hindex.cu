@@ -524,6 +524,13 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
     pass_fn fn = pick(h->q, mode);
     const int grid = P.chunk_end[ND_NB - 1] > 0 ? pass_grid(h, (const void*)fn, P.chunk_end[ND_NB - 1]) : 0;
     const int kBatch = 16;
+    // Thm. 3 / Lemma 2: SND settles within the number of degree levels, at
+    // most N_R, and AND never needs more passes than SND.  A run longer than
+    // N_R + 1 passes (including the pass that detects convergence) can only
+    // be a fault, and is reported instead of looping on.
+    const int64_t bound = N + 1;
+    bool over_bound = false;
+    if ((int64_t)max_passes > bound) { max_passes = (int32_t)bound; over_bound = true; }
     int32_t pass = 0;
     bool done = false;
     int32_t last_written = 0;  // SND: index of the buffer holding the newest tau
@@ -560,7 +567,7 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
         }
         ND_CUDA(cudaMemcpyAsync(h->h_counters + ND_SLOT * slot0, h->counters + ND_SLOT * slot0,
                                 sizeof(unsigned long long) * ND_SLOT * nb, cudaMemcpyDeviceToHost, st));
-        ND_CUDA(cudaStreamSynchronize(st));
+        ND_TRY(nd_wait(st, 600.0));
         for (int k = 0; k < nb; ++k) {
             const int32_t p = start + k;
             unsigned long long ch = h->h_counters[ND_SLOT * (slot0 + k)];
@@ -579,5 +586,9 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
     }
     *converged = done;
     *tau_result = and_mode ? h->tau[0] : h->tau[last_written];
+    if (!done && over_bound) {
+        nd_set_error("no convergence within N_R + 1 passes, the bound of Thm. 3 (internal fault)");
+        return ND_E_NOT_CONVERGED;
+    }
     return ND_OK;
 }

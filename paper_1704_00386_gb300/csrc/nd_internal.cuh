@@ -86,9 +86,13 @@ struct nd_incidence {
     unsigned long long* h_counters = nullptr;  // pinned host mirror
     std::vector<int64_t> last_changed, last_evals;
     int64_t bytes = 0;
+    cudaStream_t last_stream = 0;  // stream of the latest call on this handle
 };
 
 enum { ND_RING = 256, ND_SLOT = 4 };  // per-pass counter slots of ND_SLOT u64 each
+
+// wait for a stream with a time limit (ND_E_TIMEOUT past it)
+nd_status nd_wait(cudaStream_t st, double seconds);
 
 // device memory helpers (stream-ordered)
 nd_status nd_alloc(void** p, size_t bytes, cudaStream_t st, nd_incidence* owner);
@@ -106,6 +110,17 @@ nd_status nd_build_triangles(nd_incidence* h, cudaStream_t st);
 nd_status nd_build_k4_incidence(nd_incidence* h, cudaStream_t st);
 nd_status nd_build_buckets(nd_incidence* h, cudaStream_t st);
 nd_status nd_write_r_cliques(const nd_incidence* h, int32_t* out_dev, cudaStream_t st);
+
+// batches (disjoint unions of independent graphs)
+struct nd_union_part {
+    const int64_t* rp;
+    const int32_t* col;
+    int64_t n, nnz, n_off, nnz_off;
+};
+nd_status nd_union_device(const nd_union_part* parts_host, int count, int64_t n, int64_t nnz, int64_t* urp,
+                          int32_t* ucol, cudaStream_t st);
+nd_status nd_batch_offsets(const nd_incidence* h, const int64_t* vertex_off, int count, int64_t* r_off,
+                           cudaStream_t st);
 
 // iteration (nd_hindex.cu)
 nd_status nd_init_tau(nd_incidence* h, int32_t* tau, cudaStream_t st);

@@ -29,7 +29,7 @@ import numpy as np
 __all__ = [
     "to_csr", "chung_lu", "rmat", "erdos_renyi", "plant_cliques",
     "graph_from_edges", "toy_core_graph", "complete_graph", "cycle_graph",
-    "star_graph", "disjoint_union", "hub_graph", "workload",
+    "star_graph", "disjoint_union", "hub_graph", "batch_graphs", "workload",
 ]
 
 
@@ -206,6 +206,34 @@ def hub_graph(n: int = 3000, hubs: int = 6, seed: int = 107):
     src.append(s2)
     dst.append(d2)
     return to_csr(n, np.concatenate(src), np.concatenate(dst))
+
+
+def batch_graphs(count: int, seed: int = 4, n_lo: int = 100, n_hi: int = 50000):
+    """Independent graphs for batched runs: n uniform in [n_lo, n_hi]; each
+    graph is, with probability 1/3 each, Erdos-Renyi with mean degree 8,
+    Chung-Lu with exponent 2.2 and mean degree 8, or R-MAT with edge factor 8
+    at scale ceil(log2 n) keeping only endpoints below n.  Graph i uses seed
+    seed*1_000_003 + i.  Returns a list of (row_ptr, col, family)."""
+    out = []
+    rng = _rng(seed)
+    ns = rng.integers(n_lo, n_hi + 1, size=count)
+    fam = rng.integers(0, 3, size=count)
+    for i in range(count):
+        n = int(ns[i])
+        sd = seed * 1_000_003 + i
+        if fam[i] == 0:
+            a, b = erdos_renyi(n, 8.0 / (n - 1), seed=sd)
+            name = "er"
+        elif fam[i] == 1:
+            a, b = chung_lu(n, 2.2, 8.0, seed=sd)
+            name = "chunglu"
+        else:
+            scale = max(1, int(np.ceil(np.log2(n))))
+            _, a, b = rmat(scale, 8, seed=sd, n_limit=n)
+            name = "rmat"
+        rp, col = to_csr(n, a, b)
+        out.append((rp, col, name))
+    return out
 
 
 def graph_from_edges(n: int, edges):

@@ -24,7 +24,7 @@ ND_OK, ND_E_INVAL, ND_E_UNSUPPORTED_RS, ND_E_NOMEM, ND_E_CUDA, ND_E_NOT_CONVERGE
 ND_SND, ND_AND, ND_AND_NN = 0, 1, 2
 MODES = {"snd": ND_SND, "and": ND_AND, "and_nn": ND_AND_NN}
 
-SYMBOLS = ["nd_build_incidence", "nd_incidence_info", "nd_r_cliques", "nd_s_degree", "nd_snd",
+SYMBOLS = ["nd_build_incidence", "nd_build_incidence_batch", "nd_incidence_info", "nd_r_cliques", "nd_s_degree", "nd_snd",
            "nd_and", "nd_iterate_k", "nd_truss_classic", "nd_prof_enable", "nd_prof_read",
            "nd_last_passes", "nd_incidence_bytes", "nd_free", "nd_strerror", "nd_last_error",
            "nd_abi_version"]
@@ -63,6 +63,7 @@ def load(build_if_missing: bool = True):
         i32, i64, vp, ci = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int
         P = ctypes.POINTER
         lib.nd_build_incidence.argtypes = [P(_CSR), ci, ci, vp, P(vp)]
+        lib.nd_build_incidence_batch.argtypes = [P(_CSR), ci, ci, ci, vp, P(vp), vp]
         lib.nd_incidence_info.argtypes = [vp, P(i64), P(i64), P(ci)]
         lib.nd_r_cliques.argtypes = [vp, vp, ci, vp]
         lib.nd_s_degree.argtypes = [vp, vp, ci, vp]
@@ -242,6 +243,41 @@ def build_incidence(row_ptr, col, r: int, s: int, stream=None) -> Incidence:
     _check(lib.nd_build_incidence(ctypes.byref(csr), int(r), int(s), _stream_ptr(stream),
                                   ctypes.byref(h)), "nd_build_incidence")
     return Incidence(h, r, s, on_device, device, stream)
+
+
+def build_incidence_batch(graphs, r: int, s: int, stream=None):
+    """nd_build_incidence_batch on a list of (row_ptr, col) pairs, all numpy or
+    all CUDA tensors.  Returns (Incidence of the disjoint union, r_offsets):
+    graph i's results are the slice [r_offsets[i], r_offsets[i+1])."""
+    lib = load()
+    count = len(graphs)
+    arr = (_CSR * max(count, 1))()
+    keep = []
+    on_device = None
+    device = None
+    for i, (rp, col) in enumerate(graphs):
+        dev = _is_torch(rp)
+        if on_device is None:
+            on_device = dev
+        if dev != on_device or dev != _is_torch(col):
+            raise ValueError("all graphs must be host arrays or all CUDA tensors")
+        if dev:
+            import torch
+            rp = rp.to(torch.int64).contiguous()
+            col = col.to(torch.int32).contiguous()
+            device = rp.device
+            n, nnz = rp.numel() - 1, col.numel()
+        else:
+            rp = np.ascontiguousarray(rp, dtype=np.int64)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+            n, nnz = rp.size - 1, col.size
+        keep.append((rp, col))
+        arr[i] = _CSR(n, nnz, _ptr(rp).value, _ptr(col).value if nnz else None, int(dev))
+    offs = np.zeros(count + 1, dtype=np.int64)
+    h = ctypes.c_void_p()
+    _check(lib.nd_build_incidence_batch(arr, count, int(r), int(s), _stream_ptr(stream), ctypes.byref(h),
+                                        _ptr(offs)), "nd_build_incidence_batch")
+    return Incidence(h, r, s, bool(on_device), device, stream), offs
 
 
 def truss_classic(kappa3, stream=None):

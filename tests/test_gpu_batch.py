@@ -1,0 +1,76 @@
+"""Batched decomposition (nd_build_incidence_batch): many independent graphs
+as one disjoint union, processed in one launch per pass.  Each graph's slice
+must equal the CPU oracle's kappa and the single-graph CUDA result, bit for
+bit, for every (r,s) and both host and device inputs."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1704_00386_gb300 import graphs as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_00386_gb300 import nd as _nd
+    _nd.load()
+    return _nd
+
+
+def _batch():
+    gs = [(rp, col) for rp, col, _ in G.batch_graphs(24, seed=9, n_lo=30, n_hi=1500)]
+    gs.insert(3, (np.zeros(1, np.int64), np.zeros(0, np.int32)))       # empty graph
+    gs.insert(7, (np.zeros(5, np.int64), np.zeros(0, np.int32)))       # isolated vertices
+    gs.append(G.complete_graph(9))
+    return gs
+
+
+BATCH = _batch()
+
+
+@pytest.mark.parametrize("rs", [(1, 2), (2, 3), (3, 4)])
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_batch_slices_match_oracle(nd, rs, where):
+    gs = BATCH
+    if where == "device":
+        gs = [(torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda()) for rp, col in BATCH]
+    inc, offs = nd.build_incidence_batch(gs, *rs)
+    assert offs[0] == 0 and offs[-1] == inc.num_r
+    tau, _ = inc.snd()
+    ta, _, _ = inc.and_(notify=True)
+    tau = tau.cpu().numpy() if where == "device" else tau
+    ta = ta.cpu().numpy() if where == "device" else ta
+    np.testing.assert_array_equal(tau, ta)
+    for i, (rp, col) in enumerate(BATCH):
+        want = oracle.decompose(rp, col, *rs)
+        got = tau[offs[i]:offs[i + 1]]
+        np.testing.assert_array_equal(got, want, err_msg=f"graph {i}")
+
+
+def test_batch_equals_single_graph_runs(nd):
+    inc, offs = nd.build_incidence_batch(BATCH, 2, 3)
+    tuples = inc.r_cliques()
+    tau, _ = inc.snd()
+    base = 0
+    for i, (rp, col) in enumerate(BATCH):
+        single = nd.build_incidence(rp, col, 2, 3)
+        assert single.num_r == offs[i + 1] - offs[i]
+        if single.num_r:
+            np.testing.assert_array_equal(single.snd()[0], tau[offs[i]:offs[i + 1]])
+            np.testing.assert_array_equal(single.r_cliques() + base, tuples[offs[i]:offs[i + 1]])
+        base += rp.size - 1
+
+
+def test_batch_rejects_bad_part(nd):
+    rp, col = G.toy_core_graph()
+    bad = col.copy()
+    bad[0] = 40                      # outside its own graph's vertex range
+    with pytest.raises(nd.NDError) as e:
+        nd.build_incidence_batch([G.complete_graph(5), (rp, bad)], 1, 2)
+    assert e.value.status == nd.ND_E_INVAL
+    with pytest.raises(ValueError):
+        nd.build_incidence_batch([(rp, col), (torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda())], 1, 2)
