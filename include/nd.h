@@ -158,6 +158,31 @@ nd_status nd_last_passes(const nd_incidence* inc, int64_t* changed, int64_t* eva
 /* Device memory held by the handle, in bytes. */
 nd_status nd_incidence_bytes(const nd_incidence* inc, int64_t* bytes);
 
+/* Core numbers ((r,s) = (1,2)) by SND without allocating anything.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they call in -- their process has
+ * handed all GPU memory to another allocator up front, or they cannot
+ * afford the implicit device synchronisation of cudaMalloc / cudaFree.
+ * It returns the same core numbers and pass count as nd_build_incidence
+ * (g, 1, 2) + nd_snd, computed straight from a device CSR.
+ *   row_ptr[n+1], col[nnz]: device pointers to a simple, sorted, symmetric
+ *     CSR (rows and ids are bounds-checked: a violation gives ND_E_INVAL;
+ *     sortedness and symmetry are not checked).
+ *   core_out[n]: device pointer; receives the core numbers.
+ *   n must be at most 1,048,576; larger graphs get ND_E_TOO_LARGE.
+ *   max_iters caps the passes as for nd_snd; *iters_out (may be NULL) =
+ *   passes that changed a value.  Synchronises `stream`.
+ * Scratch: one file-scope device array of 4 MiB + 1 KiB (a previous-pass
+ * tau buffer and per-pass counters).  Every GPU that loads the library
+ * holds it until the process exits.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents (the counters are cleared at the start of each
+ * call): calls that overlap on the GPU -- on two streams, or from two
+ * threads -- race and must be serialised by the caller. */
+nd_status nd_core_snd_noalloc(const int64_t* row_ptr, const int32_t* col, int64_t n, int64_t nnz,
+                              int32_t* core_out, int32_t max_iters, int32_t* iters_out, void* stream);
+
 void nd_free(nd_incidence* inc);
 const char* nd_strerror(nd_status st);
 const char* nd_last_error(void);

@@ -27,7 +27,7 @@ MODES = {"snd": ND_SND, "and": ND_AND, "and_nn": ND_AND_NN}
 SYMBOLS = ["nd_build_incidence", "nd_build_incidence_batch", "nd_incidence_info", "nd_r_cliques", "nd_s_degree", "nd_snd",
            "nd_and", "nd_iterate_k", "nd_truss_classic", "nd_prof_enable", "nd_prof_read",
            "nd_last_passes", "nd_incidence_bytes", "nd_free", "nd_strerror", "nd_last_error",
-           "nd_abi_version"]
+           "nd_abi_version", "nd_core_snd_noalloc"]
 
 _lock = threading.Lock()
 _lib = None
@@ -75,6 +75,7 @@ def load(build_if_missing: bool = True):
         lib.nd_prof_read.argtypes = [ci, P(ctypes.c_char_p), P(i64), P(ctypes.c_double)]
         lib.nd_last_passes.argtypes = [vp, vp, vp, i32, P(i32)]
         lib.nd_incidence_bytes.argtypes = [vp, P(i64)]
+        lib.nd_core_snd_noalloc.argtypes = [vp, vp, i64, i64, vp, i32, P(i32), vp]
         lib.nd_free.argtypes = [vp]
         lib.nd_free.restype = None
         lib.nd_strerror.argtypes = [ci]
@@ -278,6 +279,21 @@ def build_incidence_batch(graphs, r: int, s: int, stream=None):
     _check(lib.nd_build_incidence_batch(arr, count, int(r), int(s), _stream_ptr(stream), ctypes.byref(h),
                                         _ptr(offs)), "nd_build_incidence_batch")
     return Incidence(h, r, s, bool(on_device), device, stream), offs
+
+
+def core_snd_noalloc(row_ptr, col, out=None, max_iters: int = 1 << 30, stream=None):
+    """nd_core_snd_noalloc: core numbers from a device CSR (CUDA int64 row_ptr,
+    int32 col) with no allocation inside the library; `out` (CUDA int32, n)
+    is allocated here by torch if not given.  Returns (core, passes)."""
+    import torch
+    n = row_ptr.numel() - 1
+    if out is None:
+        out = torch.empty(max(n, 0), dtype=torch.int32, device=row_ptr.device)
+    it = ctypes.c_int32()
+    _check(load().nd_core_snd_noalloc(_ptr(row_ptr), _ptr(col), n, col.numel(), _ptr(out),
+                                      int(max_iters), ctypes.byref(it), _stream_ptr(stream)),
+           "nd_core_snd_noalloc")
+    return out, it.value
 
 
 def truss_classic(kappa3, stream=None):
