@@ -38,6 +38,9 @@ sys.path.insert(0, ROOT)
 METRIC = "r-clique h-index updates/sec to convergence; HBM GB/s vs peak; batched p99"
 UNIT = "updates/s"
 CPU_SAMPLE_SCALE = 14
+# ncu DRAM bytes per incidence of the SND pass (k-truss, q = 2), measured on the
+# current kernel; None until it is measured again after a kernel change.
+NCU_SND_TRAFFIC_PER_INCIDENCE = None
 
 
 def parse():
@@ -49,6 +52,11 @@ def parse():
     p.add_argument("--workload", default="rmat_s20_ef16")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--mode", choices=["single", "batch", "serve"], default="single",
+                   help="single: one graph per step (default); batch: many graphs as one disjoint "
+                        "union vs one graph per launch; serve: Poisson request stream, p50/p99")
+    p.add_argument("--batch-count", type=int, default=4096)
+    p.add_argument("--requests", type=int, default=192)
     return p.parse_args()
 
 
@@ -181,20 +189,29 @@ def run_ours(args, rank, world, local_rank):
 
     w = G.workload(args.workload)
     r, s = w["r"], w["s"]
-    rp_h, col_h = w["row_ptr"], w["col"]
-    rp_d = torch.from_numpy(rp_h).to(dev)
-    col_d = torch.from_numpy(col_h).to(dev)
+    if isinstance(w["row_ptr"], np.ndarray):
+        rp_h, col_h = w["row_ptr"], w["col"]
+        rp_d = torch.from_numpy(rp_h).to(dev)
+        col_d = torch.from_numpy(col_h).to(dev)
+    else:  # generated on the device (large R-MAT)
+        rp_d, col_d = w["row_ptr"].to(dev), w["col"].to(dev)
+        rp_h, col_h = rp_d.cpu().numpy(), col_d.cpu().numpy()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # 512 MB > 129 MB L2
     stream = torch.cuda.current_stream(dev)
 
     def one_step():
         inc = nd.build_incidence(rp_d, col_d, r, s)
         tau_s, it_s = inc.snd()
-        _, ev = inc.last_passes()
+        _, ev, ic = inc.last_passes(with_incidences=True)
         ev_s = int(ev.sum())
+        snd_bytes = [4.0 * inc.q * float(x) for x in ic]
+        snd_rows = [int(x) for x in ev]
         tau_a, it_a, ev_a = inc.and_(notify=True)
+        _, ev2, ic2 = inc.last_passes(with_incidences=True)
         info = dict(num_r=inc.num_r, M=inc.num_incidences, q=inc.q, snd_iters=it_s,
-                    and_iters=it_a, snd_evals=ev_s, and_evals=ev_a)
+                    and_iters=it_a, snd_evals=ev_s, and_evals=ev_a,
+                    snd_inc=[int(x) for x in ic], snd_rows=snd_rows,
+                    and_inc=[int(x) for x in ic2], and_rows=[int(x) for x in ev2])
         inc.free()
         return tau_s, tau_a, info
 
@@ -253,29 +270,40 @@ def run_ours(args, rank, world, local_rank):
         pass
 
     # ----- roofline of the dominant kernel
+    # Algorithmic (compulsory) DRAM bytes of a pass: the incidence ids it
+    # streams (4q B each, counted by the kernel) + 24 B per evaluated r-clique
+    # (8 B row offsets, 4 B work item, 4 B own tau, 4 B tau write, 4 B first
+    # touch of its tau as a gathered value).  The q gathered tau values per
+    # incidence are L2 hits while tau fits in L2, so they are not DRAM bytes.
     info = infos[-1]
     peak, peak_kind = load_peaks()
     top = max(prof.items(), key=lambda kv: kv[1][1])
     name, (launches, ms) = top
     N_R, M, q = info["num_r"], info["M"], info["q"]
-    if name == "snd_pass":
-        eff = sum(i["snd_iters"] + 1 for i in infos)
-        per_launch = 4.0 * q * M + 24.0 * N_R
-        units = f"{q}*4 B ids per incidence x {M} + 24 B x {N_R} r-cliques, per effective pass"
-    elif name in ("tri_fill", "tri_count"):
-        eff = launches
-        per_launch = (8.0 * M if name == "tri_fill" else 0.0) + 4.0 * (rp_h[-1]) + 8.0 * (rp_h.size) + 16.0 * N_R
-        units = "CSR read + edge arrays + 8 B per incidence written (fill)"
+    if name in ("snd_pass", "and_pass"):
+        key = "snd" if name == "snd_pass" else "and"
+        tot_bytes = sum(4.0 * q * sum(i[key + "_inc"]) + 24.0 * sum(i[key + "_rows"]) for i in infos)
+        eff = sum(len(i[key + "_inc"]) for i in infos)
+        per_launch = tot_bytes / max(eff, 1)
+        units = (f"4q B x incidences streamed + 24 B x r-cliques evaluated, summed over the {eff} "
+                 f"effective {key.upper()} passes of the timed steps")
     else:
         eff = launches
-        per_launch = 4.0 * q * M + 24.0 * N_R
-        units = "4q B per incidence + 24 B per r-clique"
+        per_launch = 8.0 * M / max(launches, 1) if name == "tri_fill" else float(rp_h[-1]) * 4.0
+        units = "8 B per incidence written (fill) or CSR bytes read"
     avg_ms = ms / max(eff, 1)
     achieved = per_launch / (avg_ms / 1000.0) / 1e9
+    # DRAM traffic per SND pass from ncu (dram__bytes_read.sum + write.sum) on the R-MAT scale 18
+    # k-truss pass (2.254 GB read + 6.6 MB written per pass for 247,767,033 incidences), scaled by the
+    # incidences of this workload; None for any other kernel or once the kernel has changed.
+    traffic = None
+    if name == "snd_pass" and q == 2 and NCU_SND_TRAFFIC_PER_INCIDENCE is not None:
+        traffic = NCU_SND_TRAFFIC_PER_INCIDENCE * M
     roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "bytes_per_launch": per_launch, "launches_effective": eff, "avg_launch_ms": avg_ms,
-                "units": units}
+                "units": units,
+                "note": "gather-bound: the q tau gathers per incidence run at the L2 request rate"}
 
     # ----- end to end through the public API with host buffers
     e2e = None
@@ -329,6 +357,7 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clk,
             "per_step": {"snd_iters": info["snd_iters"], "and_iters": info["and_iters"],
                          "snd_evals": info["snd_evals"], "and_evals": info["and_evals"],
+                         "and_incidences": sum(info["and_inc"]), "snd_incidences": sum(info["snd_inc"]),
                          "step_ms": step_ms},
             "kernels": phases,
             "parity_vs_oracle_digest": parity, "snd_equals_and": same,
@@ -337,8 +366,153 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+def _evals_of(inc, and_evals):
+    _, ev = inc.last_passes()
+    return int(ev.sum()) + int(and_evals)
+
+
+def run_batch(args):
+    """Config-4 shape: independent graphs (ER / Chung-Lu / R-MAT, n in
+    [100, 50000]), core and truss numbers for each.  One graph per launch
+    against the whole list as one disjoint-union batch, same GPU."""
+    import torch
+    from paper_1704_00386_gb300 import graphs as G
+    from paper_1704_00386_gb300 import nd
+    torch.cuda.set_device(0)
+    nd.load(build_if_missing=False)
+    workers = max(1, min(16, os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    gs = G.batch_graphs(args.batch_count, seed=4, workers=workers)
+    gen_s = time.perf_counter() - t0
+    dev = [(torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda()) for rp, col, _ in gs]
+    stream = torch.cuda.current_stream()
+    out = {"metric": METRIC, "unit": UNIT, "mode": "batch", "graphs": len(gs),
+           "edges": int(sum(int(rp[-1]) // 2 for rp, _, _ in gs)), "generation_s": gen_s, "jobs": {}}
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return res, e0.elapsed_time(e1)
+
+    for r, s in ((1, 2), (2, 3)):
+        def plain():
+            ev, taus = 0, []
+            for rp, col in dev:
+                inc = nd.build_incidence(rp, col, r, s)
+                t, _ = inc.snd()
+                ev_s = _evals_of(inc, 0)
+                ta, _, ev_a = inc.and_(notify=True)
+                ev += ev_s + ev_a
+                taus.append(t)
+                inc.free()
+            return ev, taus
+
+        def batched():
+            inc, offs = nd.build_incidence_batch(dev, r, s)
+            t, _ = inc.snd()
+            ev_s = _evals_of(inc, 0)
+            ta, _, ev_a = inc.and_(notify=True)
+            inc.free()
+            return ev_s + ev_a, (t, offs)
+
+        batched()                                 # warm-up
+        (ev_b, (tb, offs)), ms_b = timed(batched)
+        ms_bs = [ms_b]
+        for _ in range(max(0, args.steps - 1)):
+            _, ms = timed(batched)
+            ms_bs.append(ms)
+        plain()                                   # warm-up
+        (ev_p, taus), ms_p = timed(plain)
+        same = all(torch.equal(taus[i], tb[offs[i]:offs[i + 1]]) for i in range(len(dev)))
+        ms_b = statistics.median(ms_bs)
+        out["jobs"][f"({r},{s})"] = {
+            "batched_ms": ms_b, "batched_updates_per_s": ev_b / (ms_b / 1e3),
+            "batched_graphs_per_s": len(dev) / (ms_b / 1e3),
+            "plain_ms": ms_p, "plain_updates_per_s": ev_p / (ms_p / 1e3),
+            "plain_graphs_per_s": len(dev) / (ms_p / 1e3),
+            "speedup": ms_p / ms_b, "results_identical": bool(same)}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Config-5a shape: a Poisson stream of graphs with 1K-2M edges
+    (log-uniform), family uniform over ER / Chung-Lu / R-MAT, job uniform
+    over (1,2) / (2,3) / (3,4) ((3,4) only where the footprint bound fits the
+    budget, else (2,3)).  Saturated throughput first, then p50/p99 latency at
+    0.5 / 0.7 / 0.9 of it; one-request-at-a-time service as the baseline."""
+    import torch
+    from paper_1704_00386_gb300 import graphs as G
+    from paper_1704_00386_gb300 import nd, serve
+    torch.cuda.set_device(0)
+    nd.load(build_if_missing=False)
+    rng = np.random.Generator(np.random.PCG64(5))
+    budget = 64 << 30
+    edges = np.exp(rng.uniform(np.log(1e3), np.log(2e6), size=args.requests))
+    reqs = []
+    for i, e in enumerate(edges):
+        fam = int(rng.integers(0, 3))
+        n = max(16, int(e * 2 / 8))
+        sd = 5_000_000 + i
+        if fam == 0:
+            a, b = G.erdos_renyi(n, 8.0 / (n - 1), seed=sd)
+        elif fam == 1:
+            a, b = G.chung_lu(n, 2.2, 8.0, seed=sd)
+        else:
+            _, a, b = G.rmat(max(1, int(np.ceil(np.log2(n)))), 8, seed=sd, n_limit=n)
+        rp, col = G.to_csr(n, a, b)
+        r, s_ = [(1, 2), (2, 3), (3, 4)][int(rng.integers(0, 3))]
+        if (r, s_) == (3, 4) and serve.footprint_bytes(rp, col, 3) > budget // 8:
+            r, s_ = 2, 3
+        reqs.append((rp, col, r, s_))
+
+    def run_stream(arrivals, workers, batching=True):
+        srv = serve.Server(budget_bytes=budget, workers=workers, batch_bytes=(1 << 30) if batching else 1,
+                           max_batch=64 if batching else 1)
+        hs = []
+        t0 = time.perf_counter()
+        for (rp, col, r, s_), at in zip(reqs, arrivals):
+            d = t0 + at - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            hs.append(srv.submit(rp, col, r, s_, "and"))
+        srv.close()
+        span = max(h.finish for h in hs) - t0
+        return hs, span
+
+    zero = np.zeros(len(reqs))
+    run_stream(zero[:8], 4)                               # warm-up
+    hs, span = run_stream(zero, 4)
+    sat = len(reqs) / span
+    base_hs, base_span = run_stream(zero, 1, batching=False)
+    alone = {i: h.result for i, h in enumerate(base_hs)}
+    same = all(np.array_equal(h.result, alone[i]) for i, h in enumerate(hs))
+    out = {"metric": METRIC, "mode": "serve", "requests": len(reqs),
+           "edges_total": int(sum(int(rp[-1]) // 2 for rp, _, _, _ in reqs)),
+           "saturated_requests_per_s": sat, "one_at_a_time_requests_per_s": len(reqs) / base_span,
+           "saturated_latency": serve.latency_stats(hs), "results_identical_to_one_at_a_time": bool(same),
+           "load": {}}
+    for frac in (0.5, 0.7, 0.9):
+        arr = serve.poisson_arrivals(frac * sat, len(reqs), seed=int(frac * 100))
+        hs2, span2 = run_stream(arr, 4)
+        same2 = all(np.array_equal(h.result, alone[i]) for i, h in enumerate(hs2))
+        out["load"][str(frac)] = {"rate_per_s": frac * sat, "throughput_per_s": len(reqs) / span2,
+                                  "latency": serve.latency_stats(hs2), "results_identical": bool(same2),
+                                  "batched_requests": int(sum(h.batched_with > 1 for h in hs2))}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "serve":
+        return run_serve(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -148,11 +148,23 @@ nd_status nd_truss_classic(const int32_t* kappa3, int64_t num_edges, int32_t* ou
 nd_status nd_prof_enable(int on);
 nd_status nd_prof_read(int i, const char** name, int64_t* launches, double* total_ms);
 
+/* Autotune the degree buckets of this handle: for each candidate threshold
+ * set (t0 in {4,8}, t1 in {32,64}, t2 in {256,1024,2048,8192}; rows of
+ * length [1,t0] go to 4-lane groups, (t0,t1] to 8-lane groups, (t1,t2] to
+ * warps, longer ones to whole CTAs) time `passes` SND passes from d_s, keep
+ * the fastest, and remember it for this device, (r,s) and size class
+ * (floor(log2 of the incidence count)): later nd_build_incidence calls of the
+ * same class start with it.  Results never depend on the thresholds.
+ * thr_out[3] and best_ms_out may be NULL.  Synchronises `stream`. */
+nd_status nd_autotune(nd_incidence* inc, int32_t passes, void* stream, int32_t* thr_out, double* best_ms_out);
+
 /* Counters of the last nd_snd / nd_and / nd_iterate_k call on this handle,
  * pass by pass: changed[i] = r-cliques whose tau changed in pass i,
- * evaluated[i] = h-index evaluations in pass i (active r-cliques for AND).
- * Fills at most cap entries and returns the number of passes in *passes. */
-nd_status nd_last_passes(const nd_incidence* inc, int64_t* changed, int64_t* evaluated,
+ * evaluated[i] = h-index evaluations in pass i (active r-cliques for AND),
+ * incidences[i] = incidences (s-cliques) streamed by those evaluations.
+ * Any array may be NULL.  Fills at most cap entries and returns the number
+ * of passes in *passes. */
+nd_status nd_last_passes(const nd_incidence* inc, int64_t* changed, int64_t* evaluated, int64_t* incidences,
                          int32_t cap, int32_t* passes);
 
 /* Device memory held by the handle, in bytes. */

@@ -29,8 +29,10 @@ def _nvcc() -> str:
 
 
 def _flags(extra=()):
+    # ND_NVCC_DEFINES: optional extra -D tuning knobs (e.g. "-DND_WARP_UNROLL=8")
+    knobs = os.environ.get("ND_NVCC_DEFINES", "").split()
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-                   "-I", CSRC, *extra]
+                   "-I", CSRC, *knobs, *extra]
 
 
 def _stale() -> bool:
@@ -42,7 +44,11 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, libdir: str | None = None) -> str:
+    global LIBDIR, LIB
+    if libdir is not None:
+        LIBDIR = libdir
+        LIB = os.path.join(libdir, "libnd.so")
     if not force and not _stale():
         return LIB
     os.makedirs(LIBDIR, exist_ok=True)

@@ -1,6 +1,10 @@
 // C ABI of libnd (declared and documented in include/nd.h).
+#include <array>
 #include <chrono>
+#include <cmath>
 #include <cstdio>
+#include <map>
+#include <tuple>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -59,7 +63,8 @@ void prof_drain() {
 }
 }  // namespace
 
-nd_prof_scope::nd_prof_scope(const char* name, cudaStream_t s) : kid(-1), st(s), a(nullptr), b(nullptr), on(false) {
+nd_prof_scope::nd_prof_scope(const char* name, cudaStream_t s, int launches)
+    : kid(-1), st(s), a(nullptr), b(nullptr), on(false), count(launches) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_prof_on) return;
     kid = prof_id(name);
@@ -72,7 +77,7 @@ nd_prof_scope::~nd_prof_scope() {
     if (!on) return;
     cudaEventRecord(b, st);
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    g_prof[kid].launches++;
+    g_prof[kid].launches += count;
     g_prof[kid].pending.push_back({a, b});
 }
 
@@ -161,6 +166,9 @@ void nd_free(nd_incidence* h) {
     void* ptrs[] = {h->nlow, h->up_start, h->eid, h->e_u, h->e_v, h->tri_ptr, h->tri_w, h->tri_e,
                     h->items, h->tau[0], h->tau[1], h->front[0], h->front[1], h->counters};
     for (void* p : ptrs) nd_release(p, st);
+    for (auto& row : h->pass_graph)
+        for (auto& ex : row)
+            if (ex) cudaGraphExecDestroy(ex);
     if (!h->inc_aliases_graph) {
         nd_release(h->inc_ptr, st);
         nd_release(h->inc, st);
@@ -170,6 +178,24 @@ void nd_free(nd_incidence* h) {
     if (h->h_counters) cudaFreeHost(h->h_counters);
     cudaStreamSynchronize(st);
     delete h;
+}
+
+// ---------------------------------------------------------------------------
+// bucket autotuning: thresholds picked by timing, cached per (device, r, s,
+// size class = floor(log2(incidences)))
+// ---------------------------------------------------------------------------
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int>, std::array<int32_t, 3>> g_tune;
+
+static int size_class(const nd_incidence* h) {
+    return (int)std::floor(std::log2((double)(h->num_inc > 0 ? h->num_inc : 1)));
+}
+
+static void apply_tuned(nd_incidence* h, int dev) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(std::make_tuple(dev, h->r, h->s, size_class(h)));
+    if (it != g_tune.end())
+        for (int i = 0; i < 3; ++i) h->thr[i] = it->second[i];
 }
 
 static nd_status check_rs(int r, int s) {
@@ -221,6 +247,7 @@ static nd_status build_common(const nd_csr* g, int r, int s, cudaStream_t st, nd
             if (rc == ND_OK) rc = nd_build_k4_incidence(h, st);
         }
     }
+    if (rc == ND_OK) apply_tuned(h, dev);
     if (rc == ND_OK) rc = nd_build_buckets(h, st);
     if (rc == ND_OK) rc = host_wait(st);
     if (rc != ND_OK) {
@@ -427,14 +454,65 @@ nd_status nd_truss_classic(const int32_t* kappa3, int64_t num_edges, int32_t* ou
     return nd_classic_truss(kappa3, num_edges, out, (cudaStream_t)stream);
 }
 
-nd_status nd_last_passes(const nd_incidence* h, int64_t* changed, int64_t* evaluated, int32_t cap,
-                         int32_t* passes) {
+nd_status nd_autotune(nd_incidence* h, int32_t passes, void* stream, int32_t* thr_out, double* best_ms_out) {
+    if (!h) { nd_set_error("handle is NULL"); return ND_E_INVAL; }
+    if (passes < 1) passes = 2;
+    cudaStream_t st = (cudaStream_t)stream;
+    h->last_stream = st;
+    int dev = 0;
+    ND_CUDA(cudaGetDevice(&dev));
+    static const int32_t T0[] = {4, 8}, T1[] = {32, 64}, T2[] = {256, 1024, 2048, 8192};
+    std::array<int32_t, 3> best = {h->thr[0], h->thr[1], h->thr[2]};
+    double best_ms = -1.0;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ND_CUDA(cudaEventCreate(&a));
+    ND_CUDA(cudaEventCreate(&b));
+    nd_status rc = ND_OK;
+    for (int32_t t0 : T0)
+        for (int32_t t1 : T1)
+            for (int32_t t2 : T2) {
+                if (rc != ND_OK) break;
+                h->thr[0] = t0;
+                h->thr[1] = t1;
+                h->thr[2] = t2;
+                rc = nd_build_buckets(h, st);
+                if (rc != ND_OK) break;
+                int32_t* res = nullptr;
+                int32_t upd = 0;
+                int64_t ev = 0;
+                bool conv = false;
+                cudaEventRecord(a, st);
+                rc = nd_run(h, ND_SND, passes, nullptr, &res, &upd, &ev, &conv, st);
+                cudaEventRecord(b, st);
+                if (rc != ND_OK) break;
+                cudaEventSynchronize(b);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, a, b);
+                if (best_ms < 0 || ms < best_ms) { best_ms = ms; best = {t0, t1, t2}; }
+            }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc != ND_OK) return rc;
+    for (int i = 0; i < 3; ++i) h->thr[i] = best[i];
+    ND_TRY(nd_build_buckets(h, st));
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[std::make_tuple(dev, h->r, h->s, size_class(h))] = best;
+    }
+    if (thr_out) for (int i = 0; i < 3; ++i) thr_out[i] = best[i];
+    if (best_ms_out) *best_ms_out = best_ms;
+    return ND_OK;
+}
+
+nd_status nd_last_passes(const nd_incidence* h, int64_t* changed, int64_t* evaluated, int64_t* incidences,
+                         int32_t cap, int32_t* passes) {
     if (!h || !passes) { nd_set_error("NULL argument"); return ND_E_INVAL; }
     const int32_t n = (int32_t)h->last_changed.size();
     *passes = n;
     for (int32_t i = 0; i < n && i < cap; ++i) {
         if (changed) changed[i] = h->last_changed[i];
         if (evaluated) evaluated[i] = h->last_evals[i];
+        if (incidences) incidences[i] = h->last_incs[i];
     }
     return ND_OK;
 }

@@ -5,13 +5,14 @@
 // (s-r)-tuples of a neighbourhood), and recomputes them on every pass.  Here
 // they are found once, by sorted-list intersection, and stored:
 //   (1,2)  the CSR itself is the incidence (q = 1);
-//   (2,3)  edge (u,v): w in N(u) /\ N(v) -> the pair (id(u,w), id(v,w));
+//   (2,3)  triangle {u,v,w} -> one pair per edge: the ids of its other two
+//          edges (found once each, by degree orientation);
 //   (3,4)  triangle (u,v,w): x in N(u) /\ N(v) /\ N(w) -> the ids of the
 //          triangles {u,v,x}, {u,w,x}, {v,w,x}.
 // Every step is a count pass, an exclusive scan and a fill pass over the same
-// enumeration, so rows come out in canonical order with no atomics.
-// Intersections: one warp per r-clique; the lanes walk the shortest list in
-// order and binary-search each element in the other list(s) (read-only path).
+// enumeration.  Intersections: one warp per list pair; the lanes walk the
+// shorter list in order and binary-search each element in the other list(s)
+// (read-only path).
 #include "nd_internal.cuh"
 
 namespace {
@@ -108,44 +109,105 @@ __global__ void k_edge_ids(int64_t n, const int64_t* __restrict__ rp, const int3
     }
 }
 
-// ---- (2,3): triangles of every edge (one warp per edge) --------------------
-// COUNT: ptr[e] = d_3(e).  FILL: writes (eid(u,w), eid(v,w)) for each common
-// neighbour w, in increasing w, at ptr[e] (already scanned).
+// ---- (2,3): triangles by degree orientation --------------------------------
+// Vertex u precedes v iff (d_u, u) < (d_v, v).  Orienting every edge from the
+// earlier to the later endpoint, each triangle {u,v,w} (u before v before w)
+// is found exactly once, as w in out(u) /\ out(v) for the oriented edge
+// u -> v; out-lists are at most sqrt(2m) long.  The triangle then adds one
+// incidence to each of its three edges, at slots taken from per-edge counters
+// (count pass) and cursors (fill pass).  Row order inside an edge's incidence
+// row is therefore unspecified; the h-index of a row does not depend on it.
+__device__ __forceinline__ bool precedes(int64_t du, int32_t u, int64_t dv, int32_t v) {
+    return du < dv || (du == dv && u < v);
+}
+
+// one warp per vertex: count / list the out-neighbours of u in id order
 template <bool FILL>
-__global__ void k_edge_triangles(int64_t m, const int64_t* __restrict__ rp,
-                                 const int32_t* __restrict__ col, const uint32_t* __restrict__ eid,
-                                 const int32_t* __restrict__ e_u, const int32_t* __restrict__ e_v,
-                                 int64_t* __restrict__ ptr, uint2* __restrict__ inc) {
+__global__ void k_orient(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                         const uint32_t* __restrict__ eid, int64_t* __restrict__ out_ptr,
+                         int32_t* __restrict__ out_col, uint32_t* __restrict__ out_eid,
+                         int32_t* __restrict__ out_src) {
     const int lane = threadIdx.x & 31;
-    for (int64_t e = warp_id_global(); e < m; e += warp_count_global()) {
-        const int32_t u = e_u[e], v = e_v[e];
-        int64_t ab = rp[u], ae = rp[u + 1], bb = rp[v], be = rp[v + 1];
-        if (ae - ab > be - bb) { int64_t t = ab; ab = bb; bb = t; t = ae; ae = be; be = t; }
-        int64_t out = FILL ? ptr[e] : 0;
+    for (int64_t u = warp_id_global(); u < n; u += warp_count_global()) {
+        const int64_t b = rp[u], e = rp[u + 1], du = e - b;
+        const int64_t base = FILL ? out_ptr[u] : 0;
         int64_t cnt = 0;
-        int64_t lo = bb;  // elements of the short list increase, so searches can start here
-        for (int64_t base = ab; base < ae; base += 32) {
-            int64_t p = base + lane;
-            bool found = false;
-            int64_t pb = 0;
-            int32_t x = 0;
-            if (p < ae) {
-                x = __ldg(col + p);
-                pb = lower_bound_i32(col, lo, be, x);
-                found = (pb < be) && (__ldg(col + pb) == x);
+        for (int64_t p0 = b; p0 < e; p0 += 32) {
+            const int64_t p = p0 + lane;
+            bool keep = false;
+            int32_t v = 0;
+            if (p < e) {
+                v = __ldg(col + p);
+                keep = precedes(du, (int32_t)u, __ldg(rp + v + 1) - __ldg(rp + v), v);
             }
-            unsigned bal = __ballot_sync(kFull, found);
-            if (FILL && found) {
-                int64_t slot = out + cnt + __popc(bal & lanemask_lt());
-                inc[slot] = make_uint2(__ldg(eid + p), __ldg(eid + pb));
+            const unsigned bal = __ballot_sync(kFull, keep);
+            if (FILL && keep) {
+                const int64_t slot = base + cnt + __popc(bal & lanemask_lt());
+                out_col[slot] = v;
+                out_eid[slot] = __ldg(eid + p);
+                out_src[slot] = (int32_t)u;
             }
             cnt += __popc(bal);
-            // next chunk starts after this chunk's last element: its position in B bounds the rest
-            int64_t last_pb = __shfl_sync(kFull, pb, 31);
-            bool full_chunk = (base + 32 <= ae);
-            if (full_chunk) lo = last_pb;
         }
-        if (!FILL && lane == 0) ptr[e] = cnt;
+        if (!FILL && lane == 0) out_ptr[u] = cnt;
+    }
+}
+
+// one warp per oriented edge u -> v: the triangles {u, v, w}, w in out(u) /\ out(v)
+template <bool FILL>
+__global__ void k_tri_oriented(int64_t m, const int64_t* __restrict__ out_ptr,
+                               const int32_t* __restrict__ out_col, const uint32_t* __restrict__ out_eid,
+                               const int32_t* __restrict__ out_src, unsigned long long* __restrict__ ctr,
+                               uint2* __restrict__ inc) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t k = warp_id_global(); k < m; k += warp_count_global()) {
+        const int32_t u = out_src[k], v = out_col[k];
+        const uint32_t e_uv = out_eid[k];
+        int64_t ab = out_ptr[u], ae = out_ptr[u + 1], bb = out_ptr[v], be = out_ptr[v + 1];
+        bool a_is_u = true;
+        if (ae - ab > be - bb) {
+            int64_t t = ab; ab = bb; bb = t; t = ae; ae = be; be = t;
+            a_is_u = false;
+        }
+        int64_t lo = bb;
+        for (int64_t base = ab; base < ae; base += 32) {
+            const int64_t p = base + lane;
+            bool found = false;
+            int64_t pb = 0;
+            if (p < ae) {
+                const int32_t x = __ldg(out_col + p);
+                pb = lower_bound_i32(out_col, lo, be, x);
+                found = (pb < be) && (__ldg(out_col + pb) == x);
+            }
+            const unsigned bal = __ballot_sync(kFull, found);
+            const int nf = __popc(bal);
+            if (nf) {
+                uint32_t e_uw = 0, e_vw = 0;
+                if (found) {
+                    const uint32_t ea = __ldg(out_eid + p), eb = __ldg(out_eid + pb);
+                    e_uw = a_is_u ? ea : eb;
+                    e_vw = a_is_u ? eb : ea;
+                }
+                if (!FILL) {
+                    if (lane == 0) atomicAdd(ctr + e_uv, (unsigned long long)nf);
+                    if (found) {
+                        atomicAdd(ctr + e_uw, 1ull);
+                        atomicAdd(ctr + e_vw, 1ull);
+                    }
+                } else {
+                    unsigned long long s0 = 0;
+                    if (lane == 0) s0 = atomicAdd(ctr + e_uv, (unsigned long long)nf);
+                    s0 = __shfl_sync(kFull, s0, 0);
+                    if (found) {
+                        inc[s0 + __popc(bal & lanemask_lt())] = make_uint2(e_uw, e_vw);
+                        inc[atomicAdd(ctr + e_uw, 1ull)] = make_uint2(e_uv, e_vw);
+                        inc[atomicAdd(ctr + e_vw, 1ull)] = make_uint2(e_uv, e_uw);
+                    }
+                }
+            }
+            const int64_t last_pb = __shfl_sync(kFull, pb, 31);
+            if (base + 32 <= ae) lo = last_pb;
+        }
     }
 }
 
@@ -270,17 +332,19 @@ __global__ void k_triangle_k4(int64_t T, const int64_t* __restrict__ rp, const i
 }
 
 // ---- degree buckets --------------------------------------------------------
-__device__ __forceinline__ int bucket_of(int64_t d) {
-    return d == 0 ? -1 : (d <= 8 ? 0 : (d <= 64 ? 1 : (d <= 2048 ? 2 : 3)));
+// bucket of a row of length d under thresholds t = (t0, t1, t2):
+// [1,t0] -> 4 lanes, (t0,t1] -> 8 lanes, (t1,t2] -> a warp, > t2 -> a CTA
+__device__ __forceinline__ int bucket_of(int64_t d, int3 t) {
+    return d == 0 ? -1 : (d <= t.x ? 0 : (d <= t.y ? 1 : (d <= t.z ? 2 : 3)));
 }
 
-__global__ void k_bucket_flags(int64_t N, const int64_t* __restrict__ inc_ptr, int b,
+__global__ void k_bucket_flags(int64_t N, const int64_t* __restrict__ inc_ptr, int b, int3 thr,
                                int64_t* __restrict__ flags, unsigned long long* __restrict__ inc_sum) {
     unsigned long long local = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         int64_t d = inc_ptr[i + 1] - inc_ptr[i];
-        bool in = bucket_of(d) == b;
+        bool in = bucket_of(d, thr) == b;
         flags[i] = in;
         if (in) local += (unsigned long long)d;
     }
@@ -289,12 +353,12 @@ __global__ void k_bucket_flags(int64_t N, const int64_t* __restrict__ inc_ptr, i
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(inc_sum, local);
 }
 
-__global__ void k_bucket_scatter(int64_t N, const int64_t* __restrict__ inc_ptr, int b,
+__global__ void k_bucket_scatter(int64_t N, const int64_t* __restrict__ inc_ptr, int b, int3 thr,
                                  const int64_t* __restrict__ pos, nd_item* __restrict__ items) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         int64_t d = inc_ptr[i + 1] - inc_ptr[i];
-        if (bucket_of(d) == b) {
+        if (bucket_of(d, thr) == b) {
             nd_item it;
             it.jb = inc_ptr[i];
             it.R = (uint32_t)i;
@@ -426,25 +490,56 @@ nd_status nd_build_edges(nd_incidence* h, cudaStream_t st) {
 }
 
 nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
-    h->num_r = h->m;
-    ND_TRY(nd_alloc((void**)&h->inc_ptr, sizeof(int64_t) * (h->m + 1), st, h));
-    ND_CUDA(cudaMemsetAsync(h->inc_ptr, 0, sizeof(int64_t) * (h->m + 1), st));
-    int blocks = nd_blocks_for(h->m * 32, kThreads, grid_cap(h) * 4);
-    if (h->m > 0) {
-        nd_prof_scope ps("tri_count", st);
-        k_edge_triangles<false><<<blocks, kThreads, 0, st>>>(h->m, h->rp, h->col, h->eid, h->e_u,
-                                                             h->e_v, h->inc_ptr, nullptr);
+    const int64_t m = h->m, n = h->n;
+    h->num_r = m;
+    ND_TRY(nd_alloc((void**)&h->inc_ptr, sizeof(int64_t) * (m + 1), st, h));
+    ND_CUDA(cudaMemsetAsync(h->inc_ptr, 0, sizeof(int64_t) * (m + 1), st));
+    if (m == 0) { h->num_inc = 0; ND_TRY(nd_alloc((void**)&h->inc, 16, st, h)); return ND_OK; }
+    // oriented out-lists (temporary)
+    int64_t* out_ptr = nullptr;
+    int32_t *out_col = nullptr, *out_src = nullptr;
+    uint32_t* out_eid = nullptr;
+    unsigned long long* cursor = nullptr;
+    ND_CUDA(cudaMallocAsync((void**)&out_ptr, sizeof(int64_t) * (n + 1), st));
+    ND_CUDA(cudaMallocAsync((void**)&out_col, sizeof(int32_t) * m, st));
+    ND_CUDA(cudaMallocAsync((void**)&out_src, sizeof(int32_t) * m, st));
+    ND_CUDA(cudaMallocAsync((void**)&out_eid, sizeof(uint32_t) * m, st));
+    ND_CUDA(cudaMemsetAsync(out_ptr + n, 0, sizeof(int64_t), st));
+    const int vblocks = nd_blocks_for(n * 32, kThreads, grid_cap(h) * 4);
+    {
+        nd_prof_scope ps("orient", st);
+        k_orient<false><<<vblocks, kThreads, 0, st>>>(n, h->rp, h->col, h->eid, out_ptr, nullptr, nullptr, nullptr);
         ND_CUDA(cudaGetLastError());
     }
-    ND_TRY(nd_scan_i64(h->inc_ptr, h->m, st));
-    ND_TRY(read_i64(h->inc_ptr + h->m, &h->num_inc, st));
+    ND_TRY(nd_scan_i64(out_ptr, n, st));
+    {
+        nd_prof_scope ps("orient", st);
+        k_orient<true><<<vblocks, kThreads, 0, st>>>(n, h->rp, h->col, h->eid, out_ptr, out_col, out_eid, out_src);
+        ND_CUDA(cudaGetLastError());
+    }
+    const int eblocks = nd_blocks_for(m * 32, kThreads, grid_cap(h) * 4);
+    {
+        nd_prof_scope ps("tri_count", st);
+        k_tri_oriented<false><<<eblocks, kThreads, 0, st>>>(m, out_ptr, out_col, out_eid, out_src,
+                                                            (unsigned long long*)h->inc_ptr, nullptr);
+        ND_CUDA(cudaGetLastError());
+    }
+    ND_TRY(nd_scan_i64(h->inc_ptr, m, st));
+    ND_TRY(read_i64(h->inc_ptr + m, &h->num_inc, st));
     ND_TRY(nd_alloc((void**)&h->inc, sizeof(uint32_t) * 2 * (h->num_inc > 0 ? h->num_inc : 1), st, h));
     if (h->num_inc > 0) {
+        ND_CUDA(cudaMallocAsync((void**)&cursor, sizeof(unsigned long long) * m, st));
+        ND_CUDA(cudaMemcpyAsync(cursor, h->inc_ptr, sizeof(int64_t) * m, cudaMemcpyDeviceToDevice, st));
         nd_prof_scope ps("tri_fill", st);
-        k_edge_triangles<true><<<blocks, kThreads, 0, st>>>(h->m, h->rp, h->col, h->eid, h->e_u,
-                                                            h->e_v, h->inc_ptr, (uint2*)h->inc);
+        k_tri_oriented<true><<<eblocks, kThreads, 0, st>>>(m, out_ptr, out_col, out_eid, out_src, cursor,
+                                                           (uint2*)h->inc);
         ND_CUDA(cudaGetLastError());
     }
+    cudaFreeAsync(out_ptr, st);
+    cudaFreeAsync(out_col, st);
+    cudaFreeAsync(out_src, st);
+    cudaFreeAsync(out_eid, st);
+    if (cursor) cudaFreeAsync(cursor, st);
     return ND_OK;
 }
 
@@ -510,12 +605,17 @@ nd_status nd_build_k4_incidence(nd_incidence* h, cudaStream_t st) {
 
 nd_status nd_build_buckets(nd_incidence* h, cudaStream_t st) {
     const int64_t N = h->num_r;
+    // pass graphs hold the chunk table of the old buckets
+    for (auto& row : h->pass_graph)
+        for (auto& ex : row)
+            if (ex) { cudaGraphExecDestroy(ex); ex = nullptr; }
+    const int3 thr = make_int3(h->thr[0], h->thr[1], h->thr[2]);
     int64_t* flags = nullptr;
     unsigned long long* sums = nullptr;
     ND_CUDA(cudaMallocAsync((void**)&flags, sizeof(int64_t) * (N + 1), st));
     ND_CUDA(cudaMallocAsync((void**)&sums, sizeof(unsigned long long) * ND_NB, st));
     ND_CUDA(cudaMemsetAsync(sums, 0, sizeof(unsigned long long) * ND_NB, st));
-    ND_TRY(nd_alloc((void**)&h->items, sizeof(nd_item) * (N > 0 ? N : 1), st, h));
+    if (!h->items) ND_TRY(nd_alloc((void**)&h->items, sizeof(nd_item) * (N > 0 ? N : 1), st, h));
     int blocks = nd_blocks_for(N, kThreads, grid_cap(h) * 2);
     int64_t lo = 0;
     for (int b = 0; b < ND_NB; ++b) {
@@ -524,13 +624,13 @@ nd_status nd_build_buckets(nd_incidence* h, cudaStream_t st) {
         ND_CUDA(cudaMemsetAsync(flags + N, 0, sizeof(int64_t), st));
         {
             nd_prof_scope ps("buckets", st);
-            k_bucket_flags<<<blocks, kThreads, 0, st>>>(N, h->inc_ptr, b, flags, sums + b);
+            k_bucket_flags<<<blocks, kThreads, 0, st>>>(N, h->inc_ptr, b, thr, flags, sums + b);
             ND_CUDA(cudaGetLastError());
         }
         ND_TRY(nd_scan_i64(flags, N, st));
         {
             nd_prof_scope ps("buckets", st);
-            k_bucket_scatter<<<blocks, kThreads, 0, st>>>(N, h->inc_ptr, b, flags, h->items + lo);
+            k_bucket_scatter<<<blocks, kThreads, 0, st>>>(N, h->inc_ptr, b, thr, flags, h->items + lo);
             ND_CUDA(cudaGetLastError());
         }
         int64_t cnt = 0;

@@ -38,6 +38,10 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int kThreads = 256;
+#ifndef ND_WARP_UNROLL
+#define ND_WARP_UNROLL 4  // streamed incidences in flight per lane (warp / CTA rows)
+#endif
+constexpr int kWarpUnroll = ND_WARP_UNROLL;
 
 // Work of one pass is a list of chunks, longest rows first (bucket 3, 2, 1,
 // 0); persistent blocks take chunks from a per-pass counter until none are
@@ -56,7 +60,8 @@ struct SweepParams {
     int64_t chunk_end[ND_NB];      // cumulative chunk counts, in processing order
     const uint32_t* cur;  // AND + notification: frontier read in this pass
     uint32_t* next;       // and the frontier written for the next pass
-    unsigned long long* ctr;         // this pass: [0] changed, [1] evaluated, [2] next chunk
+    unsigned long long* ctr;         // this pass: [0] changed, [1] evaluated, [2] next chunk,
+                                     // [3] incidences of the evaluated rows
     const unsigned long long* prev;  // previous pass (null on the first)
 };
 
@@ -164,7 +169,7 @@ __device__ __forceinline__ int32_t warp_hindex(const uint32_t* __restrict__ inc,
     const int lane = threadIdx.x & 31;
     if (t <= 0) return 0;
     int cnt = 0;
-#pragma unroll 4
+#pragma unroll kWarpUnroll
     for (int64_t j = jb + lane; j < je; j += 32) cnt += (rho_at<Q, RO>(inc, tau, j) >= t);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
@@ -194,7 +199,7 @@ __device__ __forceinline__ int32_t cta_hindex(const uint32_t* __restrict__ inc, 
                                               unsigned* bins /* 257 */, int* bounds /* 2 */) {
     if (t <= 0) return 0;
     int cnt = 0;
-#pragma unroll 4
+#pragma unroll kWarpUnroll
     for (int64_t j = jb + threadIdx.x; j < je; j += kThreads) cnt += (rho_at<Q, RO>(inc, tau, j) >= t);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
@@ -233,21 +238,31 @@ __device__ __forceinline__ int32_t cta_hindex(const uint32_t* __restrict__ inc, 
 }
 
 // notify every neighbour whose tau could still depend on R (Alg. 3, orange
-// lines): set its next-frontier bit if h <= tau(R')
+// lines): set its next-frontier bit if h <= tau(R'), reading the word first
+// so that an atomic is only issued for a bit that is still clear.  (Warp-wide
+// merging of bits that share a word was measured slower: the match runs for
+// every neighbour, while most neighbours need no write.)
 template <int Q>
 __device__ __forceinline__ void notify_row(const SweepParams& P, int64_t jb, int64_t je, int32_t h,
-                                           int first, int step) {
+                                           int first, int step, unsigned /*gmask*/) {
     for (int64_t j = jb + first; j < je; j += step) {
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
-            uint32_t Rp = __ldg(P.inc + Q * j + k);
+            const uint32_t Rp = __ldg(P.inc + Q * j + k);
             if (h <= ld_tau<false>(P.tin + Rp)) {
-                uint32_t bit = 1u << (Rp & 31);
+                const uint32_t bit = 1u << (Rp & 31);
                 uint32_t* w = P.next + (Rp >> 5);
                 if (!(*(volatile uint32_t*)w & bit)) atomicOr(w, bit);
             }
         }
     }
+}
+
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+    if (G >= 32) return 0xffffffffu;
+    const unsigned lane = threadIdx.x & 31;
+    return ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
 }
 
 __device__ __forceinline__ nd_item load_item(const nd_item* __restrict__ items, int64_t i) {
@@ -263,7 +278,8 @@ __device__ __forceinline__ nd_item load_item(const nd_item* __restrict__ items, 
 // item is loaded before the current one is evaluated
 template <int Q, int G, int C, bool AND, bool NOTIFY>
 __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, int64_t last,
-                                           unsigned long long& changed, unsigned long long& evals) {
+                                           unsigned long long& changed, unsigned long long& evals,
+                                           unsigned long long& incs) {
     auto g = cg::tiled_partition<G>(cg::this_thread_block());
     const int lane = g.thread_rank();
     int64_t i = first + g.meta_group_rank();
@@ -282,10 +298,11 @@ __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, 
             const int32_t h = group_hindex<Q, G, C, !AND>(g, P.inc, P.tin, jb, je, t);
             if (lane == 0) {
                 evals++;
+                incs += it.d;
                 if (h != t) changed++;
                 if (!AND || h != t) P.tout[R] = h;
             }
-            if (AND && NOTIFY && h != t) notify_row<Q>(P, jb, je, h, lane, G);
+            if (AND && NOTIFY && h != t) notify_row<Q>(P, jb, je, h, lane, G, group_mask<G>());
         }
         it = nx;
         i = ni;
@@ -296,7 +313,7 @@ __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, 
 template <int Q, bool AND, bool NOTIFY>
 __device__ __forceinline__ void run_warps(const SweepParams& P, int64_t first, int64_t last,
                                           unsigned* bins, unsigned long long& changed,
-                                          unsigned long long& evals) {
+                                          unsigned long long& evals, unsigned long long& incs) {
     const int lane = threadIdx.x & 31;
     for (int64_t i = first + (threadIdx.x >> 5); i < last; i += kThreads / 32) {
         const nd_item it = load_item(P.items, i);
@@ -309,10 +326,11 @@ __device__ __forceinline__ void run_warps(const SweepParams& P, int64_t first, i
         const int32_t h = warp_hindex<Q, !AND>(P.inc, P.tin, jb, je, t, bins);
         if (lane == 0) {
             evals++;
+            incs += it.d;
             if (h != t) changed++;
             if (!AND || h != t) P.tout[R] = h;
         }
-        if (AND && NOTIFY && h != t) notify_row<Q>(P, jb, je, h, lane, 32);
+        if (AND && NOTIFY && h != t) notify_row<Q>(P, jb, je, h, lane, 32, 0xffffffffu);
     }
 }
 
@@ -320,7 +338,7 @@ __device__ __forceinline__ void run_warps(const SweepParams& P, int64_t first, i
 template <int Q, bool AND, bool NOTIFY>
 __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int64_t last,
                                         unsigned* bins, int* bounds, unsigned long long& changed,
-                                        unsigned long long& evals) {
+                                        unsigned long long& evals, unsigned long long& incs) {
     for (int64_t i = first; i < last; ++i) {
         const nd_item it = load_item(P.items, i);
         const uint32_t R = it.R;
@@ -332,21 +350,25 @@ __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int
         const int32_t h = cta_hindex<Q, !AND>(P.inc, P.tin, jb, je, t, bins, bounds);
         if (threadIdx.x == 0) {
             evals++;
+            incs += it.d;
             if (h != t) changed++;
             if (!AND || h != t) P.tout[R] = h;
         }
-        if (AND && NOTIFY && h != t) notify_row<Q>(P, jb, je, h, threadIdx.x, kThreads);
+        if (AND && NOTIFY && h != t) notify_row<Q>(P, jb, je, h, threadIdx.x, kThreads, 0xffffffffu);
         __syncthreads();
     }
 }
 
 template <int Q, bool AND, bool NOTIFY>
-__global__ void __launch_bounds__(kThreads, 5) k_pass(SweepParams P) {
+#ifndef ND_PASS_MIN_BLOCKS
+#define ND_PASS_MIN_BLOCKS 6  // resident blocks per SM the register budget targets (6 measured best)
+#endif
+__global__ void __launch_bounds__(kThreads, ND_PASS_MIN_BLOCKS) k_pass(SweepParams P) {
     if (P.prev != nullptr && *(volatile const unsigned long long*)P.prev == 0ull) return;  // converged
     __shared__ unsigned bins[kThreads / 32][260];  // k-ary search bins, one set per warp
     __shared__ int bounds[2];
     __shared__ unsigned long long s_chunk;
-    unsigned long long changed = 0, evals = 0;
+    unsigned long long changed = 0, evals = 0, incs = 0;
     const int64_t total = P.chunk_end[ND_NB - 1];
     for (;;) {
         if (threadIdx.x == 0) s_chunk = atomicAdd(P.ctr + 2, 1ull);
@@ -361,26 +383,28 @@ __global__ void __launch_bounds__(kThreads, 5) k_pass(SweepParams P) {
         const int64_t first = P.lo[b] + k * chunk_r(b);
         const int64_t last = min(first + (int64_t)chunk_r(b), P.hi[b]);
         switch (b) {
-            case 0: run_groups<Q, 4, 2, AND, NOTIFY>(P, first, last, changed, evals); break;
-            case 1: run_groups<Q, 8, 8, AND, NOTIFY>(P, first, last, changed, evals); break;
-            case 2: run_warps<Q, AND, NOTIFY>(P, first, last, bins[threadIdx.x >> 5], changed, evals); break;
-            default: run_cta<Q, AND, NOTIFY>(P, first, last, bins[0], bounds, changed, evals); break;
+            case 0: run_groups<Q, 4, 2, AND, NOTIFY>(P, first, last, changed, evals, incs); break;
+            case 1: run_groups<Q, 8, 8, AND, NOTIFY>(P, first, last, changed, evals, incs); break;
+            case 2: run_warps<Q, AND, NOTIFY>(P, first, last, bins[threadIdx.x >> 5], changed, evals, incs); break;
+            default: run_cta<Q, AND, NOTIFY>(P, first, last, bins[0], bounds, changed, evals, incs); break;
         }
     }
-    __shared__ unsigned long long s_ch[kThreads / 32], s_ev[kThreads / 32];
+    __shared__ unsigned long long s_ch[kThreads / 32], s_ev[kThreads / 32], s_in[kThreads / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         changed += __shfl_xor_sync(0xffffffffu, changed, o);
         evals += __shfl_xor_sync(0xffffffffu, evals, o);
+        incs += __shfl_xor_sync(0xffffffffu, incs, o);
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) { s_ch[wid] = changed; s_ev[wid] = evals; }
+    if (lane == 0) { s_ch[wid] = changed; s_ev[wid] = evals; s_in[wid] = incs; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long a = 0, e = 0;
-        for (int w = 0; w < kThreads / 32; ++w) { a += s_ch[w]; e += s_ev[w]; }
+        unsigned long long a = 0, e = 0, c = 0;
+        for (int w = 0; w < kThreads / 32; ++w) { a += s_ch[w]; e += s_ev[w]; c += s_in[w]; }
         if (a) atomicAdd(P.ctr, a);
         if (e) atomicAdd(P.ctr + 1, e);
+        if (c) atomicAdd(P.ctr + 3, c);
     }
 }
 
@@ -457,6 +481,91 @@ nd_status ensure_state(nd_incidence* h, bool and_mode, cudaStream_t st) {
     return ND_OK;
 }
 
+
+// parameters of pass k of a batch whose counters start at slot `base`
+// (batches start at an even pass, so the parities below are per batch)
+SweepParams pass_params(const nd_incidence* h, int mode, const SweepParams& P0, int base, int k, int kind) {
+    SweepParams P = P0;
+    P.ctr = h->counters + ND_SLOT * (base + k);
+    if (k > 0) P.prev = h->counters + ND_SLOT * (base + k - 1);
+    else if (kind == 0) P.prev = nullptr;
+    else P.prev = h->counters + ND_SLOT * ((base ^ ND_BATCH) + ND_BATCH - 1);
+    if (mode != ND_SND) {
+        P.tin = h->tau[0];
+        P.tout = h->tau[0];
+        P.cur = h->front[k & 1];
+        P.next = h->front[(k & 1) ^ 1];
+    } else {
+        P.tin = h->tau[k & 1];
+        P.tout = h->tau[(k & 1) ^ 1];
+        P.cur = nullptr;
+        P.next = nullptr;
+    }
+    return P;
+}
+
+// A full batch of passes as one CUDA graph: clear the batch's counters, then
+// for each pass (AND: clear the next frontier) the pass kernel, then copy
+// the counters to the pinned host mirror.  Built explicitly (not by stream
+// capture) so that it also serves the legacy default stream.  On any
+// failure the handle falls back to ordinary launches for this kind.
+void make_batch_graph(nd_incidence* h, int mode, int kind, const SweepParams& P0, int grid, pass_fn fn,
+                      int64_t words) {
+    const int base = (kind == 2) ? ND_BATCH : 0;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+    cudaGraphNode_t last = nullptr;
+    if (ok) {
+        cudaMemsetParams ms = {};
+        ms.dst = h->counters + ND_SLOT * base;
+        ms.value = 0;
+        ms.elementSize = 4;
+        ms.width = (size_t)ND_SLOT * ND_BATCH * 2;
+        ms.height = 1;
+        ok = cudaGraphAddMemsetNode(&last, g, nullptr, 0, &ms) == cudaSuccess;
+    }
+    for (int k = 0; ok && k < ND_BATCH; ++k) {
+        SweepParams P = pass_params(h, mode, P0, base, k, kind);
+        if (mode == ND_AND) {
+            cudaMemsetParams ms = {};
+            ms.dst = P.next;
+            ms.value = 0;
+            ms.elementSize = 4;
+            ms.width = (size_t)words;
+            ms.height = 1;
+            cudaGraphNode_t n = nullptr;
+            ok = cudaGraphAddMemsetNode(&n, g, &last, 1, &ms) == cudaSuccess;
+            last = n;
+        }
+        if (!ok) break;
+        cudaKernelNodeParams kp = {};
+        void* args[] = {&P};
+        kp.func = (void*)fn;
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(kThreads);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = args;
+        cudaGraphNode_t n = nullptr;
+        ok = cudaGraphAddKernelNode(&n, g, &last, 1, &kp) == cudaSuccess;
+        last = n;
+    }
+    if (ok) {
+        cudaGraphNode_t n = nullptr;
+        ok = cudaGraphAddMemcpyNode1D(&n, g, &last, 1, h->h_counters + ND_SLOT * base, h->counters + ND_SLOT * base,
+                                      sizeof(unsigned long long) * ND_SLOT * ND_BATCH,
+                                      cudaMemcpyDeviceToHost) == cudaSuccess;
+    }
+    if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+        cudaGetLastError();  // clear, and use ordinary launches instead
+        h->pass_graph_failed[mode][kind] = true;
+        return;
+    }
+    h->pass_graph[mode][kind] = ex;
+}
+
 }  // namespace
 
 nd_status nd_init_tau(nd_incidence* h, int32_t* tau, cudaStream_t st) {
@@ -489,6 +598,7 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
     ND_TRY(ensure_state(h, and_mode, st));
     h->last_changed.clear();
     h->last_evals.clear();
+    h->last_incs.clear();
     *updating = 0;
     *evals = 0;
     *converged = false;
@@ -510,7 +620,6 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
         return ND_OK;
     }
     const int64_t words = (N + 31) / 32;
-    int fc = 0;  // index of the current frontier
     if (mode == ND_AND) {
         nd_prof_scope ps("fill_front", st);
         k_fill_front<<<nd_blocks_for(words, kThreads, h->sm_count * 8), kThreads, 0, st>>>(N, h->front[0]);
@@ -523,7 +632,7 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
     plan_chunks(h, P);
     pass_fn fn = pick(h->q, mode);
     const int grid = P.chunk_end[ND_NB - 1] > 0 ? pass_grid(h, (const void*)fn, P.chunk_end[ND_NB - 1]) : 0;
-    const int kBatch = 16;
+    const int kBatch = ND_BATCH;
     // Thm. 3 / Lemma 2: SND settles within the number of degree levels, at
     // most N_R, and AND never needs more passes than SND.  A run longer than
     // N_R + 1 passes (including the pass that detects convergence) can only
@@ -531,58 +640,63 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
     const int64_t bound = N + 1;
     bool over_bound = false;
     if ((int64_t)max_passes > bound) { max_passes = (int32_t)bound; over_bound = true; }
+    const char* pname = mode == ND_SND ? "snd_pass" : (mode == ND_AND ? "and_pass" : "and_nn_pass");
     int32_t pass = 0;
+    int64_t batch = 0;
     bool done = false;
     int32_t last_written = 0;  // SND: index of the buffer holding the newest tau
     while (!done && pass < max_passes) {
+        // batch b uses counter slots [base, base + 16); its first pass reads
+        // the last slot of batch b-1 (every batch but the last is full)
         const int32_t start = pass;
-        const int slot0 = start % ND_RING;
+        const int base = (int)(batch & 1) * kBatch;
         int nb = kBatch;
         if (nb > max_passes - pass) nb = max_passes - pass;
-        if (slot0 + nb > ND_RING) nb = ND_RING - slot0;
-        ND_CUDA(cudaMemsetAsync(h->counters + ND_SLOT * slot0, 0, sizeof(unsigned long long) * ND_SLOT * nb, st));
-        for (int k = 0; k < nb; ++k, ++pass) {
-            const int slot = pass % ND_RING;
-            P.ctr = h->counters + ND_SLOT * slot;
-            P.prev = (pass == 0) ? nullptr : h->counters + ND_SLOT * ((pass - 1) % ND_RING);
-            if (and_mode) {
-                P.tin = h->tau[0];
-                P.tout = h->tau[0];
-                P.cur = h->front[fc];
-                P.next = h->front[fc ^ 1];
-                if (mode == ND_AND)
-                    ND_CUDA(cudaMemsetAsync(h->front[fc ^ 1], 0, sizeof(uint32_t) * words, st));
-                fc ^= 1;
-            } else {
-                P.tin = h->tau[pass & 1];
-                P.tout = h->tau[(pass & 1) ^ 1];
-                P.cur = nullptr;
-                P.next = nullptr;
-            }
-            if (grid > 0) {
-                nd_prof_scope ps(mode == ND_SND ? "snd_pass" : (mode == ND_AND ? "and_pass" : "and_nn_pass"), st);
-                fn<<<grid, kThreads, 0, st>>>(P);
-                ND_CUDA(cudaGetLastError());
+        const int kind = batch == 0 ? 0 : ((batch & 1) ? 2 : 1);
+        bool launched = false;
+        if (nb == kBatch && grid > 0 && !h->pass_graph_failed[mode][kind]) {
+            if (!h->pass_graph[mode][kind])
+                make_batch_graph(h, mode, kind, P, grid, fn, words);
+            if (h->pass_graph[mode][kind]) {
+                nd_prof_scope ps(pname, st, kBatch);
+                ND_CUDA(cudaGraphLaunch(h->pass_graph[mode][kind], st));
+                launched = true;
+                pass += kBatch;
             }
         }
-        ND_CUDA(cudaMemcpyAsync(h->h_counters + ND_SLOT * slot0, h->counters + ND_SLOT * slot0,
-                                sizeof(unsigned long long) * ND_SLOT * nb, cudaMemcpyDeviceToHost, st));
+        if (!launched) {
+            ND_CUDA(cudaMemsetAsync(h->counters + ND_SLOT * base, 0, sizeof(unsigned long long) * ND_SLOT * nb, st));
+            for (int k = 0; k < nb; ++k, ++pass) {
+                SweepParams Pk = pass_params(h, mode, P, base, k, kind);
+                if (mode == ND_AND)
+                    ND_CUDA(cudaMemsetAsync(Pk.next, 0, sizeof(uint32_t) * words, st));
+                if (grid > 0) {
+                    nd_prof_scope ps(pname, st);
+                    fn<<<grid, kThreads, 0, st>>>(Pk);
+                    ND_CUDA(cudaGetLastError());
+                }
+            }
+            ND_CUDA(cudaMemcpyAsync(h->h_counters + ND_SLOT * base, h->counters + ND_SLOT * base,
+                                    sizeof(unsigned long long) * ND_SLOT * nb, cudaMemcpyDeviceToHost, st));
+        }
         ND_TRY(nd_wait(st, 600.0));
         for (int k = 0; k < nb; ++k) {
             const int32_t p = start + k;
-            unsigned long long ch = h->h_counters[ND_SLOT * (slot0 + k)];
-            unsigned long long ev = h->h_counters[ND_SLOT * (slot0 + k) + 1];
+            unsigned long long ch = h->h_counters[ND_SLOT * (base + k)];
+            unsigned long long ev = h->h_counters[ND_SLOT * (base + k) + 1];
             // r-cliques with d_s = 0 are never launched: tau = H(empty) = 0 = d_s.
             // They count as evaluated in every SND / AND-nn pass and in the first
             // AND pass, as in the paper's sequential loops.
             if (mode != ND_AND || p == 0) ev += (unsigned long long)h->num_zero;
             h->last_changed.push_back((int64_t)ch);
             h->last_evals.push_back((int64_t)ev);
+            h->last_incs.push_back((int64_t)h->h_counters[ND_SLOT * (base + k) + 3]);
             *evals += (int64_t)ev;
             if (!and_mode) last_written = (p & 1) ^ 1;
             if (ch == 0) { done = true; break; }
             (*updating)++;
         }
+        ++batch;
     }
     *converged = done;
     *tau_result = and_mode ? h->tau[0] : h->tau[last_written];

@@ -36,7 +36,8 @@ struct nd_prof_scope {
     cudaStream_t st;
     cudaEvent_t a, b;
     bool on;
-    nd_prof_scope(const char* name, cudaStream_t s);
+    int count;  // kernel launches the scope covers (a graph of passes covers several)
+    nd_prof_scope(const char* name, cudaStream_t s, int launches = 1);
     ~nd_prof_scope();
 };
 
@@ -44,7 +45,10 @@ struct nd_prof_scope {
 // degree buckets for the h-index sweeps: r-cliques are grouped by d_s so that
 // each group of lanes that evaluates one r-clique is sized to its work.
 // ----------------------------------------------------------------------------
-enum { ND_NB = 4 };  // bucket 0: d_s in [1,8], 1: [9,64], 2: [65,2048], 3: > 2048
+// buckets (thresholds t0 <= 8, t1 <= 64 fit the register caches of the
+// 4- and 8-lane groups; defaults 8 / 64 / 2048, tunable per handle):
+// 0: d_s in [1,t0] (4 lanes), 1: (t0,t1] (8 lanes), 2: (t1,t2] (a warp), 3: > t2 (a CTA)
+enum { ND_NB = 4, ND_T0_MAX = 8, ND_T1_MAX = 64 };
 
 // one unit of h-index work: the r-clique and its incidence row, so that a
 // pass reaches the row with one 16-byte load instead of two dependent ones
@@ -79,17 +83,25 @@ struct nd_incidence {
     int64_t bucket_lo[ND_NB + 1] = {0, 0, 0, 0, 0};
     int64_t bucket_inc[ND_NB] = {0, 0, 0, 0};
     int64_t num_zero = 0;          // r-cliques with d_s = 0 (kappa = 0, never updated)
+    int32_t thr[3] = {8, 64, 2048};  // bucket thresholds t0, t1, t2
     // iteration state
     int32_t* tau[2] = {nullptr, nullptr};
     uint32_t* front[2] = {nullptr, nullptr};
     unsigned long long* counters = nullptr;  // ring of per-pass counters
     unsigned long long* h_counters = nullptr;  // pinned host mirror
-    std::vector<int64_t> last_changed, last_evals;
+    std::vector<int64_t> last_changed, last_evals, last_incs;
     int64_t bytes = 0;
     cudaStream_t last_stream = 0;  // stream of the latest call on this handle
+    // instantiated CUDA graphs of a full batch of passes, per mode (SND, AND,
+    // AND-nn) and batch kind (first, even, odd); built on first use
+    cudaGraphExec_t pass_graph[3][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr},
+                                        {nullptr, nullptr, nullptr}};
+    bool pass_graph_failed[3][3] = {{false, false, false}, {false, false, false}, {false, false, false}};
 };
 
-enum { ND_RING = 256, ND_SLOT = 4 };  // per-pass counter slots of ND_SLOT u64 each
+// passes are enqueued in batches of ND_BATCH; the per-pass counters (ND_SLOT
+// u64 each) live in two halves of ND_BATCH slots used by alternate batches
+enum { ND_BATCH = 16, ND_RING = 2 * ND_BATCH, ND_SLOT = 4 };
 
 // wait for a stream with a time limit (ND_E_TIMEOUT past it)
 nd_status nd_wait(cudaStream_t st, double seconds);

@@ -208,32 +208,128 @@ def hub_graph(n: int = 3000, hubs: int = 6, seed: int = 107):
     return to_csr(n, np.concatenate(src), np.concatenate(dst))
 
 
-def batch_graphs(count: int, seed: int = 4, n_lo: int = 100, n_hi: int = 50000):
+def _batch_one(args):
+    i, n, fam, seed = args
+    sd = seed * 1_000_003 + i
+    if fam == 0:
+        a, b = erdos_renyi(n, 8.0 / (n - 1), seed=sd)
+        name = "er"
+    elif fam == 1:
+        a, b = chung_lu(n, 2.2, 8.0, seed=sd)
+        name = "chunglu"
+    else:
+        scale = max(1, int(np.ceil(np.log2(n))))
+        _, a, b = rmat(scale, 8, seed=sd, n_limit=n)
+        name = "rmat"
+    rp, col = to_csr(n, a, b)
+    return rp, col, name
+
+
+def batch_graphs(count: int, seed: int = 4, n_lo: int = 100, n_hi: int = 50000, workers: int = 1):
     """Independent graphs for batched runs: n uniform in [n_lo, n_hi]; each
     graph is, with probability 1/3 each, Erdos-Renyi with mean degree 8,
     Chung-Lu with exponent 2.2 and mean degree 8, or R-MAT with edge factor 8
     at scale ceil(log2 n) keeping only endpoints below n.  Graph i uses seed
-    seed*1_000_003 + i.  Returns a list of (row_ptr, col, family)."""
-    out = []
+    seed*1_000_003 + i, so the list does not depend on `workers` (processes
+    started with spawn).  Returns a list of (row_ptr, col, family)."""
     rng = _rng(seed)
     ns = rng.integers(n_lo, n_hi + 1, size=count)
     fam = rng.integers(0, 3, size=count)
-    for i in range(count):
-        n = int(ns[i])
-        sd = seed * 1_000_003 + i
-        if fam[i] == 0:
-            a, b = erdos_renyi(n, 8.0 / (n - 1), seed=sd)
-            name = "er"
-        elif fam[i] == 1:
-            a, b = chung_lu(n, 2.2, 8.0, seed=sd)
-            name = "chunglu"
-        else:
-            scale = max(1, int(np.ceil(np.log2(n))))
-            _, a, b = rmat(scale, 8, seed=sd, n_limit=n)
-            name = "rmat"
-        rp, col = to_csr(n, a, b)
-        out.append((rp, col, name))
-    return out
+    jobs = [(i, int(ns[i]), int(fam[i]), seed) for i in range(count)]
+    if workers <= 1 or count < 2 * workers:
+        return [_batch_one(j) for j in jobs]
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_batch_one, jobs, chunksize=max(1, count // (8 * workers))))
+
+
+# ---------------------------------------------------------------------------
+# Large R-MAT graphs, generated with torch on any device.  The random numbers
+# come from a counter-based hash (SplitMix64's finaliser applied to
+# seed * 2**40 + sample * 64 + level), so the same graph comes out on the CPU
+# and on a GPU.  Quadrants are chosen by integer comparison of the hash's top
+# 53 bits with floor(p * 2**53); vertex labels are scrambled by the bijection
+# v -> (v * 0x9E3779B97F4A7C15 + seed) mod 2**scale (odd multiplier).
+# ---------------------------------------------------------------------------
+_M64 = (1 << 64) - 1
+
+
+def _to_i64(x: int) -> int:
+    x &= _M64
+    return x - (1 << 64) if x >= (1 << 63) else x
+
+
+def _srl(t, k: int):
+    """Logical right shift of an int64 tensor holding 64-bit patterns."""
+    import torch
+    return (t >> k) & torch.tensor(_to_i64((1 << (64 - k)) - 1), dtype=torch.int64, device=t.device)
+
+
+def _splitmix(t):
+    import torch
+    c1 = torch.tensor(_to_i64(0xBF58476D1CE4E5B9), dtype=torch.int64, device=t.device)
+    c2 = torch.tensor(_to_i64(0x94D049BB133111EB), dtype=torch.int64, device=t.device)
+    t = t ^ _srl(t, 30)
+    t = t * c1
+    t = t ^ _srl(t, 27)
+    t = t * c2
+    return t ^ _srl(t, 31)
+
+
+def rmat_torch(scale: int, edge_factor: int, seed: int, abcd=(0.57, 0.19, 0.19, 0.05), device="cpu",
+               chunk: int = 1 << 26):
+    """R-MAT samples as torch int64 (src, dst) on `device`; see the notes above."""
+    import torch
+    a, b, c, _ = abcd
+    th_a = int(a * (1 << 53))
+    th_ab = int((a + b) * (1 << 53))
+    th_abc = int((a + b + c) * (1 << 53))
+    ne = edge_factor * (1 << scale)
+    n = 1 << scale
+    src = torch.empty(ne, dtype=torch.int64, device=device)
+    dst = torch.empty(ne, dtype=torch.int64, device=device)
+    mult = torch.tensor(_to_i64(0x9E3779B97F4A7C15), dtype=torch.int64, device=device)
+    for lo in range(0, ne, chunk):
+        hi = min(ne, lo + chunk)
+        idx = torch.arange(lo, hi, dtype=torch.int64, device=device)
+        s_ = torch.zeros(hi - lo, dtype=torch.int64, device=device)
+        d_ = torch.zeros(hi - lo, dtype=torch.int64, device=device)
+        for level in range(scale):
+            key = idx * 64 + level + seed * (1 << 40)
+            r = _srl(_splitmix(key), 11)  # 53 bits
+            sbit = (r >= th_ab).to(torch.int64)
+            tbit = (((r >= th_a) & (r < th_ab)) | (r >= th_abc)).to(torch.int64)
+            s_ |= sbit << level
+            d_ |= tbit << level
+        src[lo:hi] = (s_ * mult + seed) & (n - 1)
+        dst[lo:hi] = (d_ * mult + seed) & (n - 1)
+    return n, src, dst
+
+
+def to_csr_torch(n: int, src, dst):
+    """to_csr on torch tensors (any device): simple, symmetric, sorted CSR
+    as (row_ptr int64[n+1], col int32[nnz]) on the same device."""
+    import torch
+    keep = src != dst
+    lo = torch.minimum(src[keep], dst[keep])
+    hi = torch.maximum(src[keep], dst[keep])
+    del keep
+    key = torch.unique(lo * n + hi)  # sorted
+    del lo, hi
+    u = torch.cat([key // n, key % n])
+    v = torch.cat([key % n, key // n])
+    del key
+    key2, _ = torch.sort(u * n + v)
+    del u, v
+    row = key2 // n
+    col = (key2 % n).to(torch.int32)
+    del key2
+    counts = torch.bincount(row, minlength=n)
+    del row
+    row_ptr = torch.zeros(n + 1, dtype=torch.int64, device=col.device)
+    row_ptr[1:] = torch.cumsum(counts, 0)
+    return row_ptr, col
 
 
 def graph_from_edges(n: int, edges):
@@ -296,6 +392,18 @@ def workload(name: str):
         return dict(name=name, r=2, s=3, row_ptr=rp, col=col,
                     recipe=f"R-MAT scale {scale} edge factor {ef} (0.57,0.19,0.19,0.05) seed 2, "
                            "symmetrised, deduplicated, no loops; k-truss (2,3)")
+    if name.startswith("rmat_core_s") and "_ef" in name:
+        # rmat_core_s{scale}_ef{ef}: k-core of a large R-MAT graph, generated with torch
+        # (on the GPU when one is present, else on the CPU); arrays stay torch tensors
+        import torch
+        scale = int(name.split("_s")[1].split("_")[0])
+        ef = int(name.split("_ef")[1].split("_")[0])
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        n, src, dst = rmat_torch(scale, ef, seed=5, device=dev)
+        rp, col = to_csr_torch(n, src, dst)
+        return dict(name=name, r=1, s=2, row_ptr=rp, col=col,
+                    recipe=f"R-MAT scale {scale} edge factor {ef} (0.57,0.19,0.19,0.05), counter-based "
+                           "generator seed 5, symmetrised, deduplicated, no loops; k-core (1,2)")
     if name.startswith("chunglu_n") and "_planted" in name:
         # chunglu_n{n}_g2.1_d20_planted{count}
         n = int(name.split("_n")[1].split("_")[0])

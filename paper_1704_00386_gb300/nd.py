@@ -26,7 +26,7 @@ MODES = {"snd": ND_SND, "and": ND_AND, "and_nn": ND_AND_NN}
 
 SYMBOLS = ["nd_build_incidence", "nd_build_incidence_batch", "nd_incidence_info", "nd_r_cliques", "nd_s_degree", "nd_snd",
            "nd_and", "nd_iterate_k", "nd_truss_classic", "nd_prof_enable", "nd_prof_read",
-           "nd_last_passes", "nd_incidence_bytes", "nd_free", "nd_strerror", "nd_last_error",
+           "nd_last_passes", "nd_autotune", "nd_incidence_bytes", "nd_free", "nd_strerror", "nd_last_error",
            "nd_abi_version", "nd_core_snd_noalloc"]
 
 _lock = threading.Lock()
@@ -73,7 +73,8 @@ def load(build_if_missing: bool = True):
         lib.nd_truss_classic.argtypes = [vp, i64, vp, ci, vp]
         lib.nd_prof_enable.argtypes = [ci]
         lib.nd_prof_read.argtypes = [ci, P(ctypes.c_char_p), P(i64), P(ctypes.c_double)]
-        lib.nd_last_passes.argtypes = [vp, vp, vp, i32, P(i32)]
+        lib.nd_last_passes.argtypes = [vp, vp, vp, vp, i32, P(i32)]
+        lib.nd_autotune.argtypes = [vp, i32, vp, vp, P(ctypes.c_double)]
         lib.nd_incidence_bytes.argtypes = [vp, P(i64)]
         lib.nd_core_snd_noalloc.argtypes = [vp, vp, i64, i64, vp, i32, P(i32), vp]
         lib.nd_free.argtypes = [vp]
@@ -208,15 +209,28 @@ class Incidence:
                "nd_iterate_k")
         return buf, up.value
 
-    def last_passes(self):
-        """(changed, evaluated) per pass of the last iteration call."""
+    def autotune(self, passes: int = 2, stream=None):
+        """nd_autotune: pick the fastest bucket thresholds for this handle (and
+        cache them for later builds of the same size class).
+        Returns ((t0, t1, t2), ms of `passes` SND passes with them)."""
+        thr = np.zeros(3, np.int32)
+        ms = ctypes.c_double()
+        _check(load().nd_autotune(self._h, int(passes), self._sp(stream), _ptr(thr), ctypes.byref(ms)),
+               "nd_autotune")
+        return tuple(int(x) for x in thr), ms.value
+
+    def last_passes(self, with_incidences: bool = False):
+        """(changed, evaluated[, incidences]) per pass of the last iteration call."""
         lib = load()
         n = ctypes.c_int32()
-        _check(lib.nd_last_passes(self._h, None, None, 0, ctypes.byref(n)), "nd_last_passes")
+        _check(lib.nd_last_passes(self._h, None, None, None, 0, ctypes.byref(n)), "nd_last_passes")
         ch = np.zeros(max(n.value, 1), np.int64)
         ev = np.zeros(max(n.value, 1), np.int64)
-        _check(lib.nd_last_passes(self._h, _ptr(ch), _ptr(ev), n.value, ctypes.byref(n)),
+        inc = np.zeros(max(n.value, 1), np.int64)
+        _check(lib.nd_last_passes(self._h, _ptr(ch), _ptr(ev), _ptr(inc), n.value, ctypes.byref(n)),
                "nd_last_passes")
+        if with_incidences:
+            return ch[:n.value], ev[:n.value], inc[:n.value]
         return ch[:n.value], ev[:n.value]
 
 

@@ -188,3 +188,19 @@ def test_malformed_graph_rejected(nd, bad):
 def test_classic_truss_device(nd):
     k = torch.tensor([0, 3, 7], dtype=torch.int32, device="cuda")
     assert nd.truss_classic(k).cpu().tolist() == [2, 5, 9]
+
+
+def test_autotune_changes_speed_not_results(nd):
+    rp, col = CASES["hubs3000"]
+    for r, s in RS:
+        inc = nd.build_incidence(rp, col, r, s)
+        want, iters = inc.snd()
+        thr, ms = inc.autotune(passes=2)
+        assert thr[0] in (4, 8) and thr[1] in (32, 64) and thr[2] in (256, 1024, 2048, 8192)
+        assert ms > 0
+        got, iters2 = inc.snd()
+        np.testing.assert_array_equal(got, want)
+        assert iters2 == iters
+        np.testing.assert_array_equal(inc.and_()[0], want)
+        again = nd.build_incidence(rp, col, r, s)   # starts from the cached thresholds
+        np.testing.assert_array_equal(again.snd()[0], want)
