@@ -135,6 +135,33 @@ nd_status nd_and(nd_incidence* inc, int32_t* tau_out, int on_device, int notify,
 nd_status nd_iterate_k(nd_incidence* inc, int mode, int32_t k, int32_t* tau_inout,
                        int tau_init_given, int on_device, int32_t* updating_out, void* stream);
 
+/* PartialAnd (end of Section 4.3; the ego-network queries of Section 5.4):
+ * AND with notification restricted to the member set P, given as `count`
+ * r-clique ids (host or device per on_device).  Only members start active
+ * and only members are ever notified; every other r-clique keeps d_s.  The
+ * result is the greatest fixed point of the restricted update below d_s, the
+ * same for any processing order, with kappa_s <= tau (equal to kappa_s when P
+ * holds every r-clique).  An id >= num_r gives ND_E_INVAL.  tau_out: num_r
+ * int32.  Synchronises `stream`. */
+nd_status nd_and_partial(nd_incidence* inc, const uint32_t* members, int64_t count, int on_device,
+                         int32_t* tau_out, int32_t max_iters, int32_t* iters_out, int64_t* evals_out,
+                         void* stream);
+
+/* AND with notification and the active-ratio stopping rule of Section 5.2
+ * (Fig. 9): stop after the first pass that evaluated fewer than
+ * active_ratio * num_r r-cliques (the paper's 40% and 10% settings are 0.4
+ * and 0.1), or at convergence.  *stopped_out = 1 if the rule ended the run.
+ * tau_out then holds kappa_s <= tau <= d_s.  Synchronises `stream`. */
+nd_status nd_and_until(nd_incidence* inc, double active_ratio, int32_t* tau_out, int on_device,
+                       int32_t max_iters, int32_t* iters_out, int64_t* evals_out, int* stopped_out,
+                       void* stream);
+
+/* Number of positions where a[i] == b[i] over n int32 values (host or device
+ * per on_device): the accuracy of an early-stopped tau against kappa_s
+ * (Section 5.2, "accuracy").  Synchronises `stream`. */
+nd_status nd_count_equal(const int32_t* a, const int32_t* b, int64_t n, int on_device, int64_t* equal_out,
+                         void* stream);
+
 /* Classic truss numbers (Cohen's k-2 convention) from kappa_3: out = in + 2
  * for every edge.  Host or device per on_device. */
 nd_status nd_truss_classic(const int32_t* kappa3, int64_t num_edges, int32_t* out, int on_device,

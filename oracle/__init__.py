@@ -67,6 +67,8 @@ def _load():
         lib.orc_peel.argtypes = [vp, vp]
         lib.orc_snd.argtypes = [vp, vp, ctypes.c_int, i32, vp, vp, vp]
         lib.orc_and.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int, i32, vp, vp, vp]
+        lib.orc_and_partial.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int, vp, i32, vp, vp, vp]
+        lib.orc_snd_partial.argtypes = [vp, vp, ctypes.c_int, vp, i32, vp]
         lib.orc_degree_levels.argtypes = [vp, vp]
         lib.orc_degree_levels.restype = i32
         _lib = lib
@@ -171,6 +173,28 @@ class Graph:
                                  None if o is None else _ptr(o), int(notify), max_sweeps,
                                  ctypes.byref(sw), ctypes.byref(up), ctypes.byref(ev)))
         return t, sw.value, up.value, ev.value
+
+    def partial_and(self, members, notify: bool = True, order=None, max_sweeps: int = 1 << 30):
+        """PartialAnd (end of Section 4.3): AND restricted to the member set P
+        (a boolean mask over r-cliques).  Returns (tau, sweeps, updating, evaluations)."""
+        m = np.ascontiguousarray(np.asarray(members, dtype=bool).astype(np.int8))
+        if m.size != self.num_r:
+            raise ValueError("members must be a mask over the r-cliques")
+        t = np.zeros(self.num_r, dtype=np.int32)
+        o = None if order is None else np.ascontiguousarray(np.asarray(order, dtype=np.int64))
+        sw, up, ev = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(self._lib.orc_and_partial(self._h, _ptr(t), 1, None if o is None else _ptr(o), int(notify),
+                                         _ptr(m), max_sweeps, ctypes.byref(sw), ctypes.byref(up),
+                                         ctypes.byref(ev)))
+        return t, sw.value, up.value, ev.value
+
+    def partial_snd(self, members, max_sweeps: int = 1 << 30):
+        """SND restricted to the member set (synchronous counterpart used as a pin)."""
+        m = np.ascontiguousarray(np.asarray(members, dtype=bool).astype(np.int8))
+        t = np.zeros(self.num_r, dtype=np.int32)
+        sw = ctypes.c_int32()
+        _check(self._lib.orc_snd_partial(self._h, _ptr(t), 1, _ptr(m), max_sweeps, ctypes.byref(sw)))
+        return t, sw.value
 
     def degree_levels(self):
         """Degree levels, Def. 5.  Returns (number of levels, level of each R)."""

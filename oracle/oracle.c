@@ -436,22 +436,28 @@ out:
 }
 
 /* AND, Alg. 3: in-place updates in the given order (NULL = id order); with
- * notify, only notified r-cliques are recomputed (Section 4.3). */
-int orc_and(const orc_ctx *c, int32_t *tau, int init_from_ds, const int64_t *order, int notify,
-            int32_t max_sweeps, int32_t *sweeps_out, int32_t *updating_out, int64_t *evals_out) {
+ * notify, only notified r-cliques are recomputed (Section 4.3).  PartialAnd
+ * (end of Section 4.3) is the same loop restricted to a member set P
+ * (members[R] != 0): only members start active, only members are ever
+ * notified, and non-members keep their initial tau.  members = NULL means
+ * every r-clique is a member. */
+int orc_and_partial(const orc_ctx *c, int32_t *tau, int init_from_ds, const int64_t *order, int notify,
+                    const char *members, int32_t max_sweeps, int32_t *sweeps_out, int32_t *updating_out,
+                    int64_t *evals_out) {
     int st = init_tau(c, tau, init_from_ds);
     if (st) return st;
     int64_t N = c->num_r;
     int32_t *L = (int32_t *)malloc(sizeof(int32_t) * (max_ds(c) + 1));
     char *act = (char *)malloc((size_t)N + 1);
     if (!L || !act) { free(L); free(act); return ORC_E_NOMEM; }
-    memset(act, 1, (size_t)N + 1);
+    for (int64_t R = 0; R < N; ++R) act[R] = members ? (members[R] != 0) : 1;
     int32_t sweeps = 0, updating = 0;
     int64_t evals = 0;
     while (sweeps < max_sweeps) {
         int flag = 0;
         for (int64_t i = 0; i < N; ++i) {
             int64_t R = order ? order[i] : i;
+            if (members && !members[R]) continue;
             if (notify) {
                 if (!act[R]) continue;
                 act[R] = 0;
@@ -465,7 +471,7 @@ int orc_and(const orc_ctx *c, int32_t *tau, int init_from_ds, const int64_t *ord
                     for (int64_t j = c->inc_off[R]; j < c->inc_off[R + 1]; ++j)
                         for (int k = 0; k < c->q; ++k) {
                             int32_t Rp = c->inc[j * c->q + k];
-                            if (h <= tau[Rp]) act[Rp] = 1;
+                            if (h <= tau[Rp] && (!members || members[Rp])) act[Rp] = 1;
                         }
                 }
                 tau[R] = h;
@@ -480,6 +486,44 @@ out:
     if (updating_out) *updating_out = updating;
     if (evals_out) *evals_out = evals;
     free(L); free(act);
+    return st;
+}
+
+int orc_and(const orc_ctx *c, int32_t *tau, int init_from_ds, const int64_t *order, int notify,
+            int32_t max_sweeps, int32_t *sweeps_out, int32_t *updating_out, int64_t *evals_out) {
+    return orc_and_partial(c, tau, init_from_ds, order, notify, NULL, max_sweeps, sweeps_out, updating_out,
+                           evals_out);
+}
+
+/* SND restricted to a member set: members are updated synchronously from the
+ * previous pass (Alg. 2), non-members keep their tau.  Used to pin PartialAnd:
+ * both iterate a monotone operator down from the same start, so they reach
+ * the same (greatest) fixed point. */
+int orc_snd_partial(const orc_ctx *c, int32_t *tau, int init_from_ds, const char *members, int32_t max_sweeps,
+                    int32_t *sweeps_out) {
+    int st = init_tau(c, tau, init_from_ds);
+    if (st) return st;
+    int64_t N = c->num_r;
+    int32_t *tp = (int32_t *)malloc(sizeof(int32_t) * (N + 1));
+    int32_t *L = (int32_t *)malloc(sizeof(int32_t) * (max_ds(c) + 1));
+    if (!tp || !L) { free(tp); free(L); return ORC_E_NOMEM; }
+    int32_t sweeps = 0;
+    while (sweeps < max_sweeps) {
+        int flag = 0;
+        memcpy(tp, tau, sizeof(int32_t) * N);
+        for (int64_t R = 0; R < N; ++R) {
+            if (!members[R]) continue;
+            int32_t h = update_one(c, R, tp, L);
+            if (h > tp[R]) { st = ORC_E_THM1; goto out; }
+            if (h != tp[R]) flag = 1;
+            tau[R] = h;
+        }
+        sweeps++;
+        if (!flag) break;
+    }
+out:
+    if (sweeps_out) *sweeps_out = sweeps;
+    free(tp); free(L);
     return st;
 }
 

@@ -292,12 +292,12 @@ nd_status nd_build_incidence_batch(const nd_csr* graphs, int count, int r, int s
         voff[i + 1] = n;
     }
     if (n >= INT32_MAX) { nd_set_error("batch has more than 2^31-1 vertices"); return ND_E_TOO_LARGE; }
-    int64_t* urp = nullptr;
-    int32_t* ucol = nullptr;
+    nd_tmp<int64_t> urp(st);
+    nd_tmp<int32_t> ucol(st);
     nd_status rc = ND_OK;
     if (on_device) {
-        ND_CUDA(cudaMallocAsync((void**)&urp, sizeof(int64_t) * (n + 1), st));
-        ND_CUDA(cudaMallocAsync((void**)&ucol, sizeof(int32_t) * (nnz > 0 ? nnz : 1), st));
+        ND_TRY(urp.alloc(n + 1));
+        ND_TRY(ucol.alloc(nnz));
         rc = nd_union_device(parts.data(), count, n, nnz, urp, ucol, st);
     } else {
         // host graphs: assemble the union on the host and copy it once
@@ -326,8 +326,6 @@ nd_status nd_build_incidence_batch(const nd_csr* graphs, int count, int r, int s
         nd_csr u{n, nnz, urp, ucol, 1};
         rc = build_common(&u, r, s, st, out);
     }
-    cudaFreeAsync(urp, st);
-    cudaFreeAsync(ucol, st);
     if (rc == ND_OK && r_offsets) rc = nd_batch_offsets(*out, voff.data(), count, r_offsets, st);
     if (rc != ND_OK && *out) { nd_free(*out); *out = nullptr; }
     return rc;
@@ -364,12 +362,10 @@ nd_status nd_r_cliques(const nd_incidence* h, int32_t* out, int on_device, void*
     const int64_t count = h->num_r * h->r;
     if (count == 0) return ND_OK;
     if (on_device) return nd_write_r_cliques(h, out, st);
-    int32_t* tmp = nullptr;
-    ND_CUDA(cudaMallocAsync((void**)&tmp, sizeof(int32_t) * count, st));
-    nd_status s = nd_write_r_cliques(h, tmp, st);
-    if (s == ND_OK) s = deliver(tmp, count, out, 0, st);
-    cudaFreeAsync(tmp, st);
-    return s;
+    nd_tmp<int32_t> tmp(st);
+    ND_TRY(tmp.alloc(count));
+    ND_TRY(nd_write_r_cliques(h, tmp, st));
+    return deliver(tmp, count, out, 0, st);
 }
 
 nd_status nd_s_degree(const nd_incidence* h, int32_t* out, int on_device, void* stream) {
@@ -378,30 +374,28 @@ nd_status nd_s_degree(const nd_incidence* h, int32_t* out, int on_device, void* 
     const_cast<nd_incidence*>(h)->last_stream = st;
     if (h->num_r == 0) return ND_OK;
     if (on_device) return nd_init_tau(const_cast<nd_incidence*>(h), out, st);
-    int32_t* tmp = nullptr;
-    ND_CUDA(cudaMallocAsync((void**)&tmp, sizeof(int32_t) * h->num_r, st));
-    nd_status s = nd_init_tau(const_cast<nd_incidence*>(h), tmp, st);
-    if (s == ND_OK) s = deliver(tmp, h->num_r, out, 0, st);
-    cudaFreeAsync(tmp, st);
-    return s;
+    nd_tmp<int32_t> tmp(st);
+    ND_TRY(tmp.alloc(h->num_r));
+    ND_TRY(nd_init_tau(const_cast<nd_incidence*>(h), tmp, st));
+    return deliver(tmp, h->num_r, out, 0, st);
 }
 
 static nd_status run_and_deliver(nd_incidence* h, int mode, int32_t max_passes, const int32_t* tau_in,
                                  int tau_in_on_device, int32_t* tau_out, int on_device,
                                  int32_t* iters_out, int64_t* evals_out, bool require_convergence,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, nd_run_opts* opts = nullptr) {
     if (!h) { nd_set_error("handle is NULL"); return ND_E_INVAL; }
     if (!tau_out && h->num_r > 0) { nd_set_error("tau_out is NULL"); return ND_E_INVAL; }
     if (mode != ND_SND && mode != ND_AND && mode != ND_AND_NN) { nd_set_error("bad mode"); return ND_E_INVAL; }
     if (max_passes < 0) { nd_set_error("negative iteration cap"); return ND_E_INVAL; }
     h->last_stream = st;
     const int32_t* tin_dev = nullptr;
-    int32_t* staged = nullptr;
+    nd_tmp<int32_t> staged(st);
     if (tau_in && h->num_r > 0) {
         if (tau_in_on_device) {
             tin_dev = tau_in;
         } else {
-            ND_CUDA(cudaMallocAsync((void**)&staged, sizeof(int32_t) * h->num_r, st));
+            ND_TRY(staged.alloc(h->num_r));
             ND_CUDA(cudaMemcpyAsync(staged, tau_in, sizeof(int32_t) * h->num_r, cudaMemcpyHostToDevice, st));
             tin_dev = staged;
         }
@@ -410,15 +404,14 @@ static nd_status run_and_deliver(nd_incidence* h, int mode, int32_t max_passes, 
     int32_t updating = 0;
     int64_t evals = 0;
     bool converged = false;
-    nd_status s = nd_run(h, mode, max_passes, tin_dev, &result, &updating, &evals, &converged, st);
-    if (staged) cudaFreeAsync(staged, st);
+    nd_status s = nd_run(h, mode, max_passes, tin_dev, &result, &updating, &evals, &converged, st, opts);
     if (s != ND_OK) return s;
     s = deliver(result, h->num_r, tau_out, on_device, st);
     if (s != ND_OK) return s;
     if (on_device) ND_TRY(host_wait(st));
     if (iters_out) *iters_out = updating;
     if (evals_out) *evals_out = evals;
-    if (require_convergence && !converged) {
+    if (require_convergence && !converged && !(opts && opts->stopped)) {
         nd_set_error("iteration cap reached before a pass without change");
         return ND_E_NOT_CONVERGED;
     }
@@ -442,6 +435,73 @@ nd_status nd_iterate_k(nd_incidence* h, int mode, int32_t k, int32_t* tau_inout,
     if (k < 0) { nd_set_error("negative k"); return ND_E_INVAL; }
     return run_and_deliver(h, mode, k, tau_init_given ? tau_inout : nullptr, on_device, tau_inout,
                            on_device, updating_out, nullptr, false, (cudaStream_t)stream);
+}
+
+nd_status nd_and_partial(nd_incidence* h, const uint32_t* members, int64_t count, int on_device,
+                         int32_t* tau_out, int32_t max_iters, int32_t* iters_out, int64_t* evals_out,
+                         void* stream) {
+    if (!h) { nd_set_error("handle is NULL"); return ND_E_INVAL; }
+    if (count < 0 || (count > 0 && !members)) { nd_set_error("bad member list"); return ND_E_INVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    h->last_stream = st;
+    const int64_t words = (h->num_r + 31) / 32;
+    nd_tmp<uint32_t> mask(st), staged(st);
+    nd_tmp<int> derr(st);
+    ND_TRY(mask.alloc(words));
+    ND_TRY(derr.alloc(1));
+    ND_CUDA(cudaMemsetAsync(mask, 0, sizeof(uint32_t) * (words > 0 ? words : 1), st));
+    ND_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
+    const uint32_t* ids = members;
+    if (count > 0 && !on_device) {
+        ND_TRY(staged.alloc(count));
+        ND_CUDA(cudaMemcpyAsync(staged, members, sizeof(uint32_t) * count, cudaMemcpyHostToDevice, st));
+        ids = staged;
+    }
+    ND_TRY(nd_member_mask(ids, count, h->num_r, mask, derr, st));
+    int herr = 0;
+    ND_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ND_CUDA(cudaStreamSynchronize(st));
+    if (herr) { nd_set_error("a member id is not an r-clique id"); return ND_E_INVAL; }
+    nd_run_opts opts;
+    opts.members = mask;
+    return run_and_deliver(h, ND_AND, max_iters, nullptr, 0, tau_out, on_device, iters_out, evals_out, true, st,
+                           &opts);
+}
+
+nd_status nd_and_until(nd_incidence* h, double active_ratio, int32_t* tau_out, int on_device, int32_t max_iters,
+                       int32_t* iters_out, int64_t* evals_out, int* stopped_out, void* stream) {
+    if (!h) { nd_set_error("handle is NULL"); return ND_E_INVAL; }
+    if (!(active_ratio >= 0.0 && active_ratio <= 1.0)) { nd_set_error("active_ratio must be in [0,1]"); return ND_E_INVAL; }
+    nd_run_opts opts;
+    opts.stop_active = active_ratio;
+    nd_status rc = run_and_deliver(h, ND_AND, max_iters, nullptr, 0, tau_out, on_device, iters_out, evals_out,
+                                   true, (cudaStream_t)stream, &opts);
+    if (stopped_out) *stopped_out = opts.stopped ? 1 : 0;
+    return rc;
+}
+
+nd_status nd_count_equal(const int32_t* a, const int32_t* b, int64_t n, int on_device, int64_t* equal_out,
+                         void* stream) {
+    if (n < 0 || !equal_out || (n > 0 && (!a || !b))) { nd_set_error("bad arguments"); return ND_E_INVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int32_t *da = a, *db = b;
+    nd_tmp<int32_t> sa(st), sb(st);
+    nd_tmp<unsigned long long> dout(st);
+    ND_TRY(dout.alloc(1));
+    if (!on_device && n > 0) {
+        ND_TRY(sa.alloc(n));
+        ND_TRY(sb.alloc(n));
+        ND_CUDA(cudaMemcpyAsync(sa, a, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+        ND_CUDA(cudaMemcpyAsync(sb, b, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+        da = sa;
+        db = sb;
+    }
+    ND_TRY(nd_count_equal_dev(da, db, n, dout, st));
+    unsigned long long hv = 0;
+    ND_CUDA(cudaMemcpyAsync(&hv, dout, sizeof(hv), cudaMemcpyDeviceToHost, st));
+    ND_CUDA(cudaStreamSynchronize(st));
+    *equal_out = (int64_t)hv;
+    return ND_OK;
 }
 
 nd_status nd_truss_classic(const int32_t* kappa3, int64_t num_edges, int32_t* out, int on_device,

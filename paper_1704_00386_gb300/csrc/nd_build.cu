@@ -254,80 +254,159 @@ __global__ void k_triangle_list(int64_t m, const int64_t* __restrict__ rp,
     }
 }
 
-// id of triangle {a, b, x} where a < b are two vertices of the current
-// triangle, pa / pb the positions of x in rows a / b and e_ab the id of edge
-// (a,b).  Sorted, the triangle's smallest edge is (x,a) if x < a, (a,x) if
-// a < x < b, and (a,b) if x > b; its third vertex is b, b, x.
-__device__ __forceinline__ uint32_t tri_lookup(int32_t a, int32_t b, int32_t x, int64_t pa,
-                                               uint32_t e_ab, const uint32_t* __restrict__ eid,
-                                               const int64_t* __restrict__ tri_ptr,
-                                               const int32_t* __restrict__ tri_w, bool* ok) {
+// ---- (3,4): 4-cliques by degree orientation ---------------------------------
+// Every 4-clique {a,b,w,x} with a before b before w before x (degree order) is
+// found exactly once, as x in out(a) /\ out(b) /\ out(w) for the oriented
+// triangle (a,b,w).  Its four triangles get their canonical ids (lexicographic
+// u<v<w, grouped by edge (u,v) in tri_ptr / tri_w) from one binary search
+// each, because the six edge ids are known from the out-lists.  The 4-cliques
+// are listed once (4 triangle ids each), then scattered into the incidence
+// rows through per-triangle cursors; row order is therefore unspecified.
+
+struct otri {  // oriented triangle a -> b -> w and its edge ids
+    int32_t a, b, w;
+    uint32_t e_ab, e_aw, e_bw;
+};
+
+// one warp per oriented edge a -> b: the oriented triangles (a, b, w)
+template <bool FILL>
+__global__ void k_otri(int64_t m, const int64_t* __restrict__ out_ptr, const int32_t* __restrict__ out_col,
+                       const uint32_t* __restrict__ out_eid, const int32_t* __restrict__ out_src,
+                       int64_t* __restrict__ ptr, otri* __restrict__ tris) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t k = warp_id_global(); k < m; k += warp_count_global()) {
+        const int32_t a = out_src[k], b = out_col[k];
+        const uint32_t e_ab = out_eid[k];
+        int64_t ab = out_ptr[a], ae = out_ptr[a + 1], bb = out_ptr[b], be = out_ptr[b + 1];
+        bool a_is_a = true;
+        if (ae - ab > be - bb) {
+            int64_t t = ab; ab = bb; bb = t; t = ae; ae = be; be = t;
+            a_is_a = false;
+        }
+        const int64_t out = FILL ? ptr[k] : 0;
+        int64_t cnt = 0, lo = bb;
+        for (int64_t base = ab; base < ae; base += 32) {
+            const int64_t p = base + lane;
+            bool found = false;
+            int64_t pb = 0;
+            int32_t x = 0;
+            if (p < ae) {
+                x = __ldg(out_col + p);
+                pb = lower_bound_i32(out_col, lo, be, x);
+                found = (pb < be) && (__ldg(out_col + pb) == x);
+            }
+            const unsigned bal = __ballot_sync(kFull, found);
+            if (FILL && found) {
+                const uint32_t e1 = __ldg(out_eid + p), e2 = __ldg(out_eid + pb);
+                otri t;
+                t.a = a; t.b = b; t.w = x; t.e_ab = e_ab;
+                t.e_aw = a_is_a ? e1 : e2;
+                t.e_bw = a_is_a ? e2 : e1;
+                tris[out + cnt + __popc(bal & lanemask_lt())] = t;
+            }
+            cnt += __popc(bal);
+            const int64_t last_pb = __shfl_sync(kFull, pb, 31);
+            if (base + 32 <= ae) lo = last_pb;
+        }
+        if (!FILL && lane == 0) ptr[k] = cnt;
+    }
+}
+
+// canonical id of the triangle on vertices p, q, r with edge ids epq, epr, eqr
+__device__ __forceinline__ uint32_t canon_tri(int32_t p, int32_t q, int32_t r, uint32_t epq, uint32_t epr,
+                                              uint32_t eqr, const int64_t* __restrict__ tri_ptr,
+                                              const int32_t* __restrict__ tri_w, bool* ok) {
+    // the smallest two vertex ids own the triangle; the largest is its third vertex
     uint32_t edge;
     int32_t third;
-    if (x < b) { edge = __ldg(eid + pa); third = b; }
-    else { edge = e_ab; third = x; }
-    (void)a;
-    int64_t lo = __ldg(tri_ptr + edge), hi = __ldg(tri_ptr + edge + 1);
-    int64_t pos = lower_bound_i32(tri_w, lo, hi, third);
+    if (p > q && p > r) { edge = eqr; third = p; }
+    else if (q > r) { edge = epr; third = q; }
+    else { edge = epq; third = r; }
+    const int64_t lo = __ldg(tri_ptr + edge), hi = __ldg(tri_ptr + edge + 1);
+    const int64_t pos = lower_bound_i32(tri_w, lo, hi, third);
     if (pos >= hi || __ldg(tri_w + pos) != third) { *ok = false; return 0; }
     return (uint32_t)pos;
 }
 
-// ---- (3,4) step 2: 4-cliques of every triangle (one warp per triangle) -----
-template <bool FILL>
-__global__ void k_triangle_k4(int64_t T, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                              const uint32_t* __restrict__ eid, const int32_t* __restrict__ e_u,
-                              const int32_t* __restrict__ e_v, const int64_t* __restrict__ tri_ptr,
-                              const int32_t* __restrict__ tri_w, const uint32_t* __restrict__ tri_e,
-                              int64_t* __restrict__ ptr, uint32_t* __restrict__ inc,
-                              int* __restrict__ err) {
+// one warp per oriented triangle: x in out(a) /\ out(b) /\ out(w).
+// MODE 0 counts the 4-cliques of the triangle into ptr[t]; MODE 1 writes
+// their four canonical triangle ids at ptr[t] (scanned) and counts the
+// incidences of each triangle in rowcnt.
+template <int MODE>
+__global__ void k_k4(int64_t T, const otri* __restrict__ tris, const int64_t* __restrict__ out_ptr,
+                     const int32_t* __restrict__ out_col, const uint32_t* __restrict__ out_eid,
+                     const int64_t* __restrict__ tri_ptr, const int32_t* __restrict__ tri_w,
+                     int64_t* __restrict__ ptr, uint4* __restrict__ k4, unsigned long long* __restrict__ rowcnt,
+                     int* __restrict__ err) {
     const int lane = threadIdx.x & 31;
     for (int64_t t = warp_id_global(); t < T; t += warp_count_global()) {
-        const uint32_t e = tri_e[t];
-        const int32_t vtx[3] = {e_u[e], e_v[e], tri_w[t]};  // u < v < w
+        const otri tr = tris[t];
+        const int32_t vtx[3] = {tr.a, tr.b, tr.w};
         int64_t rb[3], re[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) { rb[i] = rp[vtx[i]]; re[i] = rp[vtx[i] + 1]; }
+        for (int i = 0; i < 3; ++i) { rb[i] = out_ptr[vtx[i]]; re[i] = out_ptr[vtx[i] + 1]; }
         int A = 0;
         if (re[1] - rb[1] < re[A] - rb[A]) A = 1;
         if (re[2] - rb[2] < re[A] - rb[A]) A = 2;
         const int B1 = (A == 0) ? 1 : 0, B2 = (A == 2) ? 1 : 2;
-        uint32_t e_uw = 0, e_vw = 0;
-        if (FILL) {  // ids of edges (u,w) and (v,w): positions of w in rows u and v
-            int64_t p1 = lower_bound_i32(col, rb[0], re[0], vtx[2]);
-            int64_t p2 = lower_bound_i32(col, rb[1], re[1], vtx[2]);
-            e_uw = __ldg(eid + p1);
-            e_vw = __ldg(eid + p2);
-        }
-        int64_t out = FILL ? ptr[t] : 0;
+        const int64_t out = MODE ? ptr[t] : 0;
         int64_t cnt = 0;
         bool ok = true;
+        uint32_t id0 = 0;  // MODE 1: the triangle (a,b,w) itself, shared by all its 4-cliques
+        if (MODE == 1) {
+            if (ptr[t + 1] == out) continue;  // no 4-clique here
+            id0 = canon_tri(tr.a, tr.b, tr.w, tr.e_ab, tr.e_aw, tr.e_bw, tri_ptr, tri_w, &ok);
+        }
         for (int64_t base = rb[A]; base < re[A]; base += 32) {
-            int64_t p = base + lane;
+            const int64_t p = base + lane;
             bool found = false;
             int64_t pos[3] = {0, 0, 0};
             int32_t x = 0;
             if (p < re[A]) {
-                x = __ldg(col + p);
+                x = __ldg(out_col + p);
                 pos[A] = p;
-                pos[B1] = lower_bound_i32(col, rb[B1], re[B1], x);
-                if (pos[B1] < re[B1] && __ldg(col + pos[B1]) == x) {
-                    pos[B2] = lower_bound_i32(col, rb[B2], re[B2], x);
-                    found = (pos[B2] < re[B2]) && (__ldg(col + pos[B2]) == x);
+                pos[B1] = lower_bound_i32(out_col, rb[B1], re[B1], x);
+                if (pos[B1] < re[B1] && __ldg(out_col + pos[B1]) == x) {
+                    pos[B2] = lower_bound_i32(out_col, rb[B2], re[B2], x);
+                    found = (pos[B2] < re[B2]) && (__ldg(out_col + pos[B2]) == x);
                 }
             }
-            unsigned bal = __ballot_sync(kFull, found);
-            if (FILL && found) {
-                int64_t slot = out + cnt + __popc(bal & lanemask_lt());
-                uint32_t* dst = inc + 3 * slot;
-                dst[0] = tri_lookup(vtx[0], vtx[1], x, pos[0], e, eid, tri_ptr, tri_w, &ok);
-                dst[1] = tri_lookup(vtx[0], vtx[2], x, pos[0], e_uw, eid, tri_ptr, tri_w, &ok);
-                dst[2] = tri_lookup(vtx[1], vtx[2], x, pos[1], e_vw, eid, tri_ptr, tri_w, &ok);
+            const unsigned bal = __ballot_sync(kFull, found);
+            if (MODE == 1 && found) {
+                const uint32_t e_ax = __ldg(out_eid + pos[0]), e_bx = __ldg(out_eid + pos[1]),
+                               e_wx = __ldg(out_eid + pos[2]);
+                uint4 ids;
+                ids.x = id0;
+                ids.y = canon_tri(tr.a, tr.b, x, tr.e_ab, e_ax, e_bx, tri_ptr, tri_w, &ok);
+                ids.z = canon_tri(tr.a, tr.w, x, tr.e_aw, e_ax, e_wx, tri_ptr, tri_w, &ok);
+                ids.w = canon_tri(tr.b, tr.w, x, tr.e_bw, e_bx, e_wx, tri_ptr, tri_w, &ok);
+                k4[out + cnt + __popc(bal & lanemask_lt())] = ids;
+                atomicAdd(rowcnt + ids.y, 1ull);
+                atomicAdd(rowcnt + ids.z, 1ull);
+                atomicAdd(rowcnt + ids.w, 1ull);
             }
             cnt += __popc(bal);
         }
-        if (FILL && !ok) atomicOr(err, 4);
-        if (!FILL && lane == 0) ptr[t] = cnt;
+        if (MODE == 1 && cnt > 0 && lane == 0) atomicAdd(rowcnt + id0, (unsigned long long)cnt);
+        if (MODE == 1 && !__all_sync(kFull, ok) && lane == 0) atomicOr(err, 4);
+        if (MODE == 0 && lane == 0) ptr[t] = cnt;
+    }
+}
+
+// one thread per 4-clique: add it to the rows of its four triangles
+__global__ void k_k4_scatter(int64_t K, const uint4* __restrict__ k4, unsigned long long* __restrict__ cursor,
+                             uint32_t* __restrict__ inc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 q = k4[i];
+        const uint32_t id[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t* d = inc + 3 * atomicAdd(cursor + id[k], 1ull);
+            int o = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j != k) d[o++] = id[j];
+        }
     }
 }
 
@@ -443,8 +522,8 @@ nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st) {
     if (g->nnz > 0) ND_CUDA(cudaMemcpyAsync(h->col, g->col, sizeof(int32_t) * g->nnz, kind, st));
     ND_TRY(nd_alloc((void**)&h->nlow, sizeof(int32_t) * (g->n > 0 ? g->n : 1), st, h));
     ND_TRY(nd_alloc((void**)&h->up_start, sizeof(int64_t) * (g->n + 1), st, h));
-    int* derr = nullptr;
-    ND_CUDA(cudaMallocAsync((void**)&derr, sizeof(int), st));
+    nd_tmp<int> derr(st);
+    ND_TRY(derr.alloc(1));
     ND_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
     ND_CUDA(cudaMemsetAsync(h->up_start, 0, sizeof(int64_t) * (g->n + 1), st));
     if (g->n > 0) {
@@ -455,9 +534,7 @@ nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st) {
         ND_CUDA(cudaGetLastError());
     }
     int herr = 0;
-    nd_status s = read_flag(derr, &herr, st);
-    cudaFreeAsync(derr, st);
-    if (s != ND_OK) return s;
+    ND_TRY(read_flag(derr, &herr, st));
     if (herr) {
         nd_set_error(herr & 1 ? "row_ptr is not a valid offset array"
                               : "col is not simple, sorted and symmetric");
@@ -489,38 +566,49 @@ nd_status nd_build_edges(nd_incidence* h, cudaStream_t st) {
     return ND_OK;
 }
 
+// oriented out-lists (degree order), used by the (2,3) and (3,4) builds
+struct nd_oriented {
+    nd_tmp<int64_t> out_ptr;
+    nd_tmp<int32_t> out_col, out_src;
+    nd_tmp<uint32_t> out_eid;
+    explicit nd_oriented(cudaStream_t st) : out_ptr(st), out_col(st), out_src(st), out_eid(st) {}
+};
+
+static nd_status orient_graph(nd_incidence* h, nd_oriented* o, cudaStream_t st) {
+    const int64_t n = h->n, m = h->m;
+    ND_TRY(o->out_ptr.alloc(n + 1));
+    ND_TRY(o->out_col.alloc(m));
+    ND_TRY(o->out_src.alloc(m));
+    ND_TRY(o->out_eid.alloc(m));
+    ND_CUDA(cudaMemsetAsync(o->out_ptr.p + n, 0, sizeof(int64_t), st));
+    const int vblocks = nd_blocks_for(n * 32, kThreads, grid_cap(h) * 4);
+    if (n > 0) {
+        nd_prof_scope ps("orient", st);
+        k_orient<false><<<vblocks, kThreads, 0, st>>>(n, h->rp, h->col, h->eid, o->out_ptr, nullptr, nullptr, nullptr);
+        ND_CUDA(cudaGetLastError());
+    }
+    ND_TRY(nd_scan_i64(o->out_ptr, n, st));
+    if (n > 0) {
+        nd_prof_scope ps("orient", st);
+        k_orient<true><<<vblocks, kThreads, 0, st>>>(n, h->rp, h->col, h->eid, o->out_ptr, o->out_col, o->out_eid,
+                                                     o->out_src);
+        ND_CUDA(cudaGetLastError());
+    }
+    return ND_OK;
+}
+
 nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
-    const int64_t m = h->m, n = h->n;
+    const int64_t m = h->m;
     h->num_r = m;
     ND_TRY(nd_alloc((void**)&h->inc_ptr, sizeof(int64_t) * (m + 1), st, h));
     ND_CUDA(cudaMemsetAsync(h->inc_ptr, 0, sizeof(int64_t) * (m + 1), st));
     if (m == 0) { h->num_inc = 0; ND_TRY(nd_alloc((void**)&h->inc, 16, st, h)); return ND_OK; }
-    // oriented out-lists (temporary)
-    int64_t* out_ptr = nullptr;
-    int32_t *out_col = nullptr, *out_src = nullptr;
-    uint32_t* out_eid = nullptr;
-    unsigned long long* cursor = nullptr;
-    ND_CUDA(cudaMallocAsync((void**)&out_ptr, sizeof(int64_t) * (n + 1), st));
-    ND_CUDA(cudaMallocAsync((void**)&out_col, sizeof(int32_t) * m, st));
-    ND_CUDA(cudaMallocAsync((void**)&out_src, sizeof(int32_t) * m, st));
-    ND_CUDA(cudaMallocAsync((void**)&out_eid, sizeof(uint32_t) * m, st));
-    ND_CUDA(cudaMemsetAsync(out_ptr + n, 0, sizeof(int64_t), st));
-    const int vblocks = nd_blocks_for(n * 32, kThreads, grid_cap(h) * 4);
-    {
-        nd_prof_scope ps("orient", st);
-        k_orient<false><<<vblocks, kThreads, 0, st>>>(n, h->rp, h->col, h->eid, out_ptr, nullptr, nullptr, nullptr);
-        ND_CUDA(cudaGetLastError());
-    }
-    ND_TRY(nd_scan_i64(out_ptr, n, st));
-    {
-        nd_prof_scope ps("orient", st);
-        k_orient<true><<<vblocks, kThreads, 0, st>>>(n, h->rp, h->col, h->eid, out_ptr, out_col, out_eid, out_src);
-        ND_CUDA(cudaGetLastError());
-    }
+    nd_oriented o(st);
+    ND_TRY(orient_graph(h, &o, st));
     const int eblocks = nd_blocks_for(m * 32, kThreads, grid_cap(h) * 4);
     {
         nd_prof_scope ps("tri_count", st);
-        k_tri_oriented<false><<<eblocks, kThreads, 0, st>>>(m, out_ptr, out_col, out_eid, out_src,
+        k_tri_oriented<false><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid, o.out_src,
                                                             (unsigned long long*)h->inc_ptr, nullptr);
         ND_CUDA(cudaGetLastError());
     }
@@ -528,18 +616,14 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
     ND_TRY(read_i64(h->inc_ptr + m, &h->num_inc, st));
     ND_TRY(nd_alloc((void**)&h->inc, sizeof(uint32_t) * 2 * (h->num_inc > 0 ? h->num_inc : 1), st, h));
     if (h->num_inc > 0) {
-        ND_CUDA(cudaMallocAsync((void**)&cursor, sizeof(unsigned long long) * m, st));
+        nd_tmp<unsigned long long> cursor(st);
+        ND_TRY(cursor.alloc(m));
         ND_CUDA(cudaMemcpyAsync(cursor, h->inc_ptr, sizeof(int64_t) * m, cudaMemcpyDeviceToDevice, st));
         nd_prof_scope ps("tri_fill", st);
-        k_tri_oriented<true><<<eblocks, kThreads, 0, st>>>(m, out_ptr, out_col, out_eid, out_src, cursor,
+        k_tri_oriented<true><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid, o.out_src, cursor,
                                                            (uint2*)h->inc);
         ND_CUDA(cudaGetLastError());
     }
-    cudaFreeAsync(out_ptr, st);
-    cudaFreeAsync(out_col, st);
-    cudaFreeAsync(out_src, st);
-    cudaFreeAsync(out_eid, st);
-    if (cursor) cudaFreeAsync(cursor, st);
     return ND_OK;
 }
 
@@ -570,35 +654,66 @@ nd_status nd_build_triangles(nd_incidence* h, cudaStream_t st) {
 }
 
 nd_status nd_build_k4_incidence(nd_incidence* h, cudaStream_t st) {
-    const int64_t T = h->num_tri;
+    const int64_t T = h->num_tri, m = h->m;
     h->num_r = T;
     ND_TRY(nd_alloc((void**)&h->inc_ptr, sizeof(int64_t) * (T + 1), st, h));
     ND_CUDA(cudaMemsetAsync(h->inc_ptr, 0, sizeof(int64_t) * (T + 1), st));
-    int blocks = nd_blocks_for(T * 32, kThreads, grid_cap(h) * 4);
-    int* derr = nullptr;
-    ND_CUDA(cudaMallocAsync((void**)&derr, sizeof(int), st));
+    if (T == 0) { h->num_inc = 0; ND_TRY(nd_alloc((void**)&h->inc, 16, st, h)); return ND_OK; }
+    nd_oriented o(st);
+    ND_TRY(orient_graph(h, &o, st));
+    nd_tmp<int64_t> optr(st), kptr(st);  // oriented triangles per oriented edge; 4-cliques per triangle
+    nd_tmp<otri> tris(st);
+    nd_tmp<int> derr(st);
+    ND_TRY(optr.alloc(m + 1));
+    ND_TRY(kptr.alloc(T + 1));
+    ND_TRY(tris.alloc(T));
+    ND_TRY(derr.alloc(1));
     ND_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
-    if (T > 0) {
+    ND_CUDA(cudaMemsetAsync(optr.p + m, 0, sizeof(int64_t), st));
+    ND_CUDA(cudaMemsetAsync(kptr.p + T, 0, sizeof(int64_t), st));
+    const int eblocks = nd_blocks_for(m * 32, kThreads, grid_cap(h) * 4);
+    const int tblocks = nd_blocks_for(T * 32, kThreads, grid_cap(h) * 4);
+    {
+        nd_prof_scope ps("otri", st);
+        k_otri<false><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid, o.out_src, optr, nullptr);
+        ND_CUDA(cudaGetLastError());
+    }
+    ND_TRY(nd_scan_i64(optr, m, st));
+    {
+        nd_prof_scope ps("otri", st);
+        k_otri<true><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid, o.out_src, optr, tris);
+        ND_CUDA(cudaGetLastError());
+    }
+    {
         nd_prof_scope ps("k4_count", st);
-        k_triangle_k4<false><<<blocks, kThreads, 0, st>>>(T, h->rp, h->col, h->eid, h->e_u, h->e_v,
-                                                          h->tri_ptr, h->tri_w, h->tri_e, h->inc_ptr,
-                                                          nullptr, derr);
+        k_k4<0><<<tblocks, kThreads, 0, st>>>(T, tris, o.out_ptr, o.out_col, o.out_eid, h->tri_ptr, h->tri_w,
+                                              kptr, nullptr, nullptr, derr);
+        ND_CUDA(cudaGetLastError());
+    }
+    ND_TRY(nd_scan_i64(kptr, T, st));
+    int64_t K = 0;
+    ND_TRY(read_i64(kptr.p + T, &K, st));
+    nd_tmp<uint4> k4(st);
+    ND_TRY(k4.alloc(K));
+    if (K > 0) {
+        nd_prof_scope ps("k4_list", st);
+        k_k4<1><<<tblocks, kThreads, 0, st>>>(T, tris, o.out_ptr, o.out_col, o.out_eid, h->tri_ptr, h->tri_w,
+                                              kptr, k4, (unsigned long long*)h->inc_ptr, derr);
         ND_CUDA(cudaGetLastError());
     }
     ND_TRY(nd_scan_i64(h->inc_ptr, T, st));
     ND_TRY(read_i64(h->inc_ptr + T, &h->num_inc, st));
     ND_TRY(nd_alloc((void**)&h->inc, sizeof(uint32_t) * 3 * (h->num_inc > 0 ? h->num_inc : 1), st, h));
-    if (h->num_inc > 0) {
+    if (K > 0) {
+        nd_tmp<unsigned long long> cursor(st);
+        ND_TRY(cursor.alloc(T));
+        ND_CUDA(cudaMemcpyAsync(cursor, h->inc_ptr, sizeof(int64_t) * T, cudaMemcpyDeviceToDevice, st));
         nd_prof_scope ps("k4_fill", st);
-        k_triangle_k4<true><<<blocks, kThreads, 0, st>>>(T, h->rp, h->col, h->eid, h->e_u, h->e_v,
-                                                         h->tri_ptr, h->tri_w, h->tri_e, h->inc_ptr,
-                                                         h->inc, derr);
+        k_k4_scatter<<<nd_blocks_for(K, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(K, k4, cursor, h->inc);
         ND_CUDA(cudaGetLastError());
     }
     int herr = 0;
-    nd_status s = read_flag(derr, &herr, st);
-    cudaFreeAsync(derr, st);
-    if (s != ND_OK) return s;
+    ND_TRY(read_flag(derr, &herr, st));
     if (herr) { nd_set_error("internal: a triangle of a 4-clique was not found"); return ND_E_INVAL; }
     return ND_OK;
 }
@@ -610,10 +725,10 @@ nd_status nd_build_buckets(nd_incidence* h, cudaStream_t st) {
         for (auto& ex : row)
             if (ex) { cudaGraphExecDestroy(ex); ex = nullptr; }
     const int3 thr = make_int3(h->thr[0], h->thr[1], h->thr[2]);
-    int64_t* flags = nullptr;
-    unsigned long long* sums = nullptr;
-    ND_CUDA(cudaMallocAsync((void**)&flags, sizeof(int64_t) * (N + 1), st));
-    ND_CUDA(cudaMallocAsync((void**)&sums, sizeof(unsigned long long) * ND_NB, st));
+    nd_tmp<int64_t> flags(st);
+    nd_tmp<unsigned long long> sums(st);
+    ND_TRY(flags.alloc(N + 1));
+    ND_TRY(sums.alloc(ND_NB));
     ND_CUDA(cudaMemsetAsync(sums, 0, sizeof(unsigned long long) * ND_NB, st));
     if (!h->items) ND_TRY(nd_alloc((void**)&h->items, sizeof(nd_item) * (N > 0 ? N : 1), st, h));
     int blocks = nd_blocks_for(N, kThreads, grid_cap(h) * 2);
@@ -621,10 +736,10 @@ nd_status nd_build_buckets(nd_incidence* h, cudaStream_t st) {
     for (int b = 0; b < ND_NB; ++b) {
         h->bucket_lo[b] = lo;
         if (N == 0) continue;
-        ND_CUDA(cudaMemsetAsync(flags + N, 0, sizeof(int64_t), st));
+        ND_CUDA(cudaMemsetAsync(flags.p + N, 0, sizeof(int64_t), st));
         {
             nd_prof_scope ps("buckets", st);
-            k_bucket_flags<<<blocks, kThreads, 0, st>>>(N, h->inc_ptr, b, thr, flags, sums + b);
+            k_bucket_flags<<<blocks, kThreads, 0, st>>>(N, h->inc_ptr, b, thr, flags, sums.p + b);
             ND_CUDA(cudaGetLastError());
         }
         ND_TRY(nd_scan_i64(flags, N, st));
@@ -634,7 +749,7 @@ nd_status nd_build_buckets(nd_incidence* h, cudaStream_t st) {
             ND_CUDA(cudaGetLastError());
         }
         int64_t cnt = 0;
-        ND_TRY(read_i64(flags + N, &cnt, st));
+        ND_TRY(read_i64(flags.p + N, &cnt, st));
         lo += cnt;
     }
     h->bucket_lo[ND_NB] = lo;
@@ -643,8 +758,6 @@ nd_status nd_build_buckets(nd_incidence* h, cudaStream_t st) {
     ND_CUDA(cudaStreamSynchronize(st));
     for (int b = 0; b < ND_NB; ++b) h->bucket_inc[b] = (int64_t)hs[b];
     h->num_zero = N - lo;
-    cudaFreeAsync(flags, st);
-    cudaFreeAsync(sums, st);
     return ND_OK;
 }
 
@@ -659,12 +772,13 @@ nd_status nd_write_r_cliques(const nd_incidence* h, int32_t* out_dev, cudaStream
 
 nd_status nd_union_device(const nd_union_part* parts_host, int count, int64_t n, int64_t nnz, int64_t* urp,
                           int32_t* ucol, cudaStream_t st) {
-    nd_union_part* dparts = nullptr;
-    int* derr = nullptr;
-    ND_CUDA(cudaMallocAsync((void**)&dparts, sizeof(nd_union_part) * (count > 0 ? count : 1), st));
-    ND_CUDA(cudaMallocAsync((void**)&derr, sizeof(int), st));
+    nd_tmp<nd_union_part> dparts(st);
+    nd_tmp<int> derr(st);
+    ND_TRY(dparts.alloc(count));
+    ND_TRY(derr.alloc(1));
     ND_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
-    ND_CUDA(cudaMemcpyAsync(dparts, parts_host, sizeof(nd_union_part) * count, cudaMemcpyHostToDevice, st));
+    if (count > 0)
+        ND_CUDA(cudaMemcpyAsync(dparts, parts_host, sizeof(nd_union_part) * count, cudaMemcpyHostToDevice, st));
     if (count > 0) {
         nd_prof_scope ps("union", st);
         k_union<<<count < 152 * 16 ? count : 152 * 16, kThreads, 0, st>>>(dparts, count, urp, ucol, derr);
@@ -672,10 +786,7 @@ nd_status nd_union_device(const nd_union_part* parts_host, int count, int64_t n,
     }
     ND_CUDA(cudaMemcpyAsync(urp + n, &nnz, sizeof(int64_t), cudaMemcpyHostToDevice, st));
     int herr = 0;
-    nd_status s = read_flag(derr, &herr, st);
-    cudaFreeAsync(dparts, st);
-    cudaFreeAsync(derr, st);
-    if (s != ND_OK) return s;
+    ND_TRY(read_flag(derr, &herr, st));
     if (herr) {
         nd_set_error(herr & 1 ? "a graph of the batch has an invalid row_ptr"
                               : "a graph of the batch has a neighbour id outside its own vertex range");
@@ -692,24 +803,21 @@ nd_status nd_batch_offsets(const nd_incidence* h, const int64_t* vertex_off /* c
         for (int i = 0; i <= count; ++i) r_off[i] = vertex_off[i];
         return ND_OK;
     }
-    int64_t* didx = nullptr;
-    int64_t* dout = nullptr;
-    ND_CUDA(cudaMallocAsync((void**)&didx, sizeof(int64_t) * (count + 1), st));
-    ND_CUDA(cudaMallocAsync((void**)&dout, sizeof(int64_t) * (count + 1), st));
+    nd_tmp<int64_t> didx(st), dout(st);
+    ND_TRY(didx.alloc(count + 1));
+    ND_TRY(dout.alloc(count + 1));
     ND_CUDA(cudaMemcpyAsync(didx, vertex_off, sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
     // edges owned by vertices below the graph's first vertex
     k_gather_i64<<<nd_blocks_for(count + 1, kThreads, 64), kThreads, 0, st>>>(h->up_start, didx, count + 1, dout);
     ND_CUDA(cudaGetLastError());
+    const int64_t* res = dout;
     if (h->r == 3) {
         // triangles owned by those edges
         k_gather_i64<<<nd_blocks_for(count + 1, kThreads, 64), kThreads, 0, st>>>(h->tri_ptr, dout, count + 1, didx);
         ND_CUDA(cudaGetLastError());
-        ND_CUDA(cudaMemcpyAsync(r_off, didx, sizeof(int64_t) * (count + 1), cudaMemcpyDeviceToHost, st));
-    } else {
-        ND_CUDA(cudaMemcpyAsync(r_off, dout, sizeof(int64_t) * (count + 1), cudaMemcpyDeviceToHost, st));
+        res = didx;
     }
+    ND_CUDA(cudaMemcpyAsync(r_off, res, sizeof(int64_t) * (count + 1), cudaMemcpyDeviceToHost, st));
     ND_CUDA(cudaStreamSynchronize(st));
-    cudaFreeAsync(didx, st);
-    cudaFreeAsync(dout, st);
     return ND_OK;
 }

@@ -2,9 +2,10 @@
 // with or without notification (Alg. 3, Section 4.3).
 //
 // One pass = one launch of a persistent grid.  R-cliques are grouped into
-// four degree buckets (d_s in [1,8], [9,64], [65,2048], >2048) and evaluated
-// by a group of 4 or 8 lanes, a warp, or a whole CTA; blocks take chunks of
-// r-cliques from a per-pass counter, longest rows first.  A group of 4 or 8:
+// four degree buckets (by default d_s in [1,8], [9,64], [65,2048], >2048)
+// and evaluated by a group of 4 or 8 lanes, a warp, or a whole CTA.  The CTA
+// rows are taken one per block from a per-pass counter; the rest are warp
+// tasks interleaved statically over all warps.  A group of 4 or 8:
 //   1. streams the r-clique's incidence row (coalesced, q ids per s-clique),
 //      gathers the q tau values of each s-clique and keeps
 //      rho = min(...) in registers (Def. 4, step 1);
@@ -24,7 +25,7 @@
 //
 // SND reads tau_p and writes tau (ping-pong buffers, no copy).  AND reads and
 // writes one tau array in place; tau only decreases, so a stale read is a
-// larger value and at worst delays convergence.  With notification, an
+// larger value and at worst delays a decrease by a pass.  With notification, an
 // r-clique is evaluated only if its bit is set in the current frontier; when
 // its tau drops to h it sets the next-frontier bit of every neighbour R' with
 // h <= tau(R') (Alg. 3, the orange lines).  It does not re-activate itself.
@@ -43,12 +44,9 @@ constexpr int kThreads = 256;
 #endif
 constexpr int kWarpUnroll = ND_WARP_UNROLL;
 
-// Work of one pass is a list of chunks, longest rows first (bucket 3, 2, 1,
-// 0); persistent blocks take chunks from a per-pass counter until none are
-// left, so every SM stays busy to the end of the pass.
-// processing order of the buckets, and r-cliques per chunk by bucket
-__host__ __device__ constexpr int bucket_at(int o) { return ND_NB - 1 - o; }
-__host__ __device__ constexpr int chunk_r(int b) { return b == 0 ? 256 : (b == 1 ? 64 : (b == 2 ? 8 : 1)); }
+// Work of one pass: rows longer than the CTA threshold are taken one per
+// block from a per-pass counter; all other rows form warp tasks that are
+// interleaved statically over the warps of the persistent grid.
 
 struct SweepParams {
     const int64_t* __restrict__ inc_ptr;
@@ -57,33 +55,46 @@ struct SweepParams {
     int32_t* tout;
     const nd_item* __restrict__ items;
     int64_t lo[ND_NB], hi[ND_NB];  // bucket ranges in items
-    int64_t chunk_end[ND_NB];      // cumulative chunk counts, in processing order
     const uint32_t* cur;  // AND + notification: frontier read in this pass
     uint32_t* next;       // and the frontier written for the next pass
-    unsigned long long* ctr;         // this pass: [0] changed, [1] evaluated, [2] next chunk,
+    const uint32_t* members;  // PartialAnd: only members are notified (null = everyone)
+    unsigned long long* ctr;         // this pass: [0] changed, [1] evaluated, [2] next CTA row,
                                      // [3] incidences of the evaluated rows
     const unsigned long long* prev;  // previous pass (null on the first)
 };
 
+// tau loads.  SND reads last pass's array through the read-only path.  AND
+// reads the array it is updating with plain (L1-cacheable) loads: a value
+// seen early or from another SM's stale line is never smaller than the true
+// one, because tau only decreases, so it can only delay a decrease to a later
+// pass (the writer notifies) or over-notify; every pass is a new launch, which
+// starts from fresh caches.
 template <bool RO>
 __device__ __forceinline__ int32_t ld_tau(const int32_t* p) {
     if (RO) return __ldg(p);
-    return *(volatile const int32_t*)p;
+    return *p;
 }
 
-// rho(S,R) for the s-clique at incidence j: min of the other r-cliques' tau
+// rho(S,R) for the s-clique at incidence j: min of the other r-cliques' tau.
+// SND reads each row once per pass, so its ids are loaded evict-first and do
+// not push the gathered tau values out of L2.  AND re-reads the row of a
+// changed r-clique to notify its neighbours, so its ids are cached normally.
+template <bool RO>
+__device__ __forceinline__ uint32_t ld_id(const uint32_t* p) {
+    return RO ? __ldcs(p) : __ldg(p);
+}
+
 template <int Q, bool RO>
 __device__ __forceinline__ int32_t rho_at(const uint32_t* __restrict__ inc, const int32_t* tau, int64_t j) {
-    // the incidence ids are read once per pass: evict-first, so that they do
-    // not push the gathered tau values out of L2
     if (Q == 1) {
-        return ld_tau<RO>(tau + __ldcs(inc + j));
+        return ld_tau<RO>(tau + ld_id<RO>(inc + j));
     } else if (Q == 2) {
-        uint2 id = __ldcs(reinterpret_cast<const uint2*>(inc) + j);
+        const uint2* p = reinterpret_cast<const uint2*>(inc) + j;
+        uint2 id = RO ? __ldcs(p) : __ldg(p);
         return min(ld_tau<RO>(tau + id.x), ld_tau<RO>(tau + id.y));
     } else {
         const uint32_t* p = inc + 3 * j;
-        uint32_t a = __ldcs(p), b = __ldcs(p + 1), c = __ldcs(p + 2);
+        uint32_t a = ld_id<RO>(p), b = ld_id<RO>(p + 1), c = ld_id<RO>(p + 2);
         return min(min(ld_tau<RO>(tau + a), ld_tau<RO>(tau + b)), ld_tau<RO>(tau + c));
     }
 }
@@ -238,10 +249,12 @@ __device__ __forceinline__ int32_t cta_hindex(const uint32_t* __restrict__ inc, 
 }
 
 // notify every neighbour whose tau could still depend on R (Alg. 3, orange
-// lines): set its next-frontier bit if h <= tau(R'), reading the word first
-// so that an atomic is only issued for a bit that is still clear.  (Warp-wide
-// merging of bits that share a word was measured slower: the match runs for
-// every neighbour, while most neighbours need no write.)
+// lines): set its next-frontier bit if h <= tau(R').  A neighbour whose bit
+// is already set needs nothing, so the bitmap word (2 MB for 16M r-cliques,
+// cache-resident) is read before the neighbour's tau, and an atomic is only
+// issued for a bit that is still clear.  (Warp-wide merging of bits that
+// share a word was measured slower: the match runs for every neighbour,
+// while most neighbours need no write.)
 template <int Q>
 __device__ __forceinline__ void notify_row(const SweepParams& P, int64_t jb, int64_t je, int32_t h,
                                            int first, int step, unsigned /*gmask*/) {
@@ -249,11 +262,10 @@ __device__ __forceinline__ void notify_row(const SweepParams& P, int64_t jb, int
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             const uint32_t Rp = __ldg(P.inc + Q * j + k);
-            if (h <= ld_tau<false>(P.tin + Rp)) {
-                const uint32_t bit = 1u << (Rp & 31);
-                uint32_t* w = P.next + (Rp >> 5);
-                if (!(*(volatile uint32_t*)w & bit)) atomicOr(w, bit);
-            }
+            const uint32_t bit = 1u << (Rp & 31);
+            if (P.members && !(__ldg(P.members + (Rp >> 5)) & bit)) continue;  // PartialAnd
+            uint32_t* w = P.next + (Rp >> 5);
+            if ((*(volatile uint32_t*)w & bit) == 0u && h <= ld_tau<false>(P.tin + Rp)) atomicOr(w, bit);
         }
     }
 }
@@ -274,64 +286,50 @@ __device__ __forceinline__ nd_item load_item(const nd_item* __restrict__ items, 
     return it;
 }
 
-// work items [first, last): one r-clique per group of G lanes; the next
-// item is loaded before the current one is evaluated
+// work items [first, first + 32/G): one r-clique per group of G lanes of the
+// calling warp
 template <int Q, int G, int C, bool AND, bool NOTIFY>
 __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, int64_t last,
                                            unsigned long long& changed, unsigned long long& evals,
                                            unsigned long long& incs) {
     auto g = cg::tiled_partition<G>(cg::this_thread_block());
     const int lane = g.thread_rank();
-    int64_t i = first + g.meta_group_rank();
-    nd_item it;
-    if (i < last) it = load_item(P.items, i);
-    while (i < last) {
-        const int64_t ni = i + kThreads / G;
-        nd_item nx;
-        if (ni < last) nx = load_item(P.items, ni);
-        const uint32_t R = it.R;
-        const int64_t jb = it.jb, je = it.jb + it.d;
-        bool active = true;
-        if (AND && NOTIFY) active = (__ldg(P.cur + (R >> 5)) >> (R & 31)) & 1u;
-        if (active) {
-            const int32_t t = ld_tau<!AND>(P.tin + R);
-            const int32_t h = group_hindex<Q, G, C, !AND>(g, P.inc, P.tin, jb, je, t);
-            if (lane == 0) {
-                evals++;
-                incs += it.d;
-                if (h != t) changed++;
-                if (!AND || h != t) P.tout[R] = h;
-            }
-            if (AND && NOTIFY && h != t) notify_row<Q>(P, jb, je, h, lane, G, group_mask<G>());
-        }
-        it = nx;
-        i = ni;
+    // the group's index inside its warp, from the lane id (G divides 32)
+    const int64_t i = first + (int64_t)((threadIdx.x & 31) / G);
+    if (i >= last) return;
+    const nd_item it = load_item(P.items, i);
+    const uint32_t R = it.R;
+    const int64_t jb = it.jb, je = it.jb + it.d;
+    if (AND && NOTIFY && !((__ldg(P.cur + (R >> 5)) >> (R & 31)) & 1u)) return;
+    const int32_t t = ld_tau<!AND>(P.tin + R);
+    const int32_t h = group_hindex<Q, G, C, !AND>(g, P.inc, P.tin, jb, je, t);
+    if (lane == 0) {
+        evals++;
+        incs += it.d;
+        if (h != t) changed++;
+        if (!AND || h != t) P.tout[R] = h;
     }
+    if (AND && NOTIFY && h != t) notify_row<Q>(P, jb, je, h, lane, G, group_mask<G>());
 }
 
-// work items [first, last): one r-clique per warp, streamed (rows of 65-2048)
+// one r-clique per warp (rows of the warp bucket), streamed
 template <int Q, bool AND, bool NOTIFY>
-__device__ __forceinline__ void run_warps(const SweepParams& P, int64_t first, int64_t last,
-                                          unsigned* bins, unsigned long long& changed,
-                                          unsigned long long& evals, unsigned long long& incs) {
+__device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item& it, unsigned* bins,
+                                             unsigned long long& changed, unsigned long long& evals,
+                                             unsigned long long& incs) {
     const int lane = threadIdx.x & 31;
-    for (int64_t i = first + (threadIdx.x >> 5); i < last; i += kThreads / 32) {
-        const nd_item it = load_item(P.items, i);
-        const uint32_t R = it.R;
-        if (AND && NOTIFY) {
-            if (!((__ldg(P.cur + (R >> 5)) >> (R & 31)) & 1u)) continue;
-        }
-        const int32_t t = ld_tau<!AND>(P.tin + R);
-        const int64_t jb = it.jb, je = it.jb + it.d;
-        const int32_t h = warp_hindex<Q, !AND>(P.inc, P.tin, jb, je, t, bins);
-        if (lane == 0) {
-            evals++;
-            incs += it.d;
-            if (h != t) changed++;
-            if (!AND || h != t) P.tout[R] = h;
-        }
-        if (AND && NOTIFY && h != t) notify_row<Q>(P, jb, je, h, lane, 32, 0xffffffffu);
+    const uint32_t R = it.R;
+    if (AND && NOTIFY && !((__ldg(P.cur + (R >> 5)) >> (R & 31)) & 1u)) return;
+    const int32_t t = ld_tau<!AND>(P.tin + R);
+    const int64_t jb = it.jb, je = it.jb + it.d;
+    const int32_t h = warp_hindex<Q, !AND>(P.inc, P.tin, jb, je, t, bins);
+    if (lane == 0) {
+        evals++;
+        incs += it.d;
+        if (h != t) changed++;
+        if (!AND || h != t) P.tout[R] = h;
     }
+    if (AND && NOTIFY && h != t) notify_row<Q>(P, jb, je, h, lane, 32, 0xffffffffu);
 }
 
 // one r-clique per CTA (rows longer than 2048 incidences)
@@ -369,24 +367,48 @@ __global__ void __launch_bounds__(kThreads, ND_PASS_MIN_BLOCKS) k_pass(SweepPara
     __shared__ int bounds[2];
     __shared__ unsigned long long s_chunk;
     unsigned long long changed = 0, evals = 0, incs = 0;
-    const int64_t total = P.chunk_end[ND_NB - 1];
-    for (;;) {
-        if (threadIdx.x == 0) s_chunk = atomicAdd(P.ctr + 2, 1ull);
-        __syncthreads();
-        const int64_t c = (int64_t)s_chunk;
-        __syncthreads();
-        if (c >= total) break;
-        int o = 0;
-        while (c >= P.chunk_end[o]) ++o;
-        const int b = bucket_at(o);
-        const int64_t k = c - (o ? P.chunk_end[o - 1] : 0);
-        const int64_t first = P.lo[b] + k * chunk_r(b);
-        const int64_t last = min(first + (int64_t)chunk_r(b), P.hi[b]);
-        switch (b) {
-            case 0: run_groups<Q, 4, 2, AND, NOTIFY>(P, first, last, changed, evals, incs); break;
-            case 1: run_groups<Q, 8, 8, AND, NOTIFY>(P, first, last, changed, evals, incs); break;
-            case 2: run_warps<Q, AND, NOTIFY>(P, first, last, bins[threadIdx.x >> 5], changed, evals, incs); break;
-            default: run_cta<Q, AND, NOTIFY>(P, first, last, bins[0], bounds, changed, evals, incs); break;
+    // phase 1: rows longer than the CTA threshold, one per block at a time,
+    // taken from a per-pass counter (longest rows first)
+    const int64_t n3 = P.hi[3] - P.lo[3];
+    if (n3 > 0) {
+        for (;;) {
+            if (threadIdx.x == 0) s_chunk = atomicAdd(P.ctr + 2, 1ull);
+            __syncthreads();
+            const int64_t c = (int64_t)s_chunk;
+            __syncthreads();
+            if (c >= n3) break;
+            run_cta<Q, AND, NOTIFY>(P, P.lo[3] + c, P.lo[3] + c + 1, bins[0], bounds, changed, evals, incs);
+        }
+    }
+    // phase 2: warp tasks (one warp row, four 8-lane rows or eight 4-lane
+    // rows), longest first, interleaved statically over every warp of the
+    // grid: no barrier and no shared counter, and each warp gets an equal
+    // share of every bucket
+    const int64_t n2 = P.hi[2] - P.lo[2];
+    const int64_t t1 = (P.hi[1] - P.lo[1] + 3) / 4;
+    const int64_t t0 = (P.hi[0] - P.lo[0] + 7) / 8;
+    const int64_t tasks = n2 + t1 + t0;
+    const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
+    int64_t t = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    if (t < n2) {
+        // warp rows: the next task's work item is loaded before this one runs
+        nd_item it = load_item(P.items, P.lo[2] + t);
+        while (t < n2) {
+            const int64_t tn = t + warps;
+            nd_item nx;
+            if (tn < n2) nx = load_item(P.items, P.lo[2] + tn);
+            run_warp_row<Q, AND, NOTIFY>(P, it, bins[threadIdx.x >> 5], changed, evals, incs);
+            it = nx;
+            t = tn;
+        }
+    }
+    for (; t < tasks; t += warps) {
+        if (t < n2 + t1) {
+            const int64_t first = P.lo[1] + 4 * (t - n2);
+            run_groups<Q, 8, 8, AND, NOTIFY>(P, first, min(first + 4, P.hi[1]), changed, evals, incs);
+        } else {
+            const int64_t first = P.lo[0] + 8 * (t - n2 - t1);
+            run_groups<Q, 4, 2, AND, NOTIFY>(P, first, min(first + 8, P.hi[0]), changed, evals, incs);
         }
     }
     __shared__ unsigned long long s_ch[kThreads / 32], s_ev[kThreads / 32], s_in[kThreads / 32];
@@ -427,6 +449,25 @@ __global__ void k_fill_front(int64_t N, uint32_t* __restrict__ f) {
     }
 }
 
+__global__ void k_member_mask(const uint32_t* __restrict__ ids, int64_t count, int64_t N,
+                              uint32_t* __restrict__ mask, int* __restrict__ err) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t R = ids[i];
+        if ((int64_t)R >= N) { atomicOr(err, 1); continue; }
+        atomicOr(mask + (R >> 5), 1u << (R & 31));
+    }
+}
+
+__global__ void k_count_equal(const int32_t* __restrict__ a, const int32_t* __restrict__ b, int64_t n,
+                              unsigned long long* __restrict__ out) {
+    unsigned long long c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += (a[i] == b[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
 __global__ void k_add_const(const int32_t* __restrict__ in, int64_t n, int32_t c, int32_t* __restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -442,26 +483,28 @@ pass_fn pick(int q, int mode) {
     return mode == ND_SND ? k_pass<3, false, false> : (mode == ND_AND ? k_pass<3, true, true> : k_pass<3, true, false>);
 }
 
-// chunk table of a pass (see bucket_at / chunk_r)
+// bucket ranges of a pass
 void plan_chunks(const nd_incidence* h, SweepParams& P) {
-    int64_t acc = 0;
-    for (int o = 0; o < ND_NB; ++o) {
-        const int b = bucket_at(o);
+    for (int b = 0; b < ND_NB; ++b) {
         P.lo[b] = h->bucket_lo[b];
         P.hi[b] = h->bucket_lo[b + 1];
-        acc += (P.hi[b] - P.lo[b] + chunk_r(b) - 1) / chunk_r(b);
-        P.chunk_end[o] = acc;
     }
 }
 
+// work units of a pass: CTA rows + warp tasks (see k_pass)
+int64_t pass_units(const SweepParams& P) {
+    return (P.hi[3] - P.lo[3]) + (P.hi[2] - P.lo[2]) + (P.hi[1] - P.lo[1] + 3) / 4 + (P.hi[0] - P.lo[0] + 7) / 8;
+}
+
 // persistent grid: as many blocks as fit on the GPU at once (never more than
-// there are chunks)
-int pass_grid(const nd_incidence* h, const void* fn, int64_t chunks) {
+// the work needs)
+int pass_grid(const nd_incidence* h, const void* fn, int64_t units) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     int64_t g = (int64_t)per_sm * (h->sm_count > 0 ? h->sm_count : 152);
-    if (g > chunks) g = chunks;
+    const int64_t need = (units + kThreads / 32 - 1) / (kThreads / 32);
+    if (g > need) g = need;
     return (int)(g < 1 ? 1 : g);
 }
 
@@ -577,6 +620,24 @@ nd_status nd_init_tau(nd_incidence* h, int32_t* tau, cudaStream_t st) {
     return ND_OK;
 }
 
+nd_status nd_member_mask(const uint32_t* ids, int64_t count, int64_t N, uint32_t* mask, int* err, cudaStream_t st) {
+    if (count == 0) return ND_OK;
+    nd_prof_scope ps("member_mask", st);
+    k_member_mask<<<nd_blocks_for(count, kThreads, 152 * 8), kThreads, 0, st>>>(ids, count, N, mask, err);
+    ND_CUDA(cudaGetLastError());
+    return ND_OK;
+}
+
+nd_status nd_count_equal_dev(const int32_t* a, const int32_t* b, int64_t n, unsigned long long* out_dev,
+                             cudaStream_t st) {
+    ND_CUDA(cudaMemsetAsync(out_dev, 0, sizeof(unsigned long long), st));
+    if (n == 0) return ND_OK;
+    nd_prof_scope ps("count_equal", st);
+    k_count_equal<<<nd_blocks_for(n, kThreads, 152 * 8), kThreads, 0, st>>>(a, b, n, out_dev);
+    ND_CUDA(cudaGetLastError());
+    return ND_OK;
+}
+
 nd_status nd_classic_truss(const int32_t* in, int64_t n, int32_t* out, cudaStream_t st) {
     if (n == 0) return ND_OK;
     int blocks = nd_blocks_for(n, kThreads, 152 * 8);
@@ -592,7 +653,10 @@ nd_status nd_classic_truss(const int32_t* in, int64_t n, int32_t* out, cudaStrea
 // the counters back once per batch.
 nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* tau_in_dev,
                  int32_t** tau_result, int32_t* updating, int64_t* evals, bool* converged,
-                 cudaStream_t st) {
+                 cudaStream_t st, nd_run_opts* opts) {
+    const uint32_t* members = (opts && mode != ND_SND) ? opts->members : nullptr;
+    const double stop_active = (opts && mode != ND_SND) ? opts->stop_active : 0.0;
+    if (opts) opts->stopped = false;
     const bool and_mode = (mode != ND_SND);
     const int64_t N = h->num_r;
     ND_TRY(ensure_state(h, and_mode, st));
@@ -620,7 +684,10 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
         return ND_OK;
     }
     const int64_t words = (N + 31) / 32;
-    if (mode == ND_AND) {
+    if (mode == ND_AND && members) {
+        // PartialAnd: the members start active (end of Section 4.3)
+        ND_CUDA(cudaMemcpyAsync(h->front[0], members, sizeof(uint32_t) * words, cudaMemcpyDeviceToDevice, st));
+    } else if (mode == ND_AND) {
         nd_prof_scope ps("fill_front", st);
         k_fill_front<<<nd_blocks_for(words, kThreads, h->sm_count * 8), kThreads, 0, st>>>(N, h->front[0]);
         ND_CUDA(cudaGetLastError());
@@ -629,9 +696,11 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
     P.inc_ptr = h->inc_ptr;
     P.inc = h->inc;
     P.items = h->items;
+    P.members = members;
     plan_chunks(h, P);
     pass_fn fn = pick(h->q, mode);
-    const int grid = P.chunk_end[ND_NB - 1] > 0 ? pass_grid(h, (const void*)fn, P.chunk_end[ND_NB - 1]) : 0;
+    const int64_t units = pass_units(P);
+    const int grid = units > 0 ? pass_grid(h, (const void*)fn, units) : 0;
     const int kBatch = ND_BATCH;
     // Thm. 3 / Lemma 2: SND settles within the number of degree levels, at
     // most N_R, and AND never needs more passes than SND.  A run longer than
@@ -652,9 +721,11 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
         const int base = (int)(batch & 1) * kBatch;
         int nb = kBatch;
         if (nb > max_passes - pass) nb = max_passes - pass;
+        if (stop_active > 0.0) nb = 1;  // the stopping rule looks at every pass
         const int kind = batch == 0 ? 0 : ((batch & 1) ? 2 : 1);
         bool launched = false;
-        if (nb == kBatch && grid > 0 && !h->pass_graph_failed[mode][kind]) {
+        // graphs hold the plain parameters; runs with members or a stopping rule launch directly
+        if (nb == kBatch && grid > 0 && !members && !h->pass_graph_failed[mode][kind]) {
             if (!h->pass_graph[mode][kind])
                 make_batch_graph(h, mode, kind, P, grid, fn, words);
             if (h->pass_graph[mode][kind]) {
@@ -695,10 +766,18 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
             if (!and_mode) last_written = (p & 1) ^ 1;
             if (ch == 0) { done = true; break; }
             (*updating)++;
+            // active-ratio rule (Section 5.2, Fig. 9): the fraction of r-cliques
+            // evaluated in this pass predicts how close tau is to kappa
+            const double active = (double)h->h_counters[ND_SLOT * (base + k) + 1] / (double)N;
+            if (stop_active > 0.0 && active < stop_active) {
+                opts->stopped = true;
+                done = true;
+                break;
+            }
         }
         ++batch;
     }
-    *converged = done;
+    *converged = done && !(opts && opts->stopped);
     *tau_result = and_mode ? h->tau[0] : h->tau[last_written];
     if (!done && over_bound) {
         nd_set_error("no convergence within N_R + 1 passes, the bound of Thm. 3 (internal fault)");

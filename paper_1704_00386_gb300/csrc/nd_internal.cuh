@@ -106,6 +106,31 @@ enum { ND_BATCH = 16, ND_RING = 2 * ND_BATCH, ND_SLOT = 4 };
 // wait for a stream with a time limit (ND_E_TIMEOUT past it)
 nd_status nd_wait(cudaStream_t st, double seconds);
 
+// a stream-ordered device temporary, released when it goes out of scope
+// (also on every early error return)
+template <typename T>
+struct nd_tmp {
+    T* p = nullptr;
+    cudaStream_t st = 0;
+    explicit nd_tmp(cudaStream_t s) : st(s) {}
+    nd_tmp(const nd_tmp&) = delete;
+    nd_tmp& operator=(const nd_tmp&) = delete;
+    ~nd_tmp() {
+        if (p) cudaFreeAsync(p, st);
+    }
+    nd_status alloc(int64_t count) {
+        if (count < 1) count = 1;
+        if (cudaMallocAsync((void**)&p, sizeof(T) * (size_t)count, st) != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            nd_set_error("device allocation of a temporary failed");
+            return ND_E_NOMEM;
+        }
+        return ND_OK;
+    }
+    operator T*() const { return p; }
+};
+
 // device memory helpers (stream-ordered)
 nd_status nd_alloc(void** p, size_t bytes, cudaStream_t st, nd_incidence* owner);
 void nd_release(void* p, cudaStream_t st);
@@ -136,9 +161,18 @@ nd_status nd_batch_offsets(const nd_incidence* h, const int64_t* vertex_off, int
 
 // iteration (nd_hindex.cu)
 nd_status nd_init_tau(nd_incidence* h, int32_t* tau, cudaStream_t st);
+// options of a run beyond the paper's plain SND / AND
+struct nd_run_opts {
+    const uint32_t* members = nullptr;  // PartialAnd: member bitmap (device), AND modes only
+    double stop_active = 0.0;           // AND: stop after a pass that evaluated < this fraction of N_R
+    bool stopped = false;               // out: the active-ratio rule ended the run
+};
 nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* tau_in_dev,
                  int32_t** tau_result, int32_t* updating, int64_t* evals, bool* converged,
-                 cudaStream_t st);
+                 cudaStream_t st, nd_run_opts* opts = nullptr);
+nd_status nd_member_mask(const uint32_t* ids, int64_t count, int64_t N, uint32_t* mask, int* err, cudaStream_t st);
+nd_status nd_count_equal_dev(const int32_t* a, const int32_t* b, int64_t n, unsigned long long* out_dev,
+                             cudaStream_t st);
 nd_status nd_classic_truss(const int32_t* in, int64_t n, int32_t* out, cudaStream_t st);
 
 // launch geometry

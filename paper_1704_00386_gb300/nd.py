@@ -26,7 +26,7 @@ MODES = {"snd": ND_SND, "and": ND_AND, "and_nn": ND_AND_NN}
 
 SYMBOLS = ["nd_build_incidence", "nd_build_incidence_batch", "nd_incidence_info", "nd_r_cliques", "nd_s_degree", "nd_snd",
            "nd_and", "nd_iterate_k", "nd_truss_classic", "nd_prof_enable", "nd_prof_read",
-           "nd_last_passes", "nd_autotune", "nd_incidence_bytes", "nd_free", "nd_strerror", "nd_last_error",
+           "nd_last_passes", "nd_autotune", "nd_and_partial", "nd_and_until", "nd_count_equal", "nd_incidence_bytes", "nd_free", "nd_strerror", "nd_last_error",
            "nd_abi_version", "nd_core_snd_noalloc"]
 
 _lock = threading.Lock()
@@ -75,6 +75,9 @@ def load(build_if_missing: bool = True):
         lib.nd_prof_read.argtypes = [ci, P(ctypes.c_char_p), P(i64), P(ctypes.c_double)]
         lib.nd_last_passes.argtypes = [vp, vp, vp, vp, i32, P(i32)]
         lib.nd_autotune.argtypes = [vp, i32, vp, vp, P(ctypes.c_double)]
+        lib.nd_and_partial.argtypes = [vp, vp, i64, ci, vp, i32, P(i32), P(i64), vp]
+        lib.nd_and_until.argtypes = [vp, ctypes.c_double, vp, ci, i32, P(i32), P(i64), P(ci), vp]
+        lib.nd_count_equal.argtypes = [vp, vp, i64, ci, P(i64), vp]
         lib.nd_incidence_bytes.argtypes = [vp, P(i64)]
         lib.nd_core_snd_noalloc.argtypes = [vp, vp, i64, i64, vp, i32, P(i32), vp]
         lib.nd_free.argtypes = [vp]
@@ -191,6 +194,30 @@ class Incidence:
                              int(max_iters), ctypes.byref(it), ctypes.byref(ev), self._sp(stream)),
                "nd_and")
         return tau, it.value, ev.value
+
+    def and_partial(self, members, max_iters: int = 1 << 30, out=None, stream=None):
+        """PartialAnd on the r-clique ids `members` (numpy uint32 for a host
+        graph, CUDA int32/uint32 tensor for a device graph).
+        Returns (tau, updating passes, evaluations)."""
+        if _is_torch(members):
+            ids = members.to(__import__("torch").int32).contiguous()
+        else:
+            ids = np.ascontiguousarray(np.asarray(members, dtype=np.uint32))
+        tau = self._alloc(self.num_r) if out is None else out
+        it, ev = ctypes.c_int32(), ctypes.c_int64()
+        _check(load().nd_and_partial(self._h, _ptr(ids), len(ids), int(_is_torch(ids)), _ptr(tau),
+                                     int(max_iters), ctypes.byref(it), ctypes.byref(ev), self._sp(stream)),
+               "nd_and_partial")
+        return tau, it.value, ev.value
+
+    def and_until(self, active_ratio: float, max_iters: int = 1 << 30, out=None, stream=None):
+        """AND with the active-ratio stopping rule.  Returns (tau, passes, evaluations, stopped)."""
+        tau = self._alloc(self.num_r) if out is None else out
+        it, ev, stop = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int()
+        _check(load().nd_and_until(self._h, float(active_ratio), _ptr(tau), int(self.on_device), int(max_iters),
+                                   ctypes.byref(it), ctypes.byref(ev), ctypes.byref(stop), self._sp(stream)),
+               "nd_and_until")
+        return tau, it.value, ev.value, bool(stop.value)
 
     def iterate_k(self, mode: str, k: int, tau=None, stream=None):
         """At most k passes of mode ('snd', 'and', 'and_nn') from tau (or d_s).
@@ -318,6 +345,18 @@ def truss_classic(kappa3, stream=None):
     _check(load().nd_truss_classic(_ptr(src), len(kappa3), _ptr(out), int(on_device),
                                    _stream_ptr(stream)), "nd_truss_classic")
     return out
+
+
+def count_equal(a, b, stream=None) -> int:
+    """nd_count_equal: positions where a == b (both numpy or both CUDA tensors)."""
+    on_device = _is_torch(a)
+    if not on_device:
+        a = np.ascontiguousarray(a, dtype=np.int32)
+        b = np.ascontiguousarray(b, dtype=np.int32)
+    out = ctypes.c_int64()
+    _check(load().nd_count_equal(_ptr(a), _ptr(b), len(a), int(on_device), ctypes.byref(out), _stream_ptr(stream)),
+           "nd_count_equal")
+    return out.value
 
 
 def prof_enable(on: bool = True):

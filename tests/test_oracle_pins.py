@@ -333,3 +333,32 @@ def test_rejects_invalid_csr():
     rp2, col2 = G.toy_core_graph()
     with pytest.raises(RuntimeError):
         oracle.Graph(rp2, col2, 1, 3)        # unsupported (r, s)
+
+
+# ------------------------------------------------------------- PartialAnd
+
+@pytest.mark.parametrize("rs", RS)
+def test_partial_and_pins(rs):
+    rng = np.random.default_rng(23)
+    for rp, col in _medium_graphs():
+        g = oracle.Graph(rp, col, *rs)
+        if g.num_r == 0:
+            continue
+        kap = g.peel()
+        ds = g.s_degree()
+        everyone = np.ones(g.num_r, bool)
+        assert (g.partial_and(everyone)[0] == kap).all()        # P = all: plain AND
+        nobody = np.zeros(g.num_r, bool)
+        assert (g.partial_and(nobody)[0] == ds).all()           # P = empty: d_s untouched
+        small = rng.random(g.num_r) < 0.3
+        big = small | (rng.random(g.num_r) < 0.4)
+        t_small = g.partial_and(small)[0]
+        t_big = g.partial_and(big)[0]
+        assert (t_small[~small] == ds[~small]).all()
+        assert (kap <= t_big).all() and (t_big <= t_small).all()  # more members, tighter
+        # any order, with or without notification, and the synchronous form
+        # reach the same fixed point
+        order = rng.permutation(g.num_r)
+        assert (g.partial_and(small, order=order)[0] == t_small).all()
+        assert (g.partial_and(small, notify=False)[0] == t_small).all()
+        assert (g.partial_snd(small)[0] == t_small).all()
