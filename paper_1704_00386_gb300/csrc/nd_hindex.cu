@@ -5,7 +5,8 @@
 // four degree buckets (by default d_s in [1,8], [9,64], [65,2048], >2048)
 // and evaluated by a group of 4 or 8 lanes, a warp, or a whole CTA.  The CTA
 // rows are taken one per block from a per-pass counter; the rest are warp
-// tasks interleaved statically over all warps.  A group of 4 or 8:
+// tasks, taken in chunks of consecutive tasks per warp from a second
+// counter.  A group of 4 or 8:
 //   1. streams the r-clique's incidence row (coalesced, q ids per s-clique),
 //      gathers the q tau values of each s-clique and keeps
 //      rho = min(...) in registers (Def. 4, step 1);
@@ -43,10 +44,14 @@ constexpr int kThreads = 256;
 #define ND_WARP_UNROLL 4  // streamed incidences in flight per lane (warp / CTA rows)
 #endif
 constexpr int kWarpUnroll = ND_WARP_UNROLL;
+#ifndef ND_WARP_CHUNK
+#define ND_WARP_CHUNK 16  // consecutive warp tasks per counter grab
+#endif
+constexpr int kWarpChunk = ND_WARP_CHUNK;
 
 // Work of one pass: rows longer than the CTA threshold are taken one per
-// block from a per-pass counter; all other rows form warp tasks that are
-// interleaved statically over the warps of the persistent grid.
+// block from a per-pass counter; all other rows form warp tasks that warps
+// take in chunks from a second counter.
 
 struct SweepParams {
     const int64_t* __restrict__ inc_ptr;
@@ -59,7 +64,7 @@ struct SweepParams {
     uint32_t* next;       // and the frontier written for the next pass
     const uint32_t* members;  // PartialAnd: only members are notified (null = everyone)
     unsigned long long* ctr;         // this pass: [0] changed, [1] evaluated, [2] next CTA row,
-                                     // [3] incidences of the evaluated rows
+                                     // [3] incidences of the evaluated rows, [4] next warp chunk
     const unsigned long long* prev;  // previous pass (null on the first)
 };
 
@@ -381,34 +386,43 @@ __global__ void __launch_bounds__(kThreads, ND_PASS_MIN_BLOCKS) k_pass(SweepPara
         }
     }
     // phase 2: warp tasks (one warp row, four 8-lane rows or eight 4-lane
-    // rows), longest first, interleaved statically over every warp of the
-    // grid: no barrier and no shared counter, and each warp gets an equal
-    // share of every bucket
+    // rows), longest first.  Each warp takes chunks of kWarpChunk
+    // consecutive tasks from a per-pass counter (one atomic per chunk, no
+    // barrier): consecutive r-cliques share a vertex and gather from the
+    // same part of tau, and dynamic chunks keep the warps balanced even when
+    // only a scattered subset of r-cliques is active (AND).
     const int64_t n2 = P.hi[2] - P.lo[2];
     const int64_t t1 = (P.hi[1] - P.lo[1] + 3) / 4;
     const int64_t t0 = (P.hi[0] - P.lo[0] + 7) / 8;
     const int64_t tasks = n2 + t1 + t0;
-    const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
-    int64_t t = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
-    if (t < n2) {
-        // warp rows: the next task's work item is loaded before this one runs
-        nd_item it = load_item(P.items, P.lo[2] + t);
-        while (t < n2) {
-            const int64_t tn = t + warps;
-            nd_item nx;
-            if (tn < n2) nx = load_item(P.items, P.lo[2] + tn);
-            run_warp_row<Q, AND, NOTIFY>(P, it, bins[threadIdx.x >> 5], changed, evals, incs);
-            it = nx;
-            t = tn;
+    const int lane32 = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long c = 0;
+        if (lane32 == 0) c = atomicAdd(P.ctr + 4, 1ull);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        int64_t t = (int64_t)c * kWarpChunk;
+        if (t >= tasks) break;
+        const int64_t te = min(t + (int64_t)kWarpChunk, tasks);
+        const int64_t e2 = min(te, n2);
+        if (t < e2) {
+            // warp rows: the next row's work item is loaded before this one runs
+            nd_item it = load_item(P.items, P.lo[2] + t);
+            while (t < e2) {
+                nd_item nx;
+                if (t + 1 < e2) nx = load_item(P.items, P.lo[2] + t + 1);
+                run_warp_row<Q, AND, NOTIFY>(P, it, bins[threadIdx.x >> 5], changed, evals, incs);
+                it = nx;
+                ++t;
+            }
         }
-    }
-    for (; t < tasks; t += warps) {
-        if (t < n2 + t1) {
-            const int64_t first = P.lo[1] + 4 * (t - n2);
-            run_groups<Q, 8, 8, AND, NOTIFY>(P, first, min(first + 4, P.hi[1]), changed, evals, incs);
-        } else {
-            const int64_t first = P.lo[0] + 8 * (t - n2 - t1);
-            run_groups<Q, 4, 2, AND, NOTIFY>(P, first, min(first + 8, P.hi[0]), changed, evals, incs);
+        for (; t < te; ++t) {
+            if (t < n2 + t1) {
+                const int64_t first = P.lo[1] + 4 * (t - n2);
+                run_groups<Q, 8, 8, AND, NOTIFY>(P, first, min(first + 4, P.hi[1]), changed, evals, incs);
+            } else {
+                const int64_t first = P.lo[0] + 8 * (t - n2 - t1);
+                run_groups<Q, 4, 2, AND, NOTIFY>(P, first, min(first + 8, P.hi[0]), changed, evals, incs);
+            }
         }
     }
     __shared__ unsigned long long s_ch[kThreads / 32], s_ev[kThreads / 32], s_in[kThreads / 32];
@@ -491,7 +505,8 @@ void plan_chunks(const nd_incidence* h, SweepParams& P) {
     }
 }
 
-// work units of a pass: CTA rows + warp tasks (see k_pass)
+// work units of a pass: CTA rows + warp tasks (see k_pass); the grid never
+// exceeds what the work needs
 int64_t pass_units(const SweepParams& P) {
     return (P.hi[3] - P.lo[3]) + (P.hi[2] - P.lo[2]) + (P.hi[1] - P.lo[1] + 3) / 4 + (P.hi[0] - P.lo[0] + 7) / 8;
 }

@@ -101,7 +101,7 @@ struct nd_incidence {
 
 // passes are enqueued in batches of ND_BATCH; the per-pass counters (ND_SLOT
 // u64 each) live in two halves of ND_BATCH slots used by alternate batches
-enum { ND_BATCH = 16, ND_RING = 2 * ND_BATCH, ND_SLOT = 4 };
+enum { ND_BATCH = 16, ND_RING = 2 * ND_BATCH, ND_SLOT = 6 };
 
 // wait for a stream with a time limit (ND_E_TIMEOUT past it)
 nd_status nd_wait(cudaStream_t st, double seconds);
