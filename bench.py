@@ -271,10 +271,13 @@ def run_ours(args, rank, world, local_rank):
 
     # ----- roofline of the dominant kernel
     # Algorithmic (compulsory) DRAM bytes of a pass: the incidence ids it
-    # streams (4q B each, counted by the kernel) + 24 B per evaluated r-clique
-    # (8 B row offsets, 4 B work item, 4 B own tau, 4 B tau write, 4 B first
-    # touch of its tau as a gathered value).  The q gathered tau values per
-    # incidence are L2 hits while tau fits in L2, so they are not DRAM bytes.
+    # streams (4q B each, counted by the kernel) + per evaluated r-clique
+    # 24 B (16 B work item, 4 B own tau, 4 B tau write; the first touch of
+    # its value as a gathered tau is within the 4 B write) and, for (2,3),
+    # 20 B more (8 B CSR positions of the edge, 8 B for its two copies in
+    # the gather layout, 4 B first touch of the second copy).  The q gathered
+    # tau values per incidence are L2 hits while tau fits in L2, so they are
+    # not DRAM bytes.
     info = infos[-1]
     peak, peak_kind = load_peaks()
     top = max(prof.items(), key=lambda kv: kv[1][1])
@@ -282,10 +285,11 @@ def run_ours(args, rank, world, local_rank):
     N_R, M, q = info["num_r"], info["M"], info["q"]
     if name in ("snd_pass", "and_pass"):
         key = "snd" if name == "snd_pass" else "and"
-        tot_bytes = sum(4.0 * q * sum(i[key + "_inc"]) + 24.0 * sum(i[key + "_rows"]) for i in infos)
+        row_bytes = 44.0 if q == 2 else 24.0
+        tot_bytes = sum(4.0 * q * sum(i[key + "_inc"]) + row_bytes * sum(i[key + "_rows"]) for i in infos)
         eff = sum(len(i[key + "_inc"]) for i in infos)
         per_launch = tot_bytes / max(eff, 1)
-        units = (f"4q B x incidences streamed + 24 B x r-cliques evaluated, summed over the {eff} "
+        units = (f"4q B x incidences streamed + {row_bytes:.0f} B x r-cliques evaluated, summed over the {eff} "
                  f"effective {key.upper()} passes of the timed steps")
     else:
         eff = launches

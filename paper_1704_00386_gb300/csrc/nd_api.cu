@@ -164,7 +164,8 @@ void nd_free(nd_incidence* h) {
     cudaStream_t st = h->last_stream;
     cudaStreamSynchronize(st);
     void* ptrs[] = {h->nlow, h->up_start, h->eid, h->e_u, h->e_v, h->tri_ptr, h->tri_w, h->tri_e,
-                    h->items, h->tau[0], h->tau[1], h->front[0], h->front[1], h->counters};
+                    h->items, h->tau[0], h->tau[1], h->front[0], h->front[1], h->counters,
+                    h->mirror, h->e_pos, h->tg[0], h->tg[1]};
     for (void* p : ptrs) nd_release(p, st);
     for (auto& row : h->pass_graph)
         for (auto& ex : row)

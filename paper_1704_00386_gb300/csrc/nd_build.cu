@@ -83,11 +83,14 @@ __global__ void k_validate_split(int64_t n, int64_t nnz, const int64_t* __restri
 // ---- canonical edge ids (one warp per vertex) ------------------------------
 // Edge (u,v), u < v, gets id up_start[u] + (rank of v among u's larger
 // neighbours): lexicographic order.  eid[p] is the id of the edge at CSR
-// position p, for both directions.
+// position p, for both directions.  For the (2,3) adjacency layout it also
+// writes mirror[p] (the position of the reverse entry) and, per edge (x,y)
+// with x < y, e_pos = (P(x,y), P(y,x)).
 __global__ void k_edge_ids(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                            const int32_t* __restrict__ nlow, const int64_t* __restrict__ up_start,
                            uint32_t* __restrict__ eid, int32_t* __restrict__ e_u,
-                           int32_t* __restrict__ e_v) {
+                           int32_t* __restrict__ e_v, uint32_t* __restrict__ mirror,
+                           uint2* __restrict__ e_pos) {
     const int lane = threadIdx.x & 31;
     for (int64_t u = warp_id_global(); u < n; u += warp_count_global()) {
         const int64_t b = rp[u], e = rp[u + 1];
@@ -103,7 +106,14 @@ __global__ void k_edge_ids(int64_t n, const int64_t* __restrict__ rp, const int3
             } else {
                 int64_t vfirst = rp[v] + nlow[v];
                 int64_t pos = lower_bound_i32(col, vfirst, rp[v + 1], (int32_t)u);
-                eid[p] = (uint32_t)(up_start[v] + (pos - vfirst));
+                const int64_t id = up_start[v] + (pos - vfirst);
+                eid[p] = (uint32_t)id;
+                if (mirror) {
+                    // edge (v,u), v < u: entry pos = P(v,u), entry p = P(u,v)
+                    mirror[p] = (uint32_t)pos;
+                    mirror[pos] = (uint32_t)p;
+                    e_pos[id] = make_uint2((uint32_t)pos, (uint32_t)p);
+                }
             }
         }
     }
@@ -122,11 +132,13 @@ __device__ __forceinline__ bool precedes(int64_t du, int32_t u, int64_t dv, int3
 }
 
 // one warp per vertex: count / list the out-neighbours of u in id order
+// (with out_pos: also the CSR positions of the entry and of its reverse)
 template <bool FILL>
 __global__ void k_orient(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                          const uint32_t* __restrict__ eid, int64_t* __restrict__ out_ptr,
                          int32_t* __restrict__ out_col, uint32_t* __restrict__ out_eid,
-                         int32_t* __restrict__ out_src) {
+                         int32_t* __restrict__ out_src, const uint32_t* __restrict__ mirror,
+                         uint32_t* __restrict__ out_pos, uint32_t* __restrict__ out_mir) {
     const int lane = threadIdx.x & 31;
     for (int64_t u = warp_id_global(); u < n; u += warp_count_global()) {
         const int64_t b = rp[u], e = rp[u + 1], du = e - b;
@@ -146,6 +158,10 @@ __global__ void k_orient(int64_t n, const int64_t* __restrict__ rp, const int32_
                 out_col[slot] = v;
                 out_eid[slot] = __ldg(eid + p);
                 out_src[slot] = (int32_t)u;
+                if (out_pos) {
+                    out_pos[slot] = (uint32_t)p;
+                    out_mir[slot] = __ldg(mirror + p);
+                }
             }
             cnt += __popc(bal);
         }
@@ -153,16 +169,21 @@ __global__ void k_orient(int64_t n, const int64_t* __restrict__ rp, const int32_
     }
 }
 
-// one warp per oriented edge u -> v: the triangles {u, v, w}, w in out(u) /\ out(v)
-template <bool FILL>
+// one warp per oriented edge u -> v: the triangles {u, v, w}, w in out(u) /\ out(v).
+// ADJ: the entries are CSR positions, each pair ordered by its edge's
+// canonical endpoints (the entry of the smaller endpoint first).
+template <bool FILL, bool ADJ>
 __global__ void k_tri_oriented(int64_t m, const int64_t* __restrict__ out_ptr,
                                const int32_t* __restrict__ out_col, const uint32_t* __restrict__ out_eid,
-                               const int32_t* __restrict__ out_src, unsigned long long* __restrict__ ctr,
+                               const int32_t* __restrict__ out_src, const uint32_t* __restrict__ out_pos,
+                               const uint32_t* __restrict__ out_mir, unsigned long long* __restrict__ ctr,
                                uint2* __restrict__ inc) {
     const int lane = threadIdx.x & 31;
     for (int64_t k = warp_id_global(); k < m; k += warp_count_global()) {
         const int32_t u = out_src[k], v = out_col[k];
         const uint32_t e_uv = out_eid[k];
+        uint32_t Puv = 0, Pvu = 0;
+        if (ADJ) { Puv = __ldg(out_pos + k); Pvu = __ldg(out_mir + k); }
         int64_t ab = out_ptr[u], ae = out_ptr[u + 1], bb = out_ptr[v], be = out_ptr[v + 1];
         bool a_is_u = true;
         if (ae - ab > be - bb) {
@@ -174,8 +195,9 @@ __global__ void k_tri_oriented(int64_t m, const int64_t* __restrict__ out_ptr,
             const int64_t p = base + lane;
             bool found = false;
             int64_t pb = 0;
+            int32_t x = 0;
             if (p < ae) {
-                const int32_t x = __ldg(out_col + p);
+                x = __ldg(out_col + p);
                 pb = lower_bound_i32(out_col, lo, be, x);
                 found = (pb < be) && (__ldg(out_col + pb) == x);
             }
@@ -199,15 +221,139 @@ __global__ void k_tri_oriented(int64_t m, const int64_t* __restrict__ out_ptr,
                     if (lane == 0) s0 = atomicAdd(ctr + e_uv, (unsigned long long)nf);
                     s0 = __shfl_sync(kFull, s0, 0);
                     if (found) {
-                        inc[s0 + __popc(bal & lanemask_lt())] = make_uint2(e_uw, e_vw);
-                        inc[atomicAdd(ctr + e_uw, 1ull)] = make_uint2(e_uv, e_vw);
-                        inc[atomicAdd(ctr + e_vw, 1ull)] = make_uint2(e_uv, e_uw);
+                        uint2 r_uv, r_uw, r_vw;
+                        if (ADJ) {
+                            // third vertex w = x; positions P(.,.) of the six entries
+                            const uint32_t pa = __ldg(out_pos + p), ma = __ldg(out_mir + p);
+                            const uint32_t pbp = __ldg(out_pos + pb), mb = __ldg(out_mir + pb);
+                            const uint32_t Puw = a_is_u ? pa : pbp, Pwu = a_is_u ? ma : mb;
+                            const uint32_t Pvw = a_is_u ? pbp : pa, Pwv = a_is_u ? mb : ma;
+                            r_uv = u < v ? make_uint2(Puw, Pvw) : make_uint2(Pvw, Puw);
+                            r_uw = u < x ? make_uint2(Puv, Pwv) : make_uint2(Pwv, Puv);
+                            r_vw = v < x ? make_uint2(Pvu, Pwu) : make_uint2(Pwu, Pvu);
+                        } else {
+                            r_uv = make_uint2(e_uw, e_vw);
+                            r_uw = make_uint2(e_uv, e_vw);
+                            r_vw = make_uint2(e_uv, e_uw);
+                        }
+                        inc[s0 + __popc(bal & lanemask_lt())] = r_uv;
+                        inc[atomicAdd(ctr + e_uw, 1ull)] = r_uw;
+                        inc[atomicAdd(ctr + e_vw, 1ull)] = r_vw;
                     }
                 }
             }
             const int64_t last_pb = __shfl_sync(kFull, pb, 31);
             if (base + 32 <= ae) lo = last_pb;
         }
+    }
+}
+
+// ---- (2,3) adjacency layout: order each row by its third vertex -----------
+// The entries of the row of edge (x,y) are pairs (P(x,w), P(y,w)) over the
+// triangles {x,y,w}, in fill order.  Both components grow with w, so the
+// rank of an entry is the rank of its component in the shorter of the two
+// adjacency lists, N(s): one bit per position of N(s) marks the row's
+// entries, and rank = (bits set in earlier words) + (bits below it in its
+// word).  O(d + deg(s)/32) per row, no comparison sort.  Rows up to 32
+// entries are ranked by comparing keys across the warp instead.  One warp
+// per row; the bit and prefix words sit in shared memory (kRankWords per
+// warp); a row whose shorter list needs more words is left to the overflow
+// pass, which uses global scratch.
+constexpr int kRankWarps = 4;
+#ifndef ND_RANK_WORDS
+#define ND_RANK_WORDS 2048
+#endif
+constexpr int kRankWords = ND_RANK_WORDS;
+
+__device__ __forceinline__ void rank_row(const uint2* __restrict__ src, uint2* __restrict__ dst, int64_t jb,
+                                         int64_t d, int comp, uint32_t base, int64_t nw,
+                                         uint32_t* __restrict__ bm, uint32_t* __restrict__ pre) {
+    const int lane = threadIdx.x & 31;
+    if (d <= 32) {
+        uint2 e = make_uint2(0u, 0u);
+        uint32_t key = 0xffffffffu;
+        if (lane < d) {
+            e = src[jb + lane];
+            key = comp ? e.y : e.x;
+        }
+        int rank = 0;
+        for (int o = 0; o < d; ++o) rank += (__shfl_sync(kFull, key, o) < key);
+        if (lane < d) dst[jb + rank] = e;
+        return;
+    }
+    for (int64_t w = lane; w < nw; w += 32) bm[w] = 0u;
+    __syncwarp();
+    for (int64_t j = jb + lane; j < jb + d; j += 32) {
+        const uint2 e = src[j];
+        const uint32_t k = (comp ? e.y : e.x) - base;
+        atomicOr(bm + (k >> 5), 1u << (k & 31));
+    }
+    __syncwarp();
+    uint32_t run = 0;
+    for (int64_t w0 = 0; w0 < nw; w0 += 32) {
+        const int64_t w = w0 + lane;
+        const uint32_t c = w < nw ? (uint32_t)__popc(bm[w]) : 0u;
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (w < nw) pre[w] = run + incl - c;
+        run += __shfl_sync(kFull, incl, 31);
+    }
+    __syncwarp();
+    for (int64_t j = jb + lane; j < jb + d; j += 32) {
+        const uint2 e = src[j];
+        const uint32_t k = (comp ? e.y : e.x) - base;
+        const uint32_t rank = pre[k >> 5] + (uint32_t)__popc(bm[k >> 5] & ((1u << (k & 31)) - 1u));
+        dst[jb + rank] = e;
+    }
+    __syncwarp();
+}
+
+// BIG = false: every row, bits in shared memory; rows that need more than
+// kRankWords words are appended to `over` (count in over_ctr[0], largest
+// word count in over_ctr[1]).  BIG = true: the rows in `over`, bits in
+// global scratch of 2 * scratch_words words per warp.
+template <bool BIG>
+__global__ void __launch_bounds__(32 * kRankWarps)
+k_row_rank(int64_t N, const int64_t* __restrict__ inc_ptr, const int32_t* __restrict__ e_u,
+           const int32_t* __restrict__ e_v, const int64_t* __restrict__ rp, const uint2* __restrict__ src,
+           uint2* __restrict__ dst, uint32_t* __restrict__ over, unsigned long long* __restrict__ over_ctr,
+           uint32_t* __restrict__ scratch, int64_t scratch_words) {
+    extern __shared__ uint32_t rank_smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    uint32_t *bm, *pre;
+    if (BIG) {
+        bm = scratch + (size_t)2 * scratch_words * warp_id_global();
+        pre = bm + scratch_words;
+    } else {
+        bm = rank_smem + (size_t)2 * kRankWords * wib;
+        pre = bm + kRankWords;
+    }
+    const int64_t rows = BIG ? (int64_t)over_ctr[0] : N;
+    for (int64_t i = warp_id_global(); i < rows; i += warp_count_global()) {
+        const int64_t R = BIG ? (int64_t)over[i] : i;
+        const int64_t jb = inc_ptr[R], d = inc_ptr[R + 1] - jb;
+        if (d <= 1) {
+            if (d == 1 && lane == 0) dst[jb] = src[jb];
+            continue;
+        }
+        const int32_t x = e_u[R], y = e_v[R];
+        const int64_t dx = rp[x + 1] - rp[x], dy = rp[y + 1] - rp[y];
+        const int comp = dx <= dy ? 0 : 1;
+        const uint32_t base = (uint32_t)rp[comp ? y : x];
+        const int64_t nw = ((comp ? dy : dx) + 31) / 32;
+        if (!BIG && d > 32 && nw > kRankWords) {
+            if (lane == 0) {
+                over[atomicAdd(over_ctr, 1ull)] = (uint32_t)R;
+                atomicMax(over_ctr + 1, (unsigned long long)nw);
+            }
+            continue;
+        }
+        rank_row(src, dst, jb, d, comp, base, nw, bm, pre);
     }
 }
 
@@ -556,11 +702,21 @@ nd_status nd_build_edges(nd_incidence* h, cudaStream_t st) {
     ND_TRY(nd_alloc((void**)&h->eid, sizeof(uint32_t) * (h->nnz > 0 ? h->nnz : 1), st, h));
     ND_TRY(nd_alloc((void**)&h->e_u, sizeof(int32_t) * (h->m > 0 ? h->m : 1), st, h));
     ND_TRY(nd_alloc((void**)&h->e_v, sizeof(int32_t) * (h->m > 0 ? h->m : 1), st, h));
+    if (h->r == 2) {
+        // (2,3) incidence entries are CSR positions (uint32)
+        if (h->nnz >= (int64_t)UINT32_MAX) {
+            nd_set_error("(2,3) needs fewer than 2^32-1 CSR entries");
+            return ND_E_TOO_LARGE;
+        }
+        h->adj = true;
+        ND_TRY(nd_alloc((void**)&h->mirror, sizeof(uint32_t) * (h->nnz > 0 ? h->nnz : 1), st, h));
+        ND_TRY(nd_alloc((void**)&h->e_pos, sizeof(uint2) * (h->m > 0 ? h->m : 1), st, h));
+    }
     if (h->n > 0 && h->nnz > 0) {
         nd_prof_scope ps("edge_ids", st);
         int blocks = nd_blocks_for(h->n * 32, kThreads, grid_cap(h) * 4);
         k_edge_ids<<<blocks, kThreads, 0, st>>>(h->n, h->rp, h->col, h->nlow, h->up_start, h->eid,
-                                                h->e_u, h->e_v);
+                                                h->e_u, h->e_v, h->mirror, h->e_pos);
         ND_CUDA(cudaGetLastError());
     }
     return ND_OK;
@@ -570,8 +726,9 @@ nd_status nd_build_edges(nd_incidence* h, cudaStream_t st) {
 struct nd_oriented {
     nd_tmp<int64_t> out_ptr;
     nd_tmp<int32_t> out_col, out_src;
-    nd_tmp<uint32_t> out_eid;
-    explicit nd_oriented(cudaStream_t st) : out_ptr(st), out_col(st), out_src(st), out_eid(st) {}
+    nd_tmp<uint32_t> out_eid, out_pos, out_mir;
+    explicit nd_oriented(cudaStream_t st)
+        : out_ptr(st), out_col(st), out_src(st), out_eid(st), out_pos(st), out_mir(st) {}
 };
 
 static nd_status orient_graph(nd_incidence* h, nd_oriented* o, cudaStream_t st) {
@@ -580,20 +737,72 @@ static nd_status orient_graph(nd_incidence* h, nd_oriented* o, cudaStream_t st) 
     ND_TRY(o->out_col.alloc(m));
     ND_TRY(o->out_src.alloc(m));
     ND_TRY(o->out_eid.alloc(m));
+    if (h->adj) {
+        ND_TRY(o->out_pos.alloc(m));
+        ND_TRY(o->out_mir.alloc(m));
+    }
     ND_CUDA(cudaMemsetAsync(o->out_ptr.p + n, 0, sizeof(int64_t), st));
     const int vblocks = nd_blocks_for(n * 32, kThreads, grid_cap(h) * 4);
     if (n > 0) {
         nd_prof_scope ps("orient", st);
-        k_orient<false><<<vblocks, kThreads, 0, st>>>(n, h->rp, h->col, h->eid, o->out_ptr, nullptr, nullptr, nullptr);
+        k_orient<false><<<vblocks, kThreads, 0, st>>>(n, h->rp, h->col, h->eid, o->out_ptr, nullptr, nullptr, nullptr,
+                                                      nullptr, nullptr, nullptr);
         ND_CUDA(cudaGetLastError());
     }
     ND_TRY(nd_scan_i64(o->out_ptr, n, st));
     if (n > 0) {
         nd_prof_scope ps("orient", st);
         k_orient<true><<<vblocks, kThreads, 0, st>>>(n, h->rp, h->col, h->eid, o->out_ptr, o->out_col, o->out_eid,
-                                                     o->out_src);
+                                                     o->out_src, h->mirror, h->adj ? o->out_pos.p : nullptr,
+                                                     o->out_mir);
         ND_CUDA(cudaGetLastError());
     }
+    return ND_OK;
+}
+
+// order the rows of the (2,3) adjacency layout by w (see k_row_rank); if
+// the second buffer does not fit, the rows stay in fill order (the h-index
+// does not depend on it; the gathers are only less local)
+static nd_status sort_tri_rows(nd_incidence* h, cudaStream_t st) {
+    const int64_t N = h->num_r, M = h->num_inc;
+    uint2* dst = nullptr;
+    if (cudaMallocAsync((void**)&dst, sizeof(uint2) * (size_t)M, st) != cudaSuccess) {
+        cudaGetLastError();
+        return ND_OK;
+    }
+    nd_tmp<uint32_t> over(st);
+    nd_tmp<unsigned long long> over_ctr(st);
+    nd_status rc = over.alloc(N);
+    if (rc == ND_OK) rc = over_ctr.alloc(2);
+    if (rc != ND_OK) { cudaFreeAsync(dst, st); return rc; }
+    ND_CUDA(cudaMemsetAsync(over_ctr, 0, sizeof(unsigned long long) * 2, st));
+    const size_t smem = sizeof(uint32_t) * 2 * kRankWords * kRankWarps;
+    ND_CUDA(cudaFuncSetAttribute(k_row_rank<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+        nd_prof_scope ps("row_rank", st);
+        const int blocks = nd_blocks_for(N * 32, 32 * kRankWarps, grid_cap(h) * 8);
+        k_row_rank<false><<<blocks, 32 * kRankWarps, smem, st>>>(N, h->inc_ptr, h->e_u, h->e_v, h->rp,
+                                                                  (const uint2*)h->inc, dst, over, over_ctr,
+                                                                  nullptr, 0);
+        ND_CUDA(cudaGetLastError());
+    }
+    unsigned long long hc[2] = {0, 0};
+    ND_CUDA(cudaMemcpyAsync(hc, over_ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    ND_TRY(nd_wait(st, 600.0));
+    if (hc[0] > 0) {
+        // rows whose shorter adjacency list needs more than kRankWords words
+        const int warps = 64;
+        nd_tmp<uint32_t> scratch(st);
+        ND_TRY(scratch.alloc((int64_t)2 * (int64_t)hc[1] * warps));
+        nd_prof_scope ps("row_rank", st);
+        k_row_rank<true><<<warps / kRankWarps, 32 * kRankWarps, 0, st>>>(
+            N, h->inc_ptr, h->e_u, h->e_v, h->rp, (const uint2*)h->inc, dst, over, over_ctr, scratch,
+            (int64_t)hc[1]);
+        ND_CUDA(cudaGetLastError());
+    }
+    nd_release(h->inc, st);
+    h->inc = reinterpret_cast<uint32_t*>(dst);
+    h->rows_sorted = true;
     return ND_OK;
 }
 
@@ -608,8 +817,9 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
     const int eblocks = nd_blocks_for(m * 32, kThreads, grid_cap(h) * 4);
     {
         nd_prof_scope ps("tri_count", st);
-        k_tri_oriented<false><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid, o.out_src,
-                                                            (unsigned long long*)h->inc_ptr, nullptr);
+        k_tri_oriented<false, false><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid, o.out_src,
+                                                                   nullptr, nullptr,
+                                                                   (unsigned long long*)h->inc_ptr, nullptr);
         ND_CUDA(cudaGetLastError());
     }
     ND_TRY(nd_scan_i64(h->inc_ptr, m, st));
@@ -620,9 +830,19 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
         ND_TRY(cursor.alloc(m));
         ND_CUDA(cudaMemcpyAsync(cursor, h->inc_ptr, sizeof(int64_t) * m, cudaMemcpyDeviceToDevice, st));
         nd_prof_scope ps("tri_fill", st);
-        k_tri_oriented<true><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid, o.out_src, cursor,
-                                                           (uint2*)h->inc);
+        if (h->adj)
+            k_tri_oriented<true, true><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid, o.out_src,
+                                                                     o.out_pos, o.out_mir, cursor, (uint2*)h->inc);
+        else
+            k_tri_oriented<true, false><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid,
+                                                                      o.out_src, nullptr, nullptr, cursor,
+                                                                      (uint2*)h->inc);
         ND_CUDA(cudaGetLastError());
+    }
+    if (h->adj) {
+        nd_release(h->mirror, st);  // build only
+        h->mirror = nullptr;
+        if (h->num_inc > 0) ND_TRY(sort_tri_rows(h, st));
     }
     return ND_OK;
 }

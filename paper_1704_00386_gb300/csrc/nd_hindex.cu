@@ -58,6 +58,12 @@ struct SweepParams {
     const uint32_t* __restrict__ inc;
     const int32_t* tin;   // SND: tau of the previous pass; AND: same array as tout
     int32_t* tout;
+    // gathers: (2,3) reads tau by CSR position from gin and writes both
+    // entries of an updated edge to gout (e_pos); otherwise gin = tin
+    const int32_t* gin;
+    int32_t* gout;
+    const uint2* __restrict__ epos;
+    const uint32_t* __restrict__ eid;  // CSR position -> edge id (notification)
     const nd_item* __restrict__ items;
     int64_t lo[ND_NB], hi[ND_NB];  // bucket ranges in items
     const uint32_t* cur;  // AND + notification: frontier read in this pass
@@ -80,7 +86,8 @@ __device__ __forceinline__ int32_t ld_tau(const int32_t* p) {
     return *p;
 }
 
-// rho(S,R) for the s-clique at incidence j: min of the other r-cliques' tau.
+// rho(S,R) for the s-clique at incidence j: min of the other r-cliques' tau
+// (for (2,3) the entries index the CSR-position copy of tau).
 // SND reads each row once per pass, so its ids are loaded evict-first and do
 // not push the gathered tau values out of L2.  AND re-reads the row of a
 // changed r-clique to notify its neighbours, so its ids are cached normally.
@@ -253,6 +260,17 @@ __device__ __forceinline__ int32_t cta_hindex(const uint32_t* __restrict__ inc, 
     return lo;
 }
 
+// the new tau of R; (2,3) also writes it to both CSR entries of the edge
+template <int Q>
+__device__ __forceinline__ void store_tau(const SweepParams& P, uint32_t R, int32_t h) {
+    P.tout[R] = h;
+    if (Q == 2) {
+        const uint2 ep = __ldg(P.epos + R);
+        P.gout[ep.x] = h;
+        P.gout[ep.y] = h;
+    }
+}
+
 // notify every neighbour whose tau could still depend on R (Alg. 3, orange
 // lines): set its next-frontier bit if h <= tau(R').  A neighbour whose bit
 // is already set needs nothing, so the bitmap word (2 MB for 16M r-cliques,
@@ -266,7 +284,8 @@ __device__ __forceinline__ void notify_row(const SweepParams& P, int64_t jb, int
     for (int64_t j = jb + first; j < je; j += step) {
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
-            const uint32_t Rp = __ldg(P.inc + Q * j + k);
+            const uint32_t id = __ldg(P.inc + Q * j + k);
+            const uint32_t Rp = Q == 2 ? __ldg(P.eid + id) : id;  // (2,3): entries are CSR positions
             const uint32_t bit = 1u << (Rp & 31);
             if (P.members && !(__ldg(P.members + (Rp >> 5)) & bit)) continue;  // PartialAnd
             uint32_t* w = P.next + (Rp >> 5);
@@ -307,12 +326,12 @@ __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, 
     const int64_t jb = it.jb, je = it.jb + it.d;
     if (AND && NOTIFY && !((__ldg(P.cur + (R >> 5)) >> (R & 31)) & 1u)) return;
     const int32_t t = ld_tau<!AND>(P.tin + R);
-    const int32_t h = group_hindex<Q, G, C, !AND>(g, P.inc, P.tin, jb, je, t);
+    const int32_t h = group_hindex<Q, G, C, !AND>(g, P.inc, P.gin, jb, je, t);
     if (lane == 0) {
         evals++;
         incs += it.d;
         if (h != t) changed++;
-        if (!AND || h != t) P.tout[R] = h;
+        if (!AND || h != t) store_tau<Q>(P, R, h);
     }
     if (AND && NOTIFY && h != t) notify_row<Q>(P, jb, je, h, lane, G, group_mask<G>());
 }
@@ -327,12 +346,12 @@ __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item
     if (AND && NOTIFY && !((__ldg(P.cur + (R >> 5)) >> (R & 31)) & 1u)) return;
     const int32_t t = ld_tau<!AND>(P.tin + R);
     const int64_t jb = it.jb, je = it.jb + it.d;
-    const int32_t h = warp_hindex<Q, !AND>(P.inc, P.tin, jb, je, t, bins);
+    const int32_t h = warp_hindex<Q, !AND>(P.inc, P.gin, jb, je, t, bins);
     if (lane == 0) {
         evals++;
         incs += it.d;
         if (h != t) changed++;
-        if (!AND || h != t) P.tout[R] = h;
+        if (!AND || h != t) store_tau<Q>(P, R, h);
     }
     if (AND && NOTIFY && h != t) notify_row<Q>(P, jb, je, h, lane, 32, 0xffffffffu);
 }
@@ -350,12 +369,12 @@ __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int
         }
         const int32_t t = ld_tau<!AND>(P.tin + R);
         const int64_t jb = it.jb, je = it.jb + it.d;
-        const int32_t h = cta_hindex<Q, !AND>(P.inc, P.tin, jb, je, t, bins, bounds);
+        const int32_t h = cta_hindex<Q, !AND>(P.inc, P.gin, jb, je, t, bins, bounds);
         if (threadIdx.x == 0) {
             evals++;
             incs += it.d;
             if (h != t) changed++;
-            if (!AND || h != t) P.tout[R] = h;
+            if (!AND || h != t) store_tau<Q>(P, R, h);
         }
         if (AND && NOTIFY && h != t) notify_row<Q>(P, jb, je, h, threadIdx.x, kThreads, 0xffffffffu);
         __syncthreads();
@@ -454,6 +473,22 @@ __global__ void k_init_tau(int64_t N, const int64_t* __restrict__ inc_ptr, int32
     }
 }
 
+// tau -> its CSR-position copies: both entries of every edge
+__global__ void k_tau_to_adj(int64_t N, const uint2* __restrict__ epos, const int32_t* __restrict__ tau,
+                             int32_t* __restrict__ a, int32_t* __restrict__ b) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint2 ep = epos[i];
+        const int32_t v = tau[i];
+        a[ep.x] = v;
+        a[ep.y] = v;
+        if (b) {
+            b[ep.x] = v;
+            b[ep.y] = v;
+        }
+    }
+}
+
 __global__ void k_fill_front(int64_t N, uint32_t* __restrict__ f) {
     const int64_t words = (N + 31) / 32;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
@@ -527,6 +562,11 @@ nd_status ensure_state(nd_incidence* h, bool and_mode, cudaStream_t st) {
     const int64_t N = h->num_r > 0 ? h->num_r : 1;
     if (!h->tau[0]) ND_TRY(nd_alloc((void**)&h->tau[0], sizeof(int32_t) * N, st, h));
     if (!and_mode && !h->tau[1]) ND_TRY(nd_alloc((void**)&h->tau[1], sizeof(int32_t) * N, st, h));
+    if (h->adj) {
+        const int64_t E = h->nnz > 0 ? h->nnz : 1;
+        if (!h->tg[0]) ND_TRY(nd_alloc((void**)&h->tg[0], sizeof(int32_t) * E, st, h));
+        if (!and_mode && !h->tg[1]) ND_TRY(nd_alloc((void**)&h->tg[1], sizeof(int32_t) * E, st, h));
+    }
     const int64_t words = (N + 31) / 32;
     if (and_mode && !h->front[0]) {
         ND_TRY(nd_alloc((void**)&h->front[0], sizeof(uint32_t) * words, st, h));
@@ -551,11 +591,15 @@ SweepParams pass_params(const nd_incidence* h, int mode, const SweepParams& P0, 
     if (mode != ND_SND) {
         P.tin = h->tau[0];
         P.tout = h->tau[0];
+        P.gin = h->adj ? h->tg[0] : P.tin;
+        P.gout = h->adj ? h->tg[0] : nullptr;
         P.cur = h->front[k & 1];
         P.next = h->front[(k & 1) ^ 1];
     } else {
         P.tin = h->tau[k & 1];
         P.tout = h->tau[(k & 1) ^ 1];
+        P.gin = h->adj ? h->tg[k & 1] : P.tin;
+        P.gout = h->adj ? h->tg[(k & 1) ^ 1] : nullptr;
         P.cur = nullptr;
         P.next = nullptr;
     }
@@ -692,6 +736,11 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
             k_init_tau<<<blocks, kThreads, 0, st>>>(N, h->inc_ptr, h->tau[0], and_mode ? nullptr : h->tau[1]);
             ND_CUDA(cudaGetLastError());
         }
+        if (h->adj) {
+            nd_prof_scope ps("init_tau", st);
+            k_tau_to_adj<<<blocks, kThreads, 0, st>>>(N, h->e_pos, h->tau[0], h->tg[0], and_mode ? nullptr : h->tg[1]);
+            ND_CUDA(cudaGetLastError());
+        }
     }
     *tau_result = h->tau[0];
     if (N == 0 || max_passes <= 0) {
@@ -710,6 +759,8 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
     SweepParams P;
     P.inc_ptr = h->inc_ptr;
     P.inc = h->inc;
+    P.epos = h->e_pos;
+    P.eid = h->eid;
     P.items = h->items;
     P.members = members;
     plan_chunks(h, P);

@@ -204,3 +204,27 @@ def test_autotune_changes_speed_not_results(nd):
         np.testing.assert_array_equal(inc.and_()[0], want)
         again = nd.build_incidence(rp, col, r, s)   # starts from the cached thresholds
         np.testing.assert_array_equal(again.snd()[0], want)
+
+
+def test_long_rows_with_two_huge_endpoints(nd):
+    """(2,3) rows are ordered by their third vertex with one bit per entry of
+    the shorter adjacency list; an edge whose endpoints both have more than
+    65,536 neighbours takes the global-scratch path.  Two adjacent hubs share
+    66,000 neighbours, which form a cycle: the hub edge is in 66,000
+    triangles, every other edge in 1-3."""
+    fan = 66000
+    w = np.arange(2, fan + 2)
+    src = np.concatenate([[0], np.zeros(fan, np.int64), np.ones(fan, np.int64), w])
+    dst = np.concatenate([[1], w, w, np.roll(w, -1)])
+    rp, col = G.to_csr(fan + 2, src, dst)
+    inc = nd.build_incidence(rp, col, 2, 3)
+    g = oracle.Graph(rp, col, 2, 3)
+    np.testing.assert_array_equal(inc.s_degree(), g.s_degree())
+    kap = g.peel()
+    tau, iters = inc.snd()
+    np.testing.assert_array_equal(tau, kap)
+    assert iters == g.snd()[2]
+    for k in (1, 2):
+        np.testing.assert_array_equal(inc.iterate_k("snd", k)[0], g.snd(max_sweeps=k)[0])
+    t2, _, _ = inc.and_(notify=True)
+    np.testing.assert_array_equal(t2, kap)
