@@ -58,10 +58,11 @@ struct SweepParams {
     const uint32_t* __restrict__ inc;
     const int32_t* tin;   // SND: tau of the previous pass; AND: same array as tout
     int32_t* tout;
-    // gathers: (2,3) reads tau by CSR position from gin and writes both
-    // entries of an updated edge to gout (e_pos); otherwise gin = tin
-    const int32_t* gin;
-    int32_t* gout;
+    // (2,3) gathers: tau by CSR position, 16 bits saturated at 65535 (exact
+    // for every row with d_s <= 65535, because tau <= d_s; longer rows read
+    // tin through eid).  An updated edge writes both of its entries (e_pos).
+    const uint16_t* gin;
+    uint16_t* gout;
     const uint2* __restrict__ epos;
     const uint32_t* __restrict__ eid;  // CSR position -> edge id (notification)
     const nd_item* __restrict__ items;
@@ -86,6 +87,12 @@ __device__ __forceinline__ int32_t ld_tau(const int32_t* p) {
     return *p;
 }
 
+template <bool RO>
+__device__ __forceinline__ int32_t ld_tau(const uint16_t* p) {
+    if (RO) return (int32_t)__ldg(p);
+    return (int32_t)*p;
+}
+
 // rho(S,R) for the s-clique at incidence j: min of the other r-cliques' tau
 // (for (2,3) the entries index the CSR-position copy of tau).
 // SND reads each row once per pass, so its ids are loaded evict-first and do
@@ -96,8 +103,8 @@ __device__ __forceinline__ uint32_t ld_id(const uint32_t* p) {
     return RO ? __ldcs(p) : __ldg(p);
 }
 
-template <int Q, bool RO>
-__device__ __forceinline__ int32_t rho_at(const uint32_t* __restrict__ inc, const int32_t* tau, int64_t j) {
+template <int Q, bool RO, typename T>
+__device__ __forceinline__ int32_t rho_at(const uint32_t* __restrict__ inc, const T* tau, int64_t j) {
     if (Q == 1) {
         return ld_tau<RO>(tau + ld_id<RO>(inc + j));
     } else if (Q == 2) {
@@ -111,12 +118,40 @@ __device__ __forceinline__ int32_t rho_at(const uint32_t* __restrict__ inc, cons
     }
 }
 
+// rho of incidence j, as a functor for the h-index routines below
+template <int Q, bool RO, typename T>
+struct Rho {
+    const uint32_t* __restrict__ inc;
+    const T* tau;
+    __device__ __forceinline__ int32_t operator()(int64_t j) const { return rho_at<Q, RO>(inc, tau, j); }
+};
+
+// (2,3) rows with tau(R) > 65535 (so d_s > 65535, CTA rows): exact values,
+// CSR position -> edge id -> tau
+template <bool RO>
+struct RhoExact2 {
+    const uint32_t* __restrict__ inc;
+    const uint32_t* __restrict__ eid;
+    const int32_t* tau;
+    __device__ __forceinline__ int32_t operator()(int64_t j) const {
+        const uint2 id = __ldg(reinterpret_cast<const uint2*>(inc) + j);
+        return min(ld_tau<RO>(tau + __ldg(eid + id.x)), ld_tau<RO>(tau + __ldg(eid + id.y)));
+    }
+};
+
+constexpr int32_t kTau16Max = 65535;
+
+template <int Q, bool RO>
+__device__ __forceinline__ auto make_rho(const SweepParams& P) {
+    if constexpr (Q == 2) return Rho<2, RO, uint16_t>{P.inc, P.gin};
+    else return Rho<Q, RO, int32_t>{P.inc, P.tin};
+}
+
 // H({rho_j}) clipped to t, for one r-clique, by a group of G lanes; the row
 // (at most G*C <= 1024 incidences, so t <= 1024) is held in registers as
 // min(rho, t), two 16-bit values per register.
-template <int Q, int G, int C, bool RO>
-__device__ __forceinline__ int32_t group_hindex(const cg::thread_block_tile<G>& g,
-                                                const uint32_t* __restrict__ inc, const int32_t* tau,
+template <int G, int C, typename F>
+__device__ __forceinline__ int32_t group_hindex(const cg::thread_block_tile<G>& g, const F& rho,
                                                 int64_t jb, int64_t je, int32_t t) {
     static_assert(C % 2 == 0, "values are packed in pairs");
     const int lane = g.thread_rank();
@@ -126,8 +161,8 @@ __device__ __forceinline__ int32_t group_hindex(const cg::thread_block_tile<G>& 
 #pragma unroll
     for (int c = 0; c < C; c += 2) {
         const int64_t j0 = jb + lane + (int64_t)c * G, j1 = j0 + G;
-        const int32_t r0 = (j0 < je) ? rho_at<Q, RO>(inc, tau, j0) : 0;
-        const int32_t r1 = (j1 < je) ? rho_at<Q, RO>(inc, tau, j1) : 0;
+        const int32_t r0 = (j0 < je) ? rho(j0) : 0;
+        const int32_t r1 = (j1 < je) ? rho(j1) : 0;
         cnt += (r0 >= t) + (r1 >= t);
         pk[c / 2] = (uint32_t)min(r0, t) | ((uint32_t)min(r1, t) << 16);
     }
@@ -186,14 +221,13 @@ __device__ __forceinline__ void kary_bin(unsigned* bins, int32_t r, int lo, int 
 // H({rho_j}) clipped to t by one warp, streaming the row: one pass counts
 // rho >= t; if that fails, k-ary search with 256 shared-memory bins per
 // streaming pass (at most 2 passes for t <= 65536).
-template <int Q, bool RO>
-__device__ __forceinline__ int32_t warp_hindex(const uint32_t* __restrict__ inc, const int32_t* tau,
-                                               int64_t jb, int64_t je, int32_t t, unsigned* bins) {
+template <typename F>
+__device__ __forceinline__ int32_t warp_hindex(const F& rho, int64_t jb, int64_t je, int32_t t, unsigned* bins) {
     const int lane = threadIdx.x & 31;
     if (t <= 0) return 0;
     int cnt = 0;
 #pragma unroll kWarpUnroll
-    for (int64_t j = jb + lane; j < je; j += 32) cnt += (rho_at<Q, RO>(inc, tau, j) >= t);
+    for (int64_t j = jb + lane; j < je; j += 32) cnt += (rho(j) >= t);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     if (cnt >= t) return t;
@@ -204,7 +238,7 @@ __device__ __forceinline__ int32_t warp_hindex(const uint32_t* __restrict__ inc,
         const int width = (span + nb - 1) / nb;
         for (int i = lane; i <= 256; i += 32) bins[i] = 0;
         __syncwarp();
-        for (int64_t j = jb + lane; j < je; j += 32) kary_bin(bins, rho_at<Q, RO>(inc, tau, j), lo, hi, width);
+        for (int64_t j = jb + lane; j < je; j += 32) kary_bin(bins, rho(j), lo, hi, width);
         __syncwarp();
         int nlo, nhi;
         select_bin(bins, lo, hi, width, nb, &nlo, &nhi);
@@ -216,14 +250,13 @@ __device__ __forceinline__ int32_t warp_hindex(const uint32_t* __restrict__ inc,
 }
 
 // The same by the whole CTA (the longest rows); warp 0 selects the bin.
-template <int Q, bool RO>
-__device__ __forceinline__ int32_t cta_hindex(const uint32_t* __restrict__ inc, const int32_t* tau,
-                                              int64_t jb, int64_t je, int32_t t,
+template <typename F>
+__device__ __forceinline__ int32_t cta_hindex(const F& rho, int64_t jb, int64_t je, int32_t t,
                                               unsigned* bins /* 257 */, int* bounds /* 2 */) {
     if (t <= 0) return 0;
     int cnt = 0;
 #pragma unroll kWarpUnroll
-    for (int64_t j = jb + threadIdx.x; j < je; j += kThreads) cnt += (rho_at<Q, RO>(inc, tau, j) >= t);
+    for (int64_t j = jb + threadIdx.x; j < je; j += kThreads) cnt += (rho(j) >= t);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     if ((threadIdx.x & 31) == 0) bins[threadIdx.x >> 5] = (unsigned)cnt;
@@ -245,7 +278,7 @@ __device__ __forceinline__ int32_t cta_hindex(const uint32_t* __restrict__ inc, 
         for (int i = threadIdx.x; i <= 256; i += kThreads) bins[i] = 0;
         __syncthreads();
         for (int64_t j = jb + threadIdx.x; j < je; j += kThreads)
-            kary_bin(bins, rho_at<Q, RO>(inc, tau, j), lo, hi, width);
+            kary_bin(bins, rho(j), lo, hi, width);
         __syncthreads();
         if (threadIdx.x < 32) {
             int nlo, nhi;
@@ -266,8 +299,9 @@ __device__ __forceinline__ void store_tau(const SweepParams& P, uint32_t R, int3
     P.tout[R] = h;
     if (Q == 2) {
         const uint2 ep = __ldg(P.epos + R);
-        P.gout[ep.x] = h;
-        P.gout[ep.y] = h;
+        const uint16_t v = (uint16_t)min(h, kTau16Max);
+        P.gout[ep.x] = v;
+        P.gout[ep.y] = v;
     }
 }
 
@@ -326,7 +360,7 @@ __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, 
     const int64_t jb = it.jb, je = it.jb + it.d;
     if (AND && NOTIFY && !((__ldg(P.cur + (R >> 5)) >> (R & 31)) & 1u)) return;
     const int32_t t = ld_tau<!AND>(P.tin + R);
-    const int32_t h = group_hindex<Q, G, C, !AND>(g, P.inc, P.gin, jb, je, t);
+    const int32_t h = group_hindex<G, C>(g, make_rho<Q, !AND>(P), jb, je, t);
     if (lane == 0) {
         evals++;
         incs += it.d;
@@ -346,7 +380,7 @@ __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item
     if (AND && NOTIFY && !((__ldg(P.cur + (R >> 5)) >> (R & 31)) & 1u)) return;
     const int32_t t = ld_tau<!AND>(P.tin + R);
     const int64_t jb = it.jb, je = it.jb + it.d;
-    const int32_t h = warp_hindex<Q, !AND>(P.inc, P.gin, jb, je, t, bins);
+    const int32_t h = warp_hindex(make_rho<Q, !AND>(P), jb, je, t, bins);
     if (lane == 0) {
         evals++;
         incs += it.d;
@@ -369,7 +403,11 @@ __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int
         }
         const int32_t t = ld_tau<!AND>(P.tin + R);
         const int64_t jb = it.jb, je = it.jb + it.d;
-        const int32_t h = cta_hindex<Q, !AND>(P.inc, P.gin, jb, je, t, bins, bounds);
+        int32_t h;
+        if (Q == 2 && t > kTau16Max)  // only then can a saturated value matter
+            h = cta_hindex(RhoExact2<!AND>{P.inc, P.eid, P.tin}, jb, je, t, bins, bounds);
+        else
+            h = cta_hindex(make_rho<Q, !AND>(P), jb, je, t, bins, bounds);
         if (threadIdx.x == 0) {
             evals++;
             incs += it.d;
@@ -475,11 +513,11 @@ __global__ void k_init_tau(int64_t N, const int64_t* __restrict__ inc_ptr, int32
 
 // tau -> its CSR-position copies: both entries of every edge
 __global__ void k_tau_to_adj(int64_t N, const uint2* __restrict__ epos, const int32_t* __restrict__ tau,
-                             int32_t* __restrict__ a, int32_t* __restrict__ b) {
+                             uint16_t* __restrict__ a, uint16_t* __restrict__ b) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint2 ep = epos[i];
-        const int32_t v = tau[i];
+        const uint16_t v = (uint16_t)min(max(tau[i], 0), kTau16Max);
         a[ep.x] = v;
         a[ep.y] = v;
         if (b) {
@@ -564,8 +602,8 @@ nd_status ensure_state(nd_incidence* h, bool and_mode, cudaStream_t st) {
     if (!and_mode && !h->tau[1]) ND_TRY(nd_alloc((void**)&h->tau[1], sizeof(int32_t) * N, st, h));
     if (h->adj) {
         const int64_t E = h->nnz > 0 ? h->nnz : 1;
-        if (!h->tg[0]) ND_TRY(nd_alloc((void**)&h->tg[0], sizeof(int32_t) * E, st, h));
-        if (!and_mode && !h->tg[1]) ND_TRY(nd_alloc((void**)&h->tg[1], sizeof(int32_t) * E, st, h));
+        if (!h->tg[0]) ND_TRY(nd_alloc((void**)&h->tg[0], sizeof(uint16_t) * E, st, h));
+        if (!and_mode && !h->tg[1]) ND_TRY(nd_alloc((void**)&h->tg[1], sizeof(uint16_t) * E, st, h));
     }
     const int64_t words = (N + 31) / 32;
     if (and_mode && !h->front[0]) {
@@ -591,15 +629,15 @@ SweepParams pass_params(const nd_incidence* h, int mode, const SweepParams& P0, 
     if (mode != ND_SND) {
         P.tin = h->tau[0];
         P.tout = h->tau[0];
-        P.gin = h->adj ? h->tg[0] : P.tin;
-        P.gout = h->adj ? h->tg[0] : nullptr;
+        P.gin = h->tg[0];
+        P.gout = h->tg[0];
         P.cur = h->front[k & 1];
         P.next = h->front[(k & 1) ^ 1];
     } else {
         P.tin = h->tau[k & 1];
         P.tout = h->tau[(k & 1) ^ 1];
-        P.gin = h->adj ? h->tg[k & 1] : P.tin;
-        P.gout = h->adj ? h->tg[(k & 1) ^ 1] : nullptr;
+        P.gin = h->tg[k & 1];
+        P.gout = h->tg[(k & 1) ^ 1];
         P.cur = nullptr;
         P.next = nullptr;
     }

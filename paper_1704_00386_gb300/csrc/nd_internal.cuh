@@ -79,12 +79,13 @@ struct nd_incidence {
     uint32_t* inc = nullptr;       // [num_inc*q]
     // (2,3) adjacency layout: an incidence entry of edge (x,y), x<y, for the
     // triangle {x,y,w} is the pair of CSR positions (P(x,w), P(y,w)), rows
-    // sorted by w, and the passes gather tau from a copy indexed by CSR
-    // position (each edge's value at both of its entries)
+    // sorted by w, and the passes gather tau from a 16-bit copy indexed by
+    // CSR position (each edge's value at both of its entries, saturated at
+    // 65535)
     bool adj = false;
     uint32_t* mirror = nullptr;    // [nnz] build only: P(v,u) for the entry P(u,v)
     uint2* e_pos = nullptr;        // [m] (P(x,y), P(y,x)) of edge (x,y), x<y
-    int32_t* tg[2] = {nullptr, nullptr};  // [nnz] gather copies of tau by CSR position
+    uint16_t* tg[2] = {nullptr, nullptr};  // [nnz] gather copies of tau by CSR position
     bool rows_sorted = false;      // rows ordered by w (else in fill order)
     bool inc_aliases_graph = false;  // r = 1: inc_ptr/inc are rp/col
     // degree-bucketed processing order
