@@ -48,6 +48,10 @@ constexpr int kWarpUnroll = ND_WARP_UNROLL;
 #define ND_WARP_CHUNK 16  // consecutive warp tasks per counter grab
 #endif
 constexpr int kWarpChunk = ND_WARP_CHUNK;
+#ifndef ND_NOTIFY_UNROLL
+#define ND_NOTIFY_UNROLL 4  // notification entries in flight per lane ((2,3))
+#endif
+constexpr int kNotifyUnroll = ND_NOTIFY_UNROLL;
 
 // Work of one pass: rows longer than the CTA threshold are taken one per
 // block from a per-pass counter; all other rows form warp tasks that warps
@@ -305,6 +309,33 @@ __device__ __forceinline__ void store_tau(const SweepParams& P, uint32_t R, int3
     }
 }
 
+// (2,3): notify the edge at CSR position pos, whose tau read from the
+// 16-bit copy is tv, if h <= tau (the exact int32 value when h > 65535).
+// The bit test is a relaxed L2 read: a stale 0 only costs a redundant
+// atomic, and a set bit is never cleared within a pass.
+__device__ __forceinline__ void notify_pos(const SweepParams& P, uint32_t pos, int32_t h, int32_t tv) {
+    if (h > kTau16Max) tv = ld_tau<false>(P.tin + __ldg(P.eid + pos));
+    if (h > tv) return;
+    if (P.members) {  // PartialAnd: members only
+        const uint32_t Rp = __ldg(P.eid + pos);
+        if (!((__ldg(P.members + (Rp >> 5)) >> (Rp & 31)) & 1u)) return;
+    }
+    const uint32_t bit = 1u << (pos & 31);
+    uint32_t* w = P.next + (pos >> 5);
+    if ((__ldcg(w) & bit) == 0u) atomicOr(w, bit);
+}
+
+// is R in the current frontier?  (2,3): either bit of its two CSR positions
+template <int Q>
+__device__ __forceinline__ bool in_frontier(const SweepParams& P, uint32_t R) {
+    if constexpr (Q == 2) {
+        const uint2 ep = __ldg(P.epos + R);
+        return ((__ldg(P.cur + (ep.x >> 5)) >> (ep.x & 31)) & 1u) | ((__ldg(P.cur + (ep.y >> 5)) >> (ep.y & 31)) & 1u);
+    } else {
+        return (__ldg(P.cur + (R >> 5)) >> (R & 31)) & 1u;
+    }
+}
+
 // notify every neighbour whose tau could still depend on R (Alg. 3, orange
 // lines): set its next-frontier bit if h <= tau(R').  A neighbour whose bit
 // is already set needs nothing, so the bitmap word (2 MB for 16M r-cliques,
@@ -315,15 +346,44 @@ __device__ __forceinline__ void store_tau(const SweepParams& P, uint32_t R, int3
 template <int Q>
 __device__ __forceinline__ void notify_row(const SweepParams& P, int64_t jb, int64_t je, int32_t h,
                                            int first, int step, unsigned /*gmask*/) {
-    for (int64_t j = jb + first; j < je; j += step) {
+    if constexpr (Q == 2) {
+        // (2,3): the entries are CSR positions; the frontier has one bit per
+        // position, so the test reads the 16-bit copy and the bit sits next
+        // to it (no edge id on this path).  kNotifyUnroll entries per lane
+        // are loaded before any is tested, so their latencies overlap.
+        const uint2* pairs = reinterpret_cast<const uint2*>(P.inc);
+        for (int64_t j0 = jb + first; j0 < je; j0 += (int64_t)kNotifyUnroll * step) {
+            uint2 id[kNotifyUnroll];
+            int32_t a[kNotifyUnroll], b[kNotifyUnroll];
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            const uint32_t id = __ldg(P.inc + Q * j + k);
-            const uint32_t Rp = Q == 2 ? __ldg(P.eid + id) : id;  // (2,3): entries are CSR positions
-            const uint32_t bit = 1u << (Rp & 31);
-            if (P.members && !(__ldg(P.members + (Rp >> 5)) & bit)) continue;  // PartialAnd
-            uint32_t* w = P.next + (Rp >> 5);
-            if ((*(volatile uint32_t*)w & bit) == 0u && h <= ld_tau<false>(P.tin + Rp)) atomicOr(w, bit);
+            for (int u = 0; u < kNotifyUnroll; ++u) {
+                const int64_t j = j0 + (int64_t)u * step;
+                id[u] = j < je ? __ldg(pairs + j) : make_uint2(0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < kNotifyUnroll; ++u) {
+                const bool ok = j0 + (int64_t)u * step < je;
+                a[u] = ok ? ld_tau<false>(P.gin + id[u].x) : 0;
+                b[u] = ok ? ld_tau<false>(P.gin + id[u].y) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < kNotifyUnroll; ++u) {
+                if (j0 + (int64_t)u * step < je) {
+                    notify_pos(P, id[u].x, h, a[u]);
+                    notify_pos(P, id[u].y, h, b[u]);
+                }
+            }
+        }
+    } else {
+        for (int64_t j = jb + first; j < je; j += step) {
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                const uint32_t Rp = __ldg(P.inc + Q * j + k);
+                const uint32_t bit = 1u << (Rp & 31);
+                if (P.members && !(__ldg(P.members + (Rp >> 5)) & bit)) continue;  // PartialAnd
+                uint32_t* w = P.next + (Rp >> 5);
+                if ((__ldcg(w) & bit) == 0u && h <= ld_tau<false>(P.tin + Rp)) atomicOr(w, bit);
+            }
         }
     }
 }
@@ -358,7 +418,7 @@ __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, 
     const nd_item it = load_item(P.items, i);
     const uint32_t R = it.R;
     const int64_t jb = it.jb, je = it.jb + it.d;
-    if (AND && NOTIFY && !((__ldg(P.cur + (R >> 5)) >> (R & 31)) & 1u)) return;
+    if (AND && NOTIFY && !in_frontier<Q>(P, R)) return;
     const int32_t t = ld_tau<!AND>(P.tin + R);
     const int32_t h = group_hindex<G, C>(g, make_rho<Q, !AND>(P), jb, je, t);
     if (lane == 0) {
@@ -377,7 +437,7 @@ __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item
                                              unsigned long long& incs) {
     const int lane = threadIdx.x & 31;
     const uint32_t R = it.R;
-    if (AND && NOTIFY && !((__ldg(P.cur + (R >> 5)) >> (R & 31)) & 1u)) return;
+    if (AND && NOTIFY && !in_frontier<Q>(P, R)) return;
     const int32_t t = ld_tau<!AND>(P.tin + R);
     const int64_t jb = it.jb, je = it.jb + it.d;
     const int32_t h = warp_hindex(make_rho<Q, !AND>(P), jb, je, t, bins);
@@ -398,9 +458,7 @@ __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int
     for (int64_t i = first; i < last; ++i) {
         const nd_item it = load_item(P.items, i);
         const uint32_t R = it.R;
-        if (AND && NOTIFY) {
-            if (!((__ldg(P.cur + (R >> 5)) >> (R & 31)) & 1u)) continue;
-        }
+        if (AND && NOTIFY && !in_frontier<Q>(P, R)) continue;
         const int32_t t = ld_tau<!AND>(P.tin + R);
         const int64_t jb = it.jb, je = it.jb + it.d;
         int32_t h;
@@ -527,6 +585,18 @@ __global__ void k_tau_to_adj(int64_t N, const uint2* __restrict__ epos, const in
     }
 }
 
+// PartialAnd with the (2,3) layout: both CSR positions of every member
+__global__ void k_member_pos(int64_t N, const uint32_t* __restrict__ members, const uint2* __restrict__ epos,
+                             uint32_t* __restrict__ f) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (!((members[i >> 5] >> (i & 31)) & 1u)) continue;
+        const uint2 ep = epos[i];
+        atomicOr(f + (ep.x >> 5), 1u << (ep.x & 31));
+        atomicOr(f + (ep.y >> 5), 1u << (ep.y & 31));
+    }
+}
+
 __global__ void k_fill_front(int64_t N, uint32_t* __restrict__ f) {
     const int64_t words = (N + 31) / 32;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
@@ -605,7 +675,9 @@ nd_status ensure_state(nd_incidence* h, bool and_mode, cudaStream_t st) {
         if (!h->tg[0]) ND_TRY(nd_alloc((void**)&h->tg[0], sizeof(uint16_t) * E, st, h));
         if (!and_mode && !h->tg[1]) ND_TRY(nd_alloc((void**)&h->tg[1], sizeof(uint16_t) * E, st, h));
     }
-    const int64_t words = (N + 31) / 32;
+    // (2,3): one frontier bit per CSR position (notification sets the bit of
+    // the slot it has just read); otherwise one per r-clique
+    const int64_t words = ((h->adj ? h->nnz : N) + 31) / 32;
     if (and_mode && !h->front[0]) {
         ND_TRY(nd_alloc((void**)&h->front[0], sizeof(uint32_t) * words, st, h));
         ND_TRY(nd_alloc((void**)&h->front[1], sizeof(uint32_t) * words, st, h));
@@ -785,13 +857,21 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
         *converged = (N == 0);
         return ND_OK;
     }
-    const int64_t words = (N + 31) / 32;
+    const int64_t fbits = h->adj ? h->nnz : N;  // frontier bits (see ensure_state)
+    const int64_t words = (fbits + 31) / 32;
     if (mode == ND_AND && members) {
         // PartialAnd: the members start active (end of Section 4.3)
-        ND_CUDA(cudaMemcpyAsync(h->front[0], members, sizeof(uint32_t) * words, cudaMemcpyDeviceToDevice, st));
+        if (h->adj) {
+            ND_CUDA(cudaMemsetAsync(h->front[0], 0, sizeof(uint32_t) * words, st));
+            nd_prof_scope ps("fill_front", st);
+            k_member_pos<<<blocks, kThreads, 0, st>>>(N, members, h->e_pos, h->front[0]);
+            ND_CUDA(cudaGetLastError());
+        } else {
+            ND_CUDA(cudaMemcpyAsync(h->front[0], members, sizeof(uint32_t) * words, cudaMemcpyDeviceToDevice, st));
+        }
     } else if (mode == ND_AND) {
         nd_prof_scope ps("fill_front", st);
-        k_fill_front<<<nd_blocks_for(words, kThreads, h->sm_count * 8), kThreads, 0, st>>>(N, h->front[0]);
+        k_fill_front<<<nd_blocks_for(words, kThreads, h->sm_count * 8), kThreads, 0, st>>>(fbits, h->front[0]);
         ND_CUDA(cudaGetLastError());
     }
     SweepParams P;
