@@ -173,7 +173,7 @@ __global__ void k_orient(int64_t n, const int64_t* __restrict__ rp, const int32_
 // ADJ: the entries are CSR positions, each pair ordered by its edge's
 // canonical endpoints (the entry of the smaller endpoint first).
 template <bool FILL, bool ADJ>
-__global__ void k_tri_oriented(int64_t m, const int64_t* __restrict__ out_ptr,
+__global__ void __launch_bounds__(kThreads, 6) k_tri_oriented(int64_t m, const int64_t* __restrict__ out_ptr,
                                const int32_t* __restrict__ out_col, const uint32_t* __restrict__ out_eid,
                                const int32_t* __restrict__ out_src, const uint32_t* __restrict__ out_pos,
                                const uint32_t* __restrict__ out_mir, unsigned long long* __restrict__ ctr,
@@ -259,9 +259,9 @@ __global__ void k_tri_oriented(int64_t m, const int64_t* __restrict__ out_ptr,
 // per row; the bit and prefix words sit in shared memory (kRankWords per
 // warp); a row whose shorter list needs more words is left to the overflow
 // pass, which uses global scratch.
-constexpr int kRankWarps = 4;
+constexpr int kRankWarps = 8;
 #ifndef ND_RANK_WORDS
-#define ND_RANK_WORDS 2048
+#define ND_RANK_WORDS 512  // 16,384 positions per warp; 32 KB per block
 #endif
 constexpr int kRankWords = ND_RANK_WORDS;
 

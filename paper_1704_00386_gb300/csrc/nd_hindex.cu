@@ -419,15 +419,18 @@ __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, 
     const uint32_t R = it.R;
     const int64_t jb = it.jb, je = it.jb + it.d;
     if (AND && NOTIFY && !in_frontier<Q>(P, R)) return;
-    const int32_t t = ld_tau<!AND>(P.tin + R);
+    const int32_t t0 = ld_tau<!AND>(P.tin + R);
+    // H <= d_s, so tau is clipped at d_s for the search (a no-op for every
+    // valid tau, which is <= d_s); changes are detected against the stored value
+    const int32_t t = min(t0, (int32_t)it.d);
     const int32_t h = group_hindex<G, C>(g, make_rho<Q, !AND>(P), jb, je, t);
     if (lane == 0) {
         evals++;
         incs += it.d;
-        if (h != t) changed++;
-        if (!AND || h != t) store_tau<Q>(P, R, h);
+        if (h != t0) changed++;
+        if (!AND || h != t0) store_tau<Q>(P, R, h);
     }
-    if (AND && NOTIFY && h != t) notify_row<Q>(P, jb, je, h, lane, G, group_mask<G>());
+    if (AND && NOTIFY && h != t0) notify_row<Q>(P, jb, je, h, lane, G, group_mask<G>());
 }
 
 // one r-clique per warp (rows of the warp bucket), streamed
@@ -438,16 +441,19 @@ __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item
     const int lane = threadIdx.x & 31;
     const uint32_t R = it.R;
     if (AND && NOTIFY && !in_frontier<Q>(P, R)) return;
-    const int32_t t = ld_tau<!AND>(P.tin + R);
+    const int32_t t0 = ld_tau<!AND>(P.tin + R);
+    // H <= d_s, so tau is clipped at d_s for the search (a no-op for every
+    // valid tau, which is <= d_s); changes are detected against the stored value
+    const int32_t t = min(t0, (int32_t)it.d);
     const int64_t jb = it.jb, je = it.jb + it.d;
     const int32_t h = warp_hindex(make_rho<Q, !AND>(P), jb, je, t, bins);
     if (lane == 0) {
         evals++;
         incs += it.d;
-        if (h != t) changed++;
-        if (!AND || h != t) store_tau<Q>(P, R, h);
+        if (h != t0) changed++;
+        if (!AND || h != t0) store_tau<Q>(P, R, h);
     }
-    if (AND && NOTIFY && h != t) notify_row<Q>(P, jb, je, h, lane, 32, 0xffffffffu);
+    if (AND && NOTIFY && h != t0) notify_row<Q>(P, jb, je, h, lane, 32, 0xffffffffu);
 }
 
 // one r-clique per CTA (rows longer than 2048 incidences)
@@ -459,7 +465,10 @@ __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int
         const nd_item it = load_item(P.items, i);
         const uint32_t R = it.R;
         if (AND && NOTIFY && !in_frontier<Q>(P, R)) continue;
-        const int32_t t = ld_tau<!AND>(P.tin + R);
+        const int32_t t0 = ld_tau<!AND>(P.tin + R);
+    // H <= d_s, so tau is clipped at d_s for the search (a no-op for every
+    // valid tau, which is <= d_s); changes are detected against the stored value
+    const int32_t t = min(t0, (int32_t)it.d);
         const int64_t jb = it.jb, je = it.jb + it.d;
         int32_t h;
         if (Q == 2 && t > kTau16Max)  // only then can a saturated value matter
@@ -469,10 +478,10 @@ __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int
         if (threadIdx.x == 0) {
             evals++;
             incs += it.d;
-            if (h != t) changed++;
-            if (!AND || h != t) store_tau<Q>(P, R, h);
+            if (h != t0) changed++;
+            if (!AND || h != t0) store_tau<Q>(P, R, h);
         }
-        if (AND && NOTIFY && h != t) notify_row<Q>(P, jb, je, h, threadIdx.x, kThreads, 0xffffffffu);
+        if (AND && NOTIFY && h != t0) notify_row<Q>(P, jb, je, h, threadIdx.x, kThreads, 0xffffffffu);
         __syncthreads();
     }
 }

@@ -209,7 +209,7 @@ def test_autotune_changes_speed_not_results(nd):
 def test_long_rows_with_two_huge_endpoints(nd):
     """(2,3) rows are ordered by their third vertex with one bit per entry of
     the shorter adjacency list; an edge whose endpoints both have more than
-    65,536 neighbours takes the global-scratch path.  Two adjacent hubs share
+    16,384 neighbours takes the global-scratch path.  Two adjacent hubs share
     66,000 neighbours, which form a cycle: the hub edge is in 66,000
     triangles, every other edge in 1-3."""
     fan = 66000
