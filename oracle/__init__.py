@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_LIBDIR, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -70,6 +70,8 @@ def _load():
         lib.orc_and_partial.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int, vp, i32, vp, vp, vp]
         lib.orc_snd_partial.argtypes = [vp, vp, ctypes.c_int, vp, i32, vp]
         lib.orc_degree_levels.argtypes = [vp, vp]
+        lib.orc_kendall_tau_b.argtypes = [vp, vp, i64, vp, vp, vp]
+        lib.orc_kendall_tau_b.restype = ctypes.c_double
         lib.orc_degree_levels.restype = i32
         _lib = lib
         return lib
@@ -203,6 +205,19 @@ class Graph:
         if k < 0:
             _check(k)
         return k, lv
+
+
+def kendall_tau_b(x, y):
+    """Kendall's tau-b of two integer sequences by visiting every pair
+    (Section 5.2, Fig. 7).  Returns (tau_b, S, ties_x, ties_y); tau_b is NaN
+    when either sequence is constant.  O(n^2)."""
+    a = np.ascontiguousarray(x, dtype=np.int32)
+    b = np.ascontiguousarray(y, dtype=np.int32)
+    if a.shape != b.shape:
+        raise ValueError("sequences differ in length")
+    S, tx, ty = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    t = _load().orc_kendall_tau_b(_ptr(a), _ptr(b), a.size, ctypes.byref(S), ctypes.byref(tx), ctypes.byref(ty))
+    return float(t), S.value, tx.value, ty.value
 
 
 def decompose(row_ptr, col, r: int, s: int) -> np.ndarray:

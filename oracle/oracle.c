@@ -14,6 +14,7 @@
  *   - update operator U and SND ............................. Section 3 Def. 4, Section 4.1 Alg. 2
  *   - AND, with and without notification .................... Section 4.2 Alg. 3, Section 4.3
  *   - degree levels ......................................... Section 3.1, Def. 5
+ *   - Kendall-Tau of tau against kappa (tau-b) .............. Section 5.2, Fig. 7
  *
  * Readings of the paper used here:
  *   - rho(S,R) is the minimum over the r-cliques of S other than R (Def. 4
@@ -28,9 +29,13 @@
  *     `updating` counts the passes that changed at least one tau (SND's
  *     "converges in two iterations" on Fig. 5 counts updating passes).
  *   - Canonical r-clique ids: lexicographic order of the sorted vertex tuple.
+ *   - Kendall-Tau: the paper compares the ranking of the r-cliques by tau
+ *     with the ranking by kappa and does not name the variant; with the many
+ *     ties of integer indices the tie-corrected tau-b is used.
  *
  * Parity is pinned by the tests in tests/test_oracle_*.py.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -572,4 +577,32 @@ int32_t orc_degree_levels(const orc_ctx *c, int32_t *level_of) {
 out:
     free(d); free(alive); free(inL); free(Ls); free(tmp); free(buf);
     return levels;
+}
+
+/* Kendall's tau-b of two integer sequences (Section 5.2, Fig. 7: similarity
+ * of the order of the r-cliques by tau_t with the order by kappa).  Every
+ * unordered pair {i, j} is visited: S accumulates sign(x_i - x_j) *
+ * sign(y_i - y_j), tx and ty count the pairs tied in x and in y, and
+ * tau_b = S / sqrt((n0 - tx) (n0 - ty)) with n0 = n (n - 1) / 2.  Writes the
+ * three counts; returns tau_b, or NaN when either sequence is constant.
+ * O(n^2): for small n only. */
+double orc_kendall_tau_b(const int32_t *x, const int32_t *y, int64_t n, int64_t *s_out, int64_t *tx_out,
+                         int64_t *ty_out) {
+    int64_t S = 0, tx = 0, ty = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = i + 1; j < n; ++j) {
+            const int sx = (x[i] > x[j]) - (x[i] < x[j]);
+            const int sy = (y[i] > y[j]) - (y[i] < y[j]);
+            S += sx * sy;
+            tx += (sx == 0);
+            ty += (sy == 0);
+        }
+    }
+    if (s_out) *s_out = S;
+    if (tx_out) *tx_out = tx;
+    if (ty_out) *ty_out = ty;
+    const double n0 = (double)n * (double)(n - 1) / 2.0;
+    const double den = (n0 - (double)tx) * (n0 - (double)ty);
+    if (!(den > 0.0)) return 0.0 / 0.0;
+    return (double)S / sqrt(den);
 }

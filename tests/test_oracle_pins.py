@@ -362,3 +362,37 @@ def test_partial_and_pins(rs):
         assert (g.partial_and(small, order=order)[0] == t_small).all()
         assert (g.partial_and(small, notify=False)[0] == t_small).all()
         assert (g.partial_snd(small)[0] == t_small).all()
+
+
+# ---- Kendall-Tau (Section 5.2, Fig. 7) --------------------------------------
+
+def test_kendall_tau_b_hand_counted():
+    # pairs of [1,2,2,3] / [1,3,2,2]: three concordant, one discordant, one tie
+    # in x, one tie in y: S = 2, n0 = 6, tau_b = 2 / sqrt(5 * 5)
+    t, S, tx, ty = oracle.kendall_tau_b([1, 2, 2, 3], [1, 3, 2, 2])
+    assert (S, tx, ty) == (2, 1, 1)
+    assert t == pytest.approx(0.4, abs=1e-15)
+
+
+def test_kendall_tau_b_closed_forms_and_symmetries():
+    x = np.arange(40)
+    assert oracle.kendall_tau_b(x, x)[0] == pytest.approx(1.0)
+    assert oracle.kendall_tau_b(x, x[::-1])[0] == pytest.approx(-1.0)
+    assert np.isnan(oracle.kendall_tau_b(np.zeros(5), x[:5])[0])  # constant: undefined
+    rng = np.random.default_rng(7)
+    a = rng.integers(0, 9, 300)
+    b = a // 3 + rng.integers(0, 4, 300)
+    t = oracle.kendall_tau_b(a, b)[0]
+    assert oracle.kendall_tau_b(b, a)[0] == pytest.approx(t, abs=1e-15)
+    assert oracle.kendall_tau_b(a, -b)[0] == pytest.approx(-t, abs=1e-15)
+    assert oracle.kendall_tau_b(3 * a + 5, b)[0] == pytest.approx(t, abs=1e-15)  # order only
+
+
+def test_kendall_tau_b_matches_scipy():
+    stats = pytest.importorskip("scipy.stats")
+    rng = np.random.default_rng(8)
+    for n, hi in ((60, 3), (500, 12), (3000, 200)):
+        a = rng.integers(0, hi, n)
+        b = (a + rng.integers(0, hi, n)) // 2
+        want = stats.kendalltau(a, b).statistic  # tau-b, the default variant
+        assert oracle.kendall_tau_b(a, b)[0] == pytest.approx(want, abs=1e-12)
