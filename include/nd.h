@@ -162,8 +162,22 @@ nd_status nd_and_until(nd_incidence* inc, double active_ratio, int32_t* tau_out,
 nd_status nd_count_equal(const int32_t* a, const int32_t* b, int64_t n, int on_device, int64_t* equal_out,
                          void* stream);
 
+/* Kendall's tau-b of x against y over n int32 values (host or device per
+ * on_device): the similarity of the order of the r-cliques by an
+ * early-stopped tau with the order by kappa_s (Section 5.2, Fig. 7; the
+ * paper does not name the variant, and tau-b corrects for the many ties of
+ * integer indices).  tau_b = S / sqrt((n0 - tx) (n0 - ty)), S = concordant
+ * minus discordant pairs, tx / ty = pairs tied in x / in y, n0 = n(n-1)/2.
+ * *tau_out is NaN when either sequence is constant or n < 2.  counts_out
+ * (optional, 3 int64) receives S, tx, ty.  Uses (max x - min x + 2) *
+ * (max y - min y + 2) 8-byte counters of device memory; more than 2^28
+ * gives ND_E_TOO_LARGE.  Synchronises `stream`. */
+nd_status nd_kendall_tau_b(const int32_t* x, const int32_t* y, int64_t n, int on_device, double* tau_out,
+                           int64_t* counts_out, void* stream);
+
 /* Classic truss numbers (Cohen's k-2 convention) from kappa_3: out = in + 2
- * for every edge.  Host or device per on_device. */
+ * for every edge.  Host or device per on_device (host buffers are copied
+ * through the device).  Synchronises `stream` for host buffers. */
 nd_status nd_truss_classic(const int32_t* kappa3, int64_t num_edges, int32_t* out, int on_device,
                            void* stream);
 

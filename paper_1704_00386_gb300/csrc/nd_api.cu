@@ -508,11 +508,37 @@ nd_status nd_count_equal(const int32_t* a, const int32_t* b, int64_t n, int on_d
 nd_status nd_truss_classic(const int32_t* kappa3, int64_t num_edges, int32_t* out, int on_device,
                            void* stream) {
     if (num_edges < 0 || (num_edges > 0 && (!kappa3 || !out))) { nd_set_error("bad arguments"); return ND_E_INVAL; }
-    if (!on_device) {
-        for (int64_t i = 0; i < num_edges; ++i) out[i] = kappa3[i] + 2;
-        return ND_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (on_device || num_edges == 0) return nd_classic_truss(kappa3, num_edges, out, st);
+    // host buffers: through the device like every other call
+    nd_tmp<int32_t> din(st), dout(st);
+    ND_TRY(din.alloc(num_edges));
+    ND_TRY(dout.alloc(num_edges));
+    ND_CUDA(cudaMemcpyAsync(din, kappa3, sizeof(int32_t) * num_edges, cudaMemcpyHostToDevice, st));
+    ND_TRY(nd_classic_truss(din, num_edges, dout, st));
+    ND_CUDA(cudaMemcpyAsync(out, dout, sizeof(int32_t) * num_edges, cudaMemcpyDeviceToHost, st));
+    ND_CUDA(cudaStreamSynchronize(st));
+    return ND_OK;
+}
+
+nd_status nd_kendall_tau_b(const int32_t* x, const int32_t* y, int64_t n, int on_device, double* tau_out,
+                           int64_t* counts_out, void* stream) {
+    if (n < 0 || !tau_out || (n > 0 && (!x || !y))) { nd_set_error("bad arguments"); return ND_E_INVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 152;
+    ND_CUDA(cudaGetDevice(&dev));
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 152;
+    const int32_t *dx = x, *dy = y;
+    nd_tmp<int32_t> sx(st), sy(st);
+    if (!on_device && n > 0) {
+        ND_TRY(sx.alloc(n));
+        ND_TRY(sy.alloc(n));
+        ND_CUDA(cudaMemcpyAsync(sx, x, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+        ND_CUDA(cudaMemcpyAsync(sy, y, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+        dx = sx;
+        dy = sy;
     }
-    return nd_classic_truss(kappa3, num_edges, out, (cudaStream_t)stream);
+    return nd_kendall_dev(dx, dy, n, sms, tau_out, counts_out, st);
 }
 
 nd_status nd_autotune(nd_incidence* h, int32_t passes, void* stream, int32_t* thr_out, double* best_ms_out) {

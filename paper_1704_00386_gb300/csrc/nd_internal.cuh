@@ -184,6 +184,9 @@ nd_status nd_member_mask(const uint32_t* ids, int64_t count, int64_t N, uint32_t
 nd_status nd_count_equal_dev(const int32_t* a, const int32_t* b, int64_t n, unsigned long long* out_dev,
                              cudaStream_t st);
 nd_status nd_classic_truss(const int32_t* in, int64_t n, int32_t* out, cudaStream_t st);
+// evaluation (nd_eval.cu): Kendall's tau-b of two device sequences; waits on st
+nd_status nd_kendall_dev(const int32_t* x, const int32_t* y, int64_t n, int sm_count, double* tau_out,
+                         int64_t* counts_out, cudaStream_t st);
 
 // launch geometry
 static inline int nd_blocks_for(int64_t work_items, int per_block, int cap) {

@@ -26,7 +26,7 @@ MODES = {"snd": ND_SND, "and": ND_AND, "and_nn": ND_AND_NN}
 
 SYMBOLS = ["nd_build_incidence", "nd_build_incidence_batch", "nd_incidence_info", "nd_r_cliques", "nd_s_degree", "nd_snd",
            "nd_and", "nd_iterate_k", "nd_truss_classic", "nd_prof_enable", "nd_prof_read",
-           "nd_last_passes", "nd_autotune", "nd_and_partial", "nd_and_until", "nd_count_equal", "nd_incidence_bytes", "nd_free", "nd_strerror", "nd_last_error",
+           "nd_last_passes", "nd_autotune", "nd_and_partial", "nd_and_until", "nd_count_equal", "nd_kendall_tau_b", "nd_incidence_bytes", "nd_free", "nd_strerror", "nd_last_error",
            "nd_abi_version", "nd_core_snd_noalloc"]
 
 _lock = threading.Lock()
@@ -78,6 +78,7 @@ def load(build_if_missing: bool = True):
         lib.nd_and_partial.argtypes = [vp, vp, i64, ci, vp, i32, P(i32), P(i64), vp]
         lib.nd_and_until.argtypes = [vp, ctypes.c_double, vp, ci, i32, P(i32), P(i64), P(ci), vp]
         lib.nd_count_equal.argtypes = [vp, vp, i64, ci, P(i64), vp]
+        lib.nd_kendall_tau_b.argtypes = [vp, vp, i64, ci, P(ctypes.c_double), vp, vp]
         lib.nd_incidence_bytes.argtypes = [vp, P(i64)]
         lib.nd_core_snd_noalloc.argtypes = [vp, vp, i64, i64, vp, i32, P(i32), vp]
         lib.nd_free.argtypes = [vp]
@@ -357,6 +358,25 @@ def count_equal(a, b, stream=None) -> int:
     _check(load().nd_count_equal(_ptr(a), _ptr(b), len(a), int(on_device), ctypes.byref(out), _stream_ptr(stream)),
            "nd_count_equal")
     return out.value
+
+
+def kendall_tau_b(x, y, stream=None, with_counts: bool = False):
+    """nd_kendall_tau_b: Kendall's tau-b of x against y (both numpy or both
+    CUDA tensors), e.g. an early-stopped tau against kappa.  With
+    with_counts, also (S, ties_x, ties_y)."""
+    on_device = _is_torch(x)
+    if not on_device:
+        x = np.ascontiguousarray(x, dtype=np.int32)
+        y = np.ascontiguousarray(y, dtype=np.int32)
+    if len(x) != len(y):
+        raise ValueError("sequences differ in length")
+    tau = ctypes.c_double()
+    counts = np.zeros(3, np.int64)
+    _check(load().nd_kendall_tau_b(_ptr(x), _ptr(y), len(x), int(on_device), ctypes.byref(tau), _ptr(counts),
+                                   _stream_ptr(stream)), "nd_kendall_tau_b")
+    if with_counts:
+        return tau.value, int(counts[0]), int(counts[1]), int(counts[2])
+    return tau.value
 
 
 def prof_enable(on: bool = True):

@@ -38,10 +38,18 @@ def test_host_only_calls():
     assert isinstance(lib.nd_last_error(), bytes)
 
 
-def test_classic_truss_host_path():
+def test_host_buffers_need_the_gpu_too():
+    """Host-buffer calls copy through the device; with no GPU they report an
+    error instead of computing on the CPU (there is no CPU path)."""
     import numpy as np
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
     k = np.array([0, 1, 5], np.int32)
-    assert nd.truss_classic(k).tolist() == [2, 3, 7]
+    with pytest.raises(nd.NDError):
+        nd.truss_classic(k)
+    with pytest.raises(nd.NDError):
+        nd.kendall_tau_b(k, k)
 
 
 def test_rejects_bad_arguments_before_touching_the_gpu():

@@ -188,6 +188,36 @@ def test_malformed_graph_rejected(nd, bad):
 def test_classic_truss_device(nd):
     k = torch.tensor([0, 3, 7], dtype=torch.int32, device="cuda")
     assert nd.truss_classic(k).cpu().tolist() == [2, 5, 9]
+    assert nd.truss_classic(np.array([0, 1, 5], np.int32)).tolist() == [2, 3, 7]
+
+
+def test_kendall_tau_b_against_oracle(nd):
+    """nd_kendall_tau_b (2D histogram, suffix sums) equals the oracle's pair
+    loop exactly in its counts, on SND iterates against kappa (Section 5.2,
+    Fig. 7), with and without ties and offsets."""
+    rp, col = CASES["planted800"]
+    for r, s in RS:
+        inc = nd.build_incidence(rp, col, r, s)
+        kap, _ = inc.snd()
+        for k in (1, 2, 4):
+            tk, _ = inc.iterate_k("snd", k)
+            want = oracle.kendall_tau_b(tk, kap)
+            got = nd.kendall_tau_b(tk, kap, with_counts=True)
+            assert got[1:] == want[1:]
+            assert got[0] == pytest.approx(want[0], abs=1e-12) or (np.isnan(got[0]) and np.isnan(want[0]))
+            dev = nd.kendall_tau_b(torch.from_numpy(tk).cuda(), torch.from_numpy(kap).cuda())
+            assert dev == got[0] or (np.isnan(dev) and np.isnan(got[0]))
+    rng = np.random.default_rng(11)
+    a = rng.integers(-40, 300, 5000).astype(np.int32)   # negative values: shifted histogram
+    b = (a // 7 + rng.integers(0, 30, 5000)).astype(np.int32)
+    want = oracle.kendall_tau_b(a, b)
+    got = nd.kendall_tau_b(a, b, with_counts=True)
+    assert got[1:] == want[1:]
+    assert np.isnan(nd.kendall_tau_b(np.zeros(9, np.int32), a[:9]))  # constant: undefined
+    assert np.isnan(nd.kendall_tau_b(a[:1], b[:1]))
+    with pytest.raises(nd.NDError) as e:
+        nd.kendall_tau_b(np.array([0, 1 << 20], np.int32), np.array([0, 1 << 20], np.int32))
+    assert e.value.status == nd.ND_E_TOO_LARGE
 
 
 def test_autotune_changes_speed_not_results(nd):
