@@ -39,8 +39,10 @@ METRIC = "r-clique h-index updates/sec to convergence; HBM GB/s vs peak; batched
 UNIT = "updates/s"
 CPU_SAMPLE_SCALE = 14
 # ncu DRAM bytes per incidence of the SND pass (k-truss, q = 2), measured on the
-# current kernel; None until it is measured again after a kernel change.
-NCU_SND_TRAFFIC_PER_INCIDENCE = None
+# current kernel on R-MAT scale 18 (dram__bytes_read.sum + dram__bytes_write.sum
+# = 2.686 GB + 59.4 MB per pass over 247,767,033 incidences); None once the
+# kernel changes until it is measured again.
+NCU_SND_TRAFFIC_PER_INCIDENCE = (2.685624e9 + 59.436288e6) / 247767033
 
 
 def parse():
@@ -297,9 +299,9 @@ def run_ours(args, rank, world, local_rank):
         units = "8 B per incidence written (fill) or CSR bytes read"
     avg_ms = ms / max(eff, 1)
     achieved = per_launch / (avg_ms / 1000.0) / 1e9
-    # DRAM traffic per SND pass from ncu (dram__bytes_read.sum + write.sum) on the R-MAT scale 18
-    # k-truss pass (2.254 GB read + 6.6 MB written per pass for 247,767,033 incidences), scaled by the
-    # incidences of this workload; None for any other kernel or once the kernel has changed.
+    # DRAM traffic per SND pass: the ncu bytes per incidence of the R-MAT scale 18 k-truss pass,
+    # scaled by the incidences of this workload (a full SND pass streams every row); None for any
+    # other kernel or once the kernel has changed.
     traffic = None
     if name == "snd_pass" and q == 2 and NCU_SND_TRAFFIC_PER_INCIDENCE is not None:
         traffic = NCU_SND_TRAFFIC_PER_INCIDENCE * M
@@ -307,7 +309,7 @@ def run_ours(args, rank, world, local_rank):
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "bytes_per_launch": per_launch, "launches_effective": eff, "avg_launch_ms": avg_ms,
                 "units": units,
-                "note": "gather-bound: the q tau gathers per incidence run at the L2 request rate"}
+                "note": "gather-bound: the L1 wavefronts of the q tau gathers per incidence set the pace, not DRAM"}
 
     # ----- end to end through the public API with host buffers
     e2e = None
