@@ -29,6 +29,17 @@ __device__ __forceinline__ int64_t lower_bound_i32(const int32_t* __restrict__ a
     return lo;
 }
 
+// the same within one list of fewer than 2^31 entries, with 32-bit offsets
+// (fewer instructions per step in the intersection loops)
+__device__ __forceinline__ int lower_bound_n(const int32_t* __restrict__ a, int n, int32_t x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(a + mid) < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     return (1u << (threadIdx.x & 31)) - 1u;
 }
@@ -46,9 +57,13 @@ __device__ __forceinline__ int64_t warp_count_global() {
 // other than its own, and every entry v of row u needs u in row v.  Writes
 // nlow[u] = #neighbours < u and upcnt[u] = #neighbours > u.  Reads only
 // inside the bounds it has checked, so a malformed graph cannot fault.
+// With mirror (builds with r >= 2), it also records for every entry p of
+// row u the position of u in row v: the reverse entry, found by the same
+// search.
 __global__ void k_validate_split(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
                                  const int32_t* __restrict__ col, int32_t* __restrict__ nlow,
-                                 int64_t* __restrict__ upcnt, int* __restrict__ err) {
+                                 int64_t* __restrict__ upcnt, int* __restrict__ err,
+                                 uint32_t* __restrict__ mirror) {
     const int lane = threadIdx.x & 31;
     for (int64_t u = warp_id_global(); u < n; u += warp_count_global()) {
         int64_t b = rp[u], e = rp[u + 1];
@@ -65,9 +80,11 @@ __global__ void k_validate_split(int64_t n, int64_t nnz, const int64_t* __restri
             if (p > b && col[p - 1] >= v) rowbad = true;
             low += (v < u);
             int64_t vb = rp[v], ve = rp[v + 1];
-            if (vb < 0 || ve < vb || ve > nnz) { rowbad = true; continue; }
-            int64_t pos = lower_bound_i32(col, vb, ve, (int32_t)u);
-            if (pos >= ve || col[pos] != (int32_t)u) rowbad = true;
+            // a row longer than n - 1 cannot be simple (and would not fit the 32-bit search)
+            if (vb < 0 || ve < vb || ve > nnz || ve - vb >= n) { rowbad = true; continue; }
+            const int64_t pos = vb + lower_bound_n(col + vb, (int)(ve - vb), (int32_t)u);
+            if (pos >= ve || col[pos] != (int32_t)u) { rowbad = true; continue; }
+            if (mirror) mirror[p] = (uint32_t)pos;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) low += __shfl_xor_sync(kFull, low, o);
@@ -83,9 +100,9 @@ __global__ void k_validate_split(int64_t n, int64_t nnz, const int64_t* __restri
 // ---- canonical edge ids (one warp per vertex) ------------------------------
 // Edge (u,v), u < v, gets id up_start[u] + (rank of v among u's larger
 // neighbours): lexicographic order.  eid[p] is the id of the edge at CSR
-// position p, for both directions.  For the (2,3) adjacency layout it also
-// writes mirror[p] (the position of the reverse entry) and, per edge (x,y)
-// with x < y, e_pos = (P(x,y), P(y,x)).
+// position p, for both directions (the reverse entry comes from mirror,
+// written by the validation, when there is one).  For the (2,3) adjacency
+// layout it also writes, per edge (x,y) with x < y, e_pos = (P(x,y), P(y,x)).
 __global__ void k_edge_ids(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                            const int32_t* __restrict__ nlow, const int64_t* __restrict__ up_start,
                            uint32_t* __restrict__ eid, int32_t* __restrict__ e_u,
@@ -104,16 +121,14 @@ __global__ void k_edge_ids(int64_t n, const int64_t* __restrict__ rp, const int3
                 e_u[id] = (int32_t)u;
                 e_v[id] = v;
             } else {
-                int64_t vfirst = rp[v] + nlow[v];
-                int64_t pos = lower_bound_i32(col, vfirst, rp[v + 1], (int32_t)u);
+                const int64_t vfirst = rp[v] + nlow[v];
+                // the reverse entry: recorded by the validation when available
+                const int64_t pos = mirror ? (int64_t)mirror[p]
+                                           : lower_bound_i32(col, vfirst, rp[v + 1], (int32_t)u);
                 const int64_t id = up_start[v] + (pos - vfirst);
                 eid[p] = (uint32_t)id;
-                if (mirror) {
-                    // edge (v,u), v < u: entry pos = P(v,u), entry p = P(u,v)
-                    mirror[p] = (uint32_t)pos;
-                    mirror[pos] = (uint32_t)p;
-                    e_pos[id] = make_uint2((uint32_t)pos, (uint32_t)p);
-                }
+                // edge (v,u), v < u: entry pos = P(v,u), entry p = P(u,v)
+                if (e_pos) e_pos[id] = make_uint2((uint32_t)pos, (uint32_t)p);
             }
         }
     }
@@ -196,36 +211,59 @@ __global__ void __launch_bounds__(kThreads, 6) k_tri_oriented(int64_t m, const i
             bool found = false;
             int64_t pb = 0;
             int32_t x = 0;
+            // FILL: the values at p are loaded with x, ahead of the search
+            // (coalesced), so only the loads at pb wait for it
+            uint32_t ea = 0, pa = 0, ma = 0;
             if (p < ae) {
                 x = __ldg(out_col + p);
-                pb = lower_bound_i32(out_col, lo, be, x);
+                if (FILL) {
+                    ea = __ldg(out_eid + p);
+                    if (ADJ) {
+                        pa = __ldg(out_pos + p);
+                        ma = __ldg(out_mir + p);
+                    }
+                }
+                pb = lo + lower_bound_n(out_col + lo, (int)(be - lo), x);
                 found = (pb < be) && (__ldg(out_col + pb) == x);
             }
             const unsigned bal = __ballot_sync(kFull, found);
             const int nf = __popc(bal);
             if (nf) {
                 uint32_t e_uw = 0, e_vw = 0;
-                if (found) {
-                    const uint32_t ea = __ldg(out_eid + p), eb = __ldg(out_eid + pb);
-                    e_uw = a_is_u ? ea : eb;
-                    e_vw = a_is_u ? eb : ea;
-                }
                 if (!FILL) {
+                    if (found) {
+                        const uint32_t ea0 = __ldg(out_eid + p), eb = __ldg(out_eid + pb);
+                        e_uw = a_is_u ? ea0 : eb;
+                        e_vw = a_is_u ? eb : ea0;
+                    }
                     if (lane == 0) atomicAdd(ctr + e_uv, (unsigned long long)nf);
                     if (found) {
                         atomicAdd(ctr + e_uw, 1ull);
                         atomicAdd(ctr + e_vw, 1ull);
                     }
                 } else {
-                    unsigned long long s0 = 0;
+                    uint32_t pbp = 0, mb = 0;
+                    if (found) {
+                        const uint32_t eb = __ldg(out_eid + pb);
+                        if (ADJ) {
+                            pbp = __ldg(out_pos + pb);
+                            mb = __ldg(out_mir + pb);
+                        }
+                        e_uw = a_is_u ? ea : eb;
+                        e_vw = a_is_u ? eb : ea;
+                    }
+                    // the three slot reservations are independent: issue them together
+                    unsigned long long s0 = 0, s_uw = 0, s_vw = 0;
                     if (lane == 0) s0 = atomicAdd(ctr + e_uv, (unsigned long long)nf);
+                    if (found) {
+                        s_uw = atomicAdd(ctr + e_uw, 1ull);
+                        s_vw = atomicAdd(ctr + e_vw, 1ull);
+                    }
                     s0 = __shfl_sync(kFull, s0, 0);
                     if (found) {
                         uint2 r_uv, r_uw, r_vw;
                         if (ADJ) {
                             // third vertex w = x; positions P(.,.) of the six entries
-                            const uint32_t pa = __ldg(out_pos + p), ma = __ldg(out_mir + p);
-                            const uint32_t pbp = __ldg(out_pos + pb), mb = __ldg(out_mir + pb);
                             const uint32_t Puw = a_is_u ? pa : pbp, Pwu = a_is_u ? ma : mb;
                             const uint32_t Pvw = a_is_u ? pbp : pa, Pwv = a_is_u ? mb : ma;
                             r_uv = u < v ? make_uint2(Puw, Pvw) : make_uint2(Pvw, Puw);
@@ -237,8 +275,8 @@ __global__ void __launch_bounds__(kThreads, 6) k_tri_oriented(int64_t m, const i
                             r_vw = make_uint2(e_uv, e_uw);
                         }
                         inc[s0 + __popc(bal & lanemask_lt())] = r_uv;
-                        inc[atomicAdd(ctr + e_uw, 1ull)] = r_uw;
-                        inc[atomicAdd(ctr + e_vw, 1ull)] = r_vw;
+                        inc[s_uw] = r_uw;
+                        inc[s_vw] = r_vw;
                     }
                 }
             }
@@ -668,6 +706,9 @@ nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st) {
     if (g->nnz > 0) ND_CUDA(cudaMemcpyAsync(h->col, g->col, sizeof(int32_t) * g->nnz, kind, st));
     ND_TRY(nd_alloc((void**)&h->nlow, sizeof(int32_t) * (g->n > 0 ? g->n : 1), st, h));
     ND_TRY(nd_alloc((void**)&h->up_start, sizeof(int64_t) * (g->n + 1), st, h));
+    // reverse entries for the edge ids and the (2,3) adjacency layout (build only)
+    if (h->r >= 2 && g->nnz > 0 && g->nnz < (int64_t)UINT32_MAX)
+        ND_TRY(nd_alloc((void**)&h->mirror, sizeof(uint32_t) * g->nnz, st, h));
     nd_tmp<int> derr(st);
     ND_TRY(derr.alloc(1));
     ND_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
@@ -676,7 +717,7 @@ nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st) {
         nd_prof_scope ps("validate_split", st);
         int blocks = nd_blocks_for(g->n * 32, kThreads, grid_cap(h) * 4);
         k_validate_split<<<blocks, kThreads, 0, st>>>(g->n, g->nnz, h->rp, h->col, h->nlow,
-                                                      h->up_start, derr);
+                                                      h->up_start, derr, h->mirror);
         ND_CUDA(cudaGetLastError());
     }
     int herr = 0;
@@ -709,7 +750,6 @@ nd_status nd_build_edges(nd_incidence* h, cudaStream_t st) {
             return ND_E_TOO_LARGE;
         }
         h->adj = true;
-        ND_TRY(nd_alloc((void**)&h->mirror, sizeof(uint32_t) * (h->nnz > 0 ? h->nnz : 1), st, h));
         ND_TRY(nd_alloc((void**)&h->e_pos, sizeof(uint2) * (h->m > 0 ? h->m : 1), st, h));
     }
     if (h->n > 0 && h->nnz > 0) {
@@ -718,6 +758,10 @@ nd_status nd_build_edges(nd_incidence* h, cudaStream_t st) {
         k_edge_ids<<<blocks, kThreads, 0, st>>>(h->n, h->rp, h->col, h->nlow, h->up_start, h->eid,
                                                 h->e_u, h->e_v, h->mirror, h->e_pos);
         ND_CUDA(cudaGetLastError());
+    }
+    if (!h->adj && h->mirror) {  // only the (2,3) build needs it further
+        nd_release(h->mirror, st);
+        h->mirror = nullptr;
     }
     return ND_OK;
 }
