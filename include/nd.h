@@ -83,6 +83,21 @@ typedef struct nd_incidence nd_incidence; /* opaque; owned by the library */
  * On success *out owns device memory until nd_free(*out). */
 nd_status nd_build_incidence(const nd_csr* g, int r, int s, void* stream, nd_incidence** out);
 
+/* nd_build_incidence with options.  flags = 0 is nd_build_incidence.
+ * ND_BUILD_ON_THE_FLY: store no r-clique -> s-clique incidence.  The paper's
+ * own implementation does not store the s-cliques but finds them again
+ * through the neighbourhoods on every update (Section 4.1, "Time
+ * complexity"; Section 5); this mode does the same for memory-bound inputs.
+ * Only the counts d_s are kept (tau_0 and the work buckets); every SND / AND
+ * pass then finds the triangles of edge (x,y) by searching each entry of the
+ * shorter of N(x), N(y) in the longer.  Results are identical to the stored
+ * mode; a pass costs about sum over edges of min(deg) binary searches
+ * instead of a stream of 8 B per incidence.  For (1,2) the CSR already is the
+ * incidence and the flag changes nothing; (3,4) gives ND_E_UNSUPPORTED_RS.
+ * Unknown flags give ND_E_INVAL. */
+#define ND_BUILD_ON_THE_FLY 1u
+nd_status nd_build_incidence_ex(const nd_csr* g, int r, int s, unsigned flags, void* stream, nd_incidence** out);
+
 /* Batched build: the incidence of many independent graphs at once, as the
  * incidence of their disjoint union (graph i's vertex ids are shifted past
  * those of graphs 0..i-1).  kappa_s of a disjoint union is kappa_s of each

@@ -220,7 +220,8 @@ static nd_status check_csr(const nd_csr* g) {
 }
 
 // the whole build on one (validated-header) CSR
-static nd_status build_common(const nd_csr* g, int r, int s, cudaStream_t st, nd_incidence** out) {
+static nd_status build_common(const nd_csr* g, int r, int s, cudaStream_t st, nd_incidence** out,
+                              unsigned flags = 0) {
     int dev = 0;
     ND_CUDA(cudaGetDevice(&dev));
     keep_pool(dev);
@@ -229,6 +230,7 @@ static nd_status build_common(const nd_csr* g, int r, int s, cudaStream_t st, nd
     h->r = r;
     h->s = s;
     h->q = (r == 1) ? 1 : (r == 2 ? 2 : 3);
+    h->otf = (flags & ND_BUILD_ON_THE_FLY) && r == 2;
     if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         h->sm_count = 152;
     h->last_stream = st;
@@ -268,6 +270,19 @@ nd_status nd_build_incidence(const nd_csr* g, int r, int s, void* stream, nd_inc
     ND_TRY(check_rs(r, s));
     ND_TRY(check_csr(g));
     return build_common(g, r, s, (cudaStream_t)stream, out);
+}
+
+nd_status nd_build_incidence_ex(const nd_csr* g, int r, int s, unsigned flags, void* stream, nd_incidence** out) {
+    if (!out) { nd_set_error("out is NULL"); return ND_E_INVAL; }
+    *out = nullptr;
+    ND_TRY(check_rs(r, s));
+    if (flags & ~(unsigned)ND_BUILD_ON_THE_FLY) { nd_set_error("unknown build flag"); return ND_E_INVAL; }
+    if ((flags & ND_BUILD_ON_THE_FLY) && r == 3) {
+        nd_set_error("the on-the-fly mode covers (1,2) and (2,3)");
+        return ND_E_UNSUPPORTED_RS;
+    }
+    ND_TRY(check_csr(g));
+    return build_common(g, r, s, (cudaStream_t)stream, out, flags);
 }
 
 nd_status nd_build_incidence_batch(const nd_csr* graphs, int count, int r, int s, void* stream,

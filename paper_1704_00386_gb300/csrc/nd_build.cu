@@ -29,17 +29,6 @@ __device__ __forceinline__ int64_t lower_bound_i32(const int32_t* __restrict__ a
     return lo;
 }
 
-// the same within one list of fewer than 2^31 entries, with 32-bit offsets
-// (fewer instructions per step in the intersection loops)
-__device__ __forceinline__ int lower_bound_n(const int32_t* __restrict__ a, int n, int32_t x) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(a + mid) < x) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
 __device__ __forceinline__ unsigned lanemask_lt() {
     return (1u << (threadIdx.x & 31)) - 1u;
 }
@@ -82,7 +71,7 @@ __global__ void k_validate_split(int64_t n, int64_t nnz, const int64_t* __restri
             int64_t vb = rp[v], ve = rp[v + 1];
             // a row longer than n - 1 cannot be simple (and would not fit the 32-bit search)
             if (vb < 0 || ve < vb || ve > nnz || ve - vb >= n) { rowbad = true; continue; }
-            const int64_t pos = vb + lower_bound_n(col + vb, (int)(ve - vb), (int32_t)u);
+            const int64_t pos = vb + nd_lower_bound_n(col + vb, (int)(ve - vb), (int32_t)u);
             if (pos >= ve || col[pos] != (int32_t)u) { rowbad = true; continue; }
             if (mirror) mirror[p] = (uint32_t)pos;
         }
@@ -223,7 +212,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_tri_oriented(int64_t m, const i
                         ma = __ldg(out_mir + p);
                     }
                 }
-                pb = lo + lower_bound_n(out_col + lo, (int)(be - lo), x);
+                pb = lo + nd_lower_bound_n(out_col + lo, (int)(be - lo), x);
                 found = (pb < be) && (__ldg(out_col + pb) == x);
             }
             const unsigned bal = __ballot_sync(kFull, found);
@@ -781,7 +770,8 @@ static nd_status orient_graph(nd_incidence* h, nd_oriented* o, cudaStream_t st) 
     ND_TRY(o->out_col.alloc(m));
     ND_TRY(o->out_src.alloc(m));
     ND_TRY(o->out_eid.alloc(m));
-    if (h->adj) {
+    const bool positions = h->adj && !h->otf;  // only the stored (2,3) fill uses them
+    if (positions) {
         ND_TRY(o->out_pos.alloc(m));
         ND_TRY(o->out_mir.alloc(m));
     }
@@ -797,7 +787,7 @@ static nd_status orient_graph(nd_incidence* h, nd_oriented* o, cudaStream_t st) 
     if (n > 0) {
         nd_prof_scope ps("orient", st);
         k_orient<true><<<vblocks, kThreads, 0, st>>>(n, h->rp, h->col, h->eid, o->out_ptr, o->out_col, o->out_eid,
-                                                     o->out_src, h->mirror, h->adj ? o->out_pos.p : nullptr,
+                                                     o->out_src, h->mirror, positions ? o->out_pos.p : nullptr,
                                                      o->out_mir);
         ND_CUDA(cudaGetLastError());
     }
@@ -868,6 +858,13 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
     }
     ND_TRY(nd_scan_i64(h->inc_ptr, m, st));
     ND_TRY(read_i64(h->inc_ptr + m, &h->num_inc, st));
+    if (h->otf) {
+        // no stored incidence: the counts (d_s, tau_0 and the buckets) are all
+        // that is kept; every pass finds the triangles again
+        nd_release(h->mirror, st);
+        h->mirror = nullptr;
+        return nd_alloc((void**)&h->inc, 16, st, h);
+    }
     ND_TRY(nd_alloc((void**)&h->inc, sizeof(uint32_t) * 2 * (h->num_inc > 0 ? h->num_inc : 1), st, h));
     if (h->num_inc > 0) {
         nd_tmp<unsigned long long> cursor(st);

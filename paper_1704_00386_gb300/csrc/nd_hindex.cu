@@ -69,6 +69,11 @@ struct SweepParams {
     uint16_t* gout;
     const uint2* __restrict__ epos;
     const uint32_t* __restrict__ eid;  // CSR position -> edge id (notification)
+    // (2,3) without a stored incidence: the graph and the edge endpoints
+    const int64_t* __restrict__ rp;
+    const int32_t* __restrict__ col;
+    const int32_t* __restrict__ eu;
+    const int32_t* __restrict__ ev;
     const nd_item* __restrict__ items;
     int64_t lo[ND_NB], hi[ND_NB];  // bucket ranges in items
     const uint32_t* cur;  // AND + notification: frontier read in this pass
@@ -640,10 +645,114 @@ __global__ void k_add_const(const int32_t* __restrict__ in, int64_t n, int32_t c
         out[i] = in[i] + c;
 }
 
+// ---- (2,3) without a stored incidence ----------------------------------------
+// The paper's own mode (its s-cliques are not stored but found again on every
+// pass, Section 4.1 "Time complexity" and Section 5): for row R = edge (x,y)
+// the triangles are the w in both N(x) and N(y).  Its entries are indexed by
+// the slots of the shorter list N(s): entry j is w = N(s)[j], present if w is
+// in the longer list N(l) (binary search).  A present entry has
+// rho = min(tau at P(s,w), tau at P(l,w)), two slots of the CSR-position copy
+// (the same slots the stored layout lists); a missing one returns -1, which
+// no h-index step counts (every bound is >= 0).  One warp per row, longest
+// rows first, in chunks from a counter.
+template <bool RO, bool EXACT>
+struct RhoOtf {
+    const int32_t* __restrict__ col;
+    int64_t sb, lb;  // first slots of N(s) and N(l)
+    int ln;          // |N(l)|
+    const uint16_t* tau16;
+    const uint32_t* __restrict__ eid;
+    const int32_t* tau32;
+    __device__ __forceinline__ int32_t operator()(int64_t j) const {
+        const int32_t w = __ldg(col + sb + j);
+        const int k = nd_lower_bound_n(col + lb, ln, w);
+        if (k >= ln || __ldg(col + lb + k) != w) return -1;
+        const int64_t ps = sb + j, pl = lb + k;
+        if (EXACT) return min(ld_tau<RO>(tau32 + __ldg(eid + ps)), ld_tau<RO>(tau32 + __ldg(eid + pl)));
+        return min(ld_tau<RO>(tau16 + ps), ld_tau<RO>(tau16 + pl));
+    }
+};
+
+constexpr int kOtfChunk = 4;  // rows per counter grab
+
+template <bool AND, bool NOTIFY>
+__global__ void __launch_bounds__(kThreads, ND_PASS_MIN_BLOCKS) k_pass_otf(SweepParams P) {
+    if (P.prev != nullptr && *(volatile const unsigned long long*)P.prev == 0ull) return;  // converged
+    __shared__ unsigned bins[kThreads / 32][260];
+    unsigned long long changed = 0, evals = 0, incs = 0;
+    const int lane = threadIdx.x & 31;
+    unsigned* wb = bins[threadIdx.x >> 5];
+    const int64_t first = P.lo[0], rows = P.hi[ND_NB - 1] - P.lo[0];
+    for (;;) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(P.ctr + 4, 1ull);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        const int64_t t0 = (int64_t)c * kOtfChunk;
+        if (t0 >= rows) break;
+        const int64_t t1 = min(t0 + (int64_t)kOtfChunk, rows);
+        for (int64_t t = t0; t < t1; ++t) {
+            const nd_item it = load_item(P.items, first + rows - 1 - t);  // longest first
+            const uint32_t R = it.R;
+            if (AND && NOTIFY && !in_frontier<2>(P, R)) continue;
+            const int32_t tr = ld_tau<!AND>(P.tin + R);
+            const int32_t tc = min(tr, (int32_t)it.d);
+            const int32_t x = __ldg(P.eu + R), y = __ldg(P.ev + R);
+            const int64_t xb = __ldg(P.rp + x), xe = __ldg(P.rp + x + 1);
+            const int64_t yb = __ldg(P.rp + y), ye = __ldg(P.rp + y + 1);
+            const bool xs = (xe - xb) <= (ye - yb);
+            const int64_t sb = xs ? xb : yb, se = xs ? xe : ye;
+            const int64_t lb = xs ? yb : xb, le = xs ? ye : xe;
+            int32_t h;
+            if (tc > kTau16Max)
+                h = warp_hindex(RhoOtf<!AND, true>{P.col, sb, lb, (int)(le - lb), P.gin, P.eid, P.tin}, 0, se - sb,
+                                tc, wb);
+            else
+                h = warp_hindex(RhoOtf<!AND, false>{P.col, sb, lb, (int)(le - lb), P.gin, P.eid, P.tin}, 0, se - sb,
+                                tc, wb);
+            if (lane == 0) {
+                evals++;
+                incs += it.d;
+                if (h != tr) changed++;
+                if (!AND || h != tr) store_tau<2>(P, R, h);
+            }
+            if (AND && NOTIFY && h != tr) {
+                // notify the other two edges of every triangle, found again
+                for (int64_t j = lane; j < se - sb; j += 32) {
+                    const int32_t w = __ldg(P.col + sb + j);
+                    const int k = nd_lower_bound_n(P.col + lb, (int)(le - lb), w);
+                    if (k >= (int)(le - lb) || __ldg(P.col + lb + k) != w) continue;
+                    const uint32_t ps = (uint32_t)(sb + j), pl = (uint32_t)(lb + k);
+                    notify_pos(P, ps, h, ld_tau<false>(P.gin + ps));
+                    notify_pos(P, pl, h, ld_tau<false>(P.gin + pl));
+                }
+            }
+        }
+    }
+    __shared__ unsigned long long s_ch[kThreads / 32], s_ev[kThreads / 32], s_in[kThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        changed += __shfl_xor_sync(0xffffffffu, changed, o);
+        evals += __shfl_xor_sync(0xffffffffu, evals, o);
+        incs += __shfl_xor_sync(0xffffffffu, incs, o);
+    }
+    const int wid = threadIdx.x >> 5;
+    if (lane == 0) { s_ch[wid] = changed; s_ev[wid] = evals; s_in[wid] = incs; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long a = 0, e = 0, c2 = 0;
+        for (int w = 0; w < kThreads / 32; ++w) { a += s_ch[w]; e += s_ev[w]; c2 += s_in[w]; }
+        if (a) atomicAdd(P.ctr, a);
+        if (e) atomicAdd(P.ctr + 1, e);
+        if (c2) atomicAdd(P.ctr + 3, c2);
+    }
+}
+
 typedef void (*pass_fn)(SweepParams);
 
-pass_fn pick(int q, int mode) {
+pass_fn pick(const nd_incidence* h, int mode) {
     // mode: ND_SND, ND_AND (notify), ND_AND_NN
+    const int q = h->q;
+    if (h->otf) return mode == ND_SND ? k_pass_otf<false, false> : (mode == ND_AND ? k_pass_otf<true, true> : k_pass_otf<true, false>);
     if (q == 1) return mode == ND_SND ? k_pass<1, false, false> : (mode == ND_AND ? k_pass<1, true, true> : k_pass<1, true, false>);
     if (q == 2) return mode == ND_SND ? k_pass<2, false, false> : (mode == ND_AND ? k_pass<2, true, true> : k_pass<2, true, false>);
     return mode == ND_SND ? k_pass<3, false, false> : (mode == ND_AND ? k_pass<3, true, true> : k_pass<3, true, false>);
@@ -659,7 +768,8 @@ void plan_chunks(const nd_incidence* h, SweepParams& P) {
 
 // work units of a pass: CTA rows + warp tasks (see k_pass); the grid never
 // exceeds what the work needs
-int64_t pass_units(const SweepParams& P) {
+int64_t pass_units(const nd_incidence* h, const SweepParams& P) {
+    if (h->otf) return P.hi[ND_NB - 1] - P.lo[0];  // one warp per row
     return (P.hi[3] - P.lo[3]) + (P.hi[2] - P.lo[2]) + (P.hi[1] - P.lo[1] + 3) / 4 + (P.hi[0] - P.lo[0] + 7) / 8;
 }
 
@@ -888,11 +998,15 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
     P.inc = h->inc;
     P.epos = h->e_pos;
     P.eid = h->eid;
+    P.rp = h->rp;
+    P.col = h->col;
+    P.eu = h->e_u;
+    P.ev = h->e_v;
     P.items = h->items;
     P.members = members;
     plan_chunks(h, P);
-    pass_fn fn = pick(h->q, mode);
-    const int64_t units = pass_units(P);
+    pass_fn fn = pick(h, mode);
+    const int64_t units = pass_units(h, P);
     const int grid = units > 0 ? pass_grid(h, (const void*)fn, units) : 0;
     const int kBatch = ND_BATCH;
     // Thm. 3 / Lemma 2: SND settles within the number of degree levels, at

@@ -87,6 +87,9 @@ struct nd_incidence {
     uint2* e_pos = nullptr;        // [m] (P(x,y), P(y,x)) of edge (x,y), x<y
     uint16_t* tg[2] = {nullptr, nullptr};  // [nnz] gather copies of tau by CSR position
     bool rows_sorted = false;      // rows ordered by w (else in fill order)
+    // (2,3) with no stored incidence (ND_BUILD_ON_THE_FLY): inc is empty and
+    // every pass finds the triangles of each edge again
+    bool otf = false;
     bool inc_aliases_graph = false;  // r = 1: inc_ptr/inc are rp/col
     // degree-bucketed processing order
     nd_item* items = nullptr;      // [num_r - num_zero], bucket by bucket
@@ -187,6 +190,16 @@ nd_status nd_classic_truss(const int32_t* in, int64_t n, int32_t* out, cudaStrea
 // evaluation (nd_eval.cu): Kendall's tau-b of two device sequences; waits on st
 nd_status nd_kendall_dev(const int32_t* x, const int32_t* y, int64_t n, int sm_count, double* tau_out,
                          int64_t* counts_out, cudaStream_t st);
+
+// lower bound of x in the sorted list a[0, n), n < 2^31 (32-bit offsets)
+static __device__ __forceinline__ int nd_lower_bound_n(const int32_t* __restrict__ a, int n, int32_t x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(a + mid) < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
 
 // launch geometry
 static inline int nd_blocks_for(int64_t work_items, int per_block, int cap) {

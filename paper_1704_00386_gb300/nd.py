@@ -24,7 +24,7 @@ ND_OK, ND_E_INVAL, ND_E_UNSUPPORTED_RS, ND_E_NOMEM, ND_E_CUDA, ND_E_NOT_CONVERGE
 ND_SND, ND_AND, ND_AND_NN = 0, 1, 2
 MODES = {"snd": ND_SND, "and": ND_AND, "and_nn": ND_AND_NN}
 
-SYMBOLS = ["nd_build_incidence", "nd_build_incidence_batch", "nd_incidence_info", "nd_r_cliques", "nd_s_degree", "nd_snd",
+SYMBOLS = ["nd_build_incidence", "nd_build_incidence_ex", "nd_build_incidence_batch", "nd_incidence_info", "nd_r_cliques", "nd_s_degree", "nd_snd",
            "nd_and", "nd_iterate_k", "nd_truss_classic", "nd_prof_enable", "nd_prof_read",
            "nd_last_passes", "nd_autotune", "nd_and_partial", "nd_and_until", "nd_count_equal", "nd_kendall_tau_b", "nd_incidence_bytes", "nd_free", "nd_strerror", "nd_last_error",
            "nd_abi_version", "nd_core_snd_noalloc"]
@@ -63,6 +63,7 @@ def load(build_if_missing: bool = True):
         i32, i64, vp, ci = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int
         P = ctypes.POINTER
         lib.nd_build_incidence.argtypes = [P(_CSR), ci, ci, vp, P(vp)]
+        lib.nd_build_incidence_ex.argtypes = [P(_CSR), ci, ci, ctypes.c_uint, vp, P(vp)]
         lib.nd_build_incidence_batch.argtypes = [P(_CSR), ci, ci, ci, vp, P(vp), vp]
         lib.nd_incidence_info.argtypes = [vp, P(i64), P(i64), P(ci)]
         lib.nd_r_cliques.argtypes = [vp, vp, ci, vp]
@@ -262,8 +263,13 @@ class Incidence:
         return ch[:n.value], ev[:n.value]
 
 
-def build_incidence(row_ptr, col, r: int, s: int, stream=None) -> Incidence:
-    """nd_build_incidence on a CSR given as numpy arrays (host) or CUDA tensors."""
+ND_BUILD_ON_THE_FLY = 1
+
+
+def build_incidence(row_ptr, col, r: int, s: int, stream=None, on_the_fly: bool = False) -> Incidence:
+    """nd_build_incidence on a CSR given as numpy arrays (host) or CUDA tensors.
+    on_the_fly: store no incidence and find the s-cliques again on every pass
+    (nd_build_incidence_ex with ND_BUILD_ON_THE_FLY; (1,2) and (2,3))."""
     lib = load()
     on_device = _is_torch(row_ptr)
     if on_device != _is_torch(col):
@@ -283,8 +289,12 @@ def build_incidence(row_ptr, col, r: int, s: int, stream=None) -> Incidence:
         n, nnz = row_ptr.size - 1, col.size
     csr = _CSR(n, nnz, _ptr(row_ptr).value, _ptr(col).value if nnz else None, int(on_device))
     h = ctypes.c_void_p()
-    _check(lib.nd_build_incidence(ctypes.byref(csr), int(r), int(s), _stream_ptr(stream),
-                                  ctypes.byref(h)), "nd_build_incidence")
+    if on_the_fly:
+        _check(lib.nd_build_incidence_ex(ctypes.byref(csr), int(r), int(s), ND_BUILD_ON_THE_FLY,
+                                         _stream_ptr(stream), ctypes.byref(h)), "nd_build_incidence_ex")
+    else:
+        _check(lib.nd_build_incidence(ctypes.byref(csr), int(r), int(s), _stream_ptr(stream),
+                                      ctypes.byref(h)), "nd_build_incidence")
     return Incidence(h, r, s, on_device, device, stream)
 
 

@@ -52,6 +52,20 @@ def test_host_buffers_need_the_gpu_too():
         nd.kendall_tau_b(k, k)
 
 
+def test_on_the_fly_flags_checked_before_touching_the_gpu():
+    import ctypes
+    import numpy as np
+    lib = nd.load()
+    rp = np.array([0, 1, 2], np.int64)
+    col = np.array([1, 0], np.int32)
+    csr = nd._CSR(2, 2, nd._ptr(rp).value, nd._ptr(col).value, 0)
+    h = ctypes.c_void_p()
+    assert lib.nd_build_incidence_ex(ctypes.byref(csr), 2, 3, 6, None, ctypes.byref(h)) == nd.ND_E_INVAL
+    assert lib.nd_build_incidence_ex(ctypes.byref(csr), 3, 4, nd.ND_BUILD_ON_THE_FLY, None,
+                                     ctypes.byref(h)) == nd.ND_E_UNSUPPORTED_RS
+    assert not h.value
+
+
 def test_rejects_bad_arguments_before_touching_the_gpu():
     import numpy as np
     rp = np.array([0, 1, 2], np.int64)
