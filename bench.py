@@ -54,9 +54,11 @@ def parse():
     p.add_argument("--workload", default="rmat_s20_ef16")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--mode", choices=["single", "batch", "serve"], default="single",
+    p.add_argument("--mode", choices=["single", "batch", "serve", "otf", "quality"], default="single",
                    help="single: one graph per step (default); batch: many graphs as one disjoint "
-                        "union vs one graph per launch; serve: Poisson request stream, p50/p99")
+                        "union vs one graph per launch; serve: Poisson request stream, p50/p99; "
+                        "otf: stored incidence vs no-storage passes; quality: Kendall-Tau and "
+                        "accuracy of the early-stopped iterates against kappa")
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--requests", type=int, default=192)
     return p.parse_args()
@@ -513,8 +515,83 @@ def run_serve(args):
     return 0
 
 
+def run_otf(args):
+    """The stored incidence against the no-storage mode (ND_BUILD_ON_THE_FLY)
+    on one workload: build, SND and AND times, memory held by the handle."""
+    import torch
+    from paper_1704_00386_gb300 import graphs as G
+    from paper_1704_00386_gb300 import nd
+    torch.cuda.set_device(0)
+    nd.load(build_if_missing=False)
+    w = G.workload(args.workload)
+    rp = torch.from_numpy(w["row_ptr"]).cuda()
+    col = torch.from_numpy(w["col"]).cuda()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return res, e0.elapsed_time(e1)
+
+    out = {"metric": METRIC, "unit": UNIT, "mode": "otf", "workload": args.workload, "r": w["r"], "s": w["s"]}
+    kappa = {}
+    for name, otf in (("stored", False), ("on_the_fly", True)):
+        inc = nd.build_incidence(rp, col, w["r"], w["s"], on_the_fly=otf)  # warm-up
+        inc.snd()
+        inc.free()
+        inc, ms_build = timed(lambda: nd.build_incidence(rp, col, w["r"], w["s"], on_the_fly=otf))
+        (tau, iters), ms_snd = timed(inc.snd)
+        ev_s = _evals_of(inc, 0)
+        (ta, it_a, ev_a), ms_and = timed(lambda: inc.and_(notify=True))
+        kappa[name] = tau
+        out[name] = {"build_ms": ms_build, "snd_ms": ms_snd, "snd_ms_per_pass": ms_snd / (iters + 1),
+                     "and_ms": ms_and, "updates_per_s": (ev_s + ev_a) / ((ms_snd + ms_and) / 1e3),
+                     "handle_bytes": inc.incidence_bytes(), "snd_equals_and": bool(torch.equal(tau, ta))}
+        inc.free()
+    out["results_identical"] = bool(torch.equal(kappa["stored"], kappa["on_the_fly"]))
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_quality(args):
+    """Section 5.2: how close the early-stopped iterates are to kappa, per
+    pass, as Kendall's tau-b against kappa and as the fraction of r-cliques
+    already at kappa (SND, and AND with notification)."""
+    import torch
+    from paper_1704_00386_gb300 import graphs as G
+    from paper_1704_00386_gb300 import nd
+    torch.cuda.set_device(0)
+    nd.load(build_if_missing=False)
+    w = G.workload(args.workload)
+    rp = torch.from_numpy(w["row_ptr"]).cuda()
+    col = torch.from_numpy(w["col"]).cuda()
+    inc = nd.build_incidence(rp, col, w["r"], w["s"])
+    kappa, iters = inc.snd()
+    out = {"mode": "quality", "workload": args.workload, "r": w["r"], "s": w["s"], "snd_iters": iters,
+           "kendall_tau_b": {}, "accuracy": {}}
+    for mode in ("snd", "and"):
+        kt, acc = [], []
+        for k in range(0, iters + 1):
+            tk, _ = inc.iterate_k(mode, k)
+            kt.append(nd.kendall_tau_b(tk, kappa))
+            acc.append(nd.count_equal(tk, kappa) / max(inc.num_r, 1))
+        out["kendall_tau_b"][mode] = kt
+        out["accuracy"][mode] = acc
+        out[f"{mode}_passes_to_kendall_0.90"] = next((k for k, v in enumerate(kt) if v >= 0.9), None)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.mode == "otf":
+        return run_otf(args)
+    if args.mode == "quality":
+        return run_quality(args)
     if args.mode == "batch":
         return run_batch(args)
     if args.mode == "serve":
