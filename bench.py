@@ -148,6 +148,23 @@ def cpu_oracle_sample(scale: int = CPU_SAMPLE_SCALE):
     return (ev_s + ev_a) / dt, dt, ev_s + ev_a, f"R-MAT scale {scale} EF16 (2,3), oracle build+SND+AND"
 
 
+# ------------------------------------------------------------- replicas
+
+def job_rate(local_ms: float, local_units: float, dist=None, device="cpu"):
+    """Whole-job throughput of N replicas: the units every rank processed,
+    summed, over the slowest rank's time (max over ranks).  Returns (rate per
+    second, max ms, total units).  With dist = None, the single-rank values."""
+    if dist is None:
+        return local_units / (local_ms / 1000.0), float(local_ms), float(local_units)
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    ms, units = float(t.item()), float(e.item())
+    return units / (ms / 1000.0), ms, units
+
+
 # ----------------------------------------------------------- reference arm
 
 def run_reference(args, rank, world):
@@ -250,16 +267,7 @@ def run_ours(args, rank, world, local_rank):
 
     total_ms = sum(step_ms)
     evals_rank = sum(i["snd_evals"] + i["and_evals"] for i in infos)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms_max = float(t.item())
-        e = torch.tensor([evals_rank], dtype=torch.float64, device=dev)
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-        evals_all = float(e.item())
-    else:
-        total_ms_max, evals_all = total_ms, float(evals_rank)
-    value = evals_all / (total_ms_max / 1000.0)
+    value, total_ms_max, evals_all = job_rate(total_ms, evals_rank, dist, dev)
 
     # parity of the timed results (bit-exact against the oracle's digest)
     tau_host = tau_s.cpu().numpy()
@@ -332,14 +340,8 @@ def run_ours(args, rank, world, local_rank):
             inc.free()
         barrier()
         dt = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([dt], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-            e = torch.tensor([float(ev_total)], dtype=torch.float64, device=dev)
-            dist.all_reduce(e, op=dist.ReduceOp.SUM)
-            ev_total = float(e.item())
-        e2e = {"value": ev_total / dt, "unit": UNIT,
+        e2e_rate, _, _ = job_rate(1000.0 * dt, ev_total, dist, dev)
+        e2e = {"value": e2e_rate, "unit": UNIT,
                "h2d_bytes_per_step": int(rp_pin.nbytes + col_pin.nbytes),
                "d2h_bytes_per_step": int(out_s.nbytes + out_a.nbytes)}
 
