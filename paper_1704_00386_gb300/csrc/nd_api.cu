@@ -220,6 +220,20 @@ static nd_status check_csr(const nd_csr* g) {
 }
 
 // the whole build on one (validated-header) CSR
+// size limits that can be told from the header, checked before any copy:
+// (2,3) keeps CSR positions and edge ids in 32 bits
+static nd_status check_limits(const nd_csr* g, int r) {
+    if (r >= 2 && g->nnz / 2 >= (int64_t)UINT32_MAX) {
+        nd_set_error("more than 2^32-1 edges");
+        return ND_E_TOO_LARGE;
+    }
+    if (r == 2 && g->nnz >= (int64_t)UINT32_MAX) {
+        nd_set_error("(2,3) needs fewer than 2^32-1 CSR entries");
+        return ND_E_TOO_LARGE;
+    }
+    return ND_OK;
+}
+
 static nd_status build_common(const nd_csr* g, int r, int s, cudaStream_t st, nd_incidence** out,
                               unsigned flags = 0) {
     int dev = 0;
@@ -269,6 +283,7 @@ nd_status nd_build_incidence(const nd_csr* g, int r, int s, void* stream, nd_inc
     *out = nullptr;
     ND_TRY(check_rs(r, s));
     ND_TRY(check_csr(g));
+    ND_TRY(check_limits(g, r));
     return build_common(g, r, s, (cudaStream_t)stream, out);
 }
 
@@ -282,6 +297,7 @@ nd_status nd_build_incidence_ex(const nd_csr* g, int r, int s, unsigned flags, v
         return ND_E_UNSUPPORTED_RS;
     }
     ND_TRY(check_csr(g));
+    ND_TRY(check_limits(g, r));
     return build_common(g, r, s, (cudaStream_t)stream, out, flags);
 }
 
@@ -308,6 +324,10 @@ nd_status nd_build_incidence_batch(const nd_csr* graphs, int count, int r, int s
         voff[i + 1] = n;
     }
     if (n >= INT32_MAX) { nd_set_error("batch has more than 2^31-1 vertices"); return ND_E_TOO_LARGE; }
+    {
+        const nd_csr whole{n, nnz, nullptr, nullptr, on_device};
+        ND_TRY(check_limits(&whole, r));
+    }
     nd_tmp<int64_t> urp(st);
     nd_tmp<int32_t> ucol(st);
     nd_status rc = ND_OK;

@@ -66,6 +66,23 @@ def test_on_the_fly_flags_checked_before_touching_the_gpu():
     assert not h.value
 
 
+def test_size_limits_checked_before_any_copy():
+    """A k-truss input with 2^32 or more CSR entries (any r >= 2 with 2^32 or
+    more edges) is refused from its header alone (the arrays are never read; a device pointer that is never
+    dereferenced stands in for 16 GB of column indices)."""
+    import ctypes
+    import numpy as np
+    lib = nd.load()
+    rp = np.array([0, 0], np.int64)
+    big = nd._CSR(1, 1 << 32, nd._ptr(rp).value, 0x1000, 1)
+    h = ctypes.c_void_p()
+    assert lib.nd_build_incidence(ctypes.byref(big), 2, 3, None, ctypes.byref(h)) == nd.ND_E_TOO_LARGE
+    assert "2^32" in nd.load().nd_last_error().decode()
+    bigger = nd._CSR(1, 1 << 33, nd._ptr(rp).value, 0x1000, 1)  # 2^32 edges: past the edge-id range
+    assert lib.nd_build_incidence(ctypes.byref(bigger), 3, 4, None, ctypes.byref(h)) == nd.ND_E_TOO_LARGE
+    assert not h.value
+
+
 def test_rejects_bad_arguments_before_touching_the_gpu():
     import numpy as np
     rp = np.array([0, 1, 2], np.int64)
