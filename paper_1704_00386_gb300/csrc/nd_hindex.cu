@@ -316,18 +316,23 @@ __device__ __forceinline__ void store_tau(const SweepParams& P, uint32_t R, int3
 
 // (2,3): notify the edge at CSR position pos, whose tau read from the
 // 16-bit copy is tv, if h <= tau (the exact int32 value when h > 65535).
-// The bit test is a relaxed L2 read: a stale 0 only costs a redundant
-// atomic, and a set bit is never cleared within a pass.
-__device__ __forceinline__ void notify_pos(const SweepParams& P, uint32_t pos, int32_t h, int32_t tv) {
+// The caller has just seen its frontier bit clear, with a relaxed L2 read:
+// a bit set meanwhile only costs a redundant atomic, and a set bit is never
+// cleared within a pass.
+__device__ __forceinline__ void notify_clear(const SweepParams& P, uint32_t pos, int32_t h, int32_t tv) {
     if (h > kTau16Max) tv = ld_tau<false>(P.tin + __ldg(P.eid + pos));
     if (h > tv) return;
     if (P.members) {  // PartialAnd: members only
         const uint32_t Rp = __ldg(P.eid + pos);
         if (!((__ldg(P.members + (Rp >> 5)) >> (Rp & 31)) & 1u)) return;
     }
-    const uint32_t bit = 1u << (pos & 31);
-    uint32_t* w = P.next + (pos >> 5);
-    if ((__ldcg(w) & bit) == 0u) atomicOr(w, bit);
+    atomicOr(P.next + (pos >> 5), 1u << (pos & 31));
+}
+
+// the same, testing the bit first and reading tau only if it is clear
+__device__ __forceinline__ void notify_pos(const SweepParams& P, uint32_t pos, int32_t h) {
+    if ((__ldcg(P.next + (pos >> 5)) >> (pos & 31)) & 1u) return;
+    notify_clear(P, pos, h, ld_tau<false>(P.gin + pos));
 }
 
 // is R in the current frontier?  (2,3): either bit of its two CSR positions
@@ -359,24 +364,24 @@ __device__ __forceinline__ void notify_row(const SweepParams& P, int64_t jb, int
         const uint2* pairs = reinterpret_cast<const uint2*>(P.inc);
         for (int64_t j0 = jb + first; j0 < je; j0 += (int64_t)kNotifyUnroll * step) {
             uint2 id[kNotifyUnroll];
-            int32_t a[kNotifyUnroll], b[kNotifyUnroll];
+            uint32_t wx[kNotifyUnroll], wy[kNotifyUnroll];
 #pragma unroll
             for (int u = 0; u < kNotifyUnroll; ++u) {
                 const int64_t j = j0 + (int64_t)u * step;
                 id[u] = j < je ? __ldg(pairs + j) : make_uint2(0u, 0u);
             }
+            // the frontier words first: a neighbour whose bit is already set
+            // needs neither its tau nor an atomic
 #pragma unroll
             for (int u = 0; u < kNotifyUnroll; ++u) {
                 const bool ok = j0 + (int64_t)u * step < je;
-                a[u] = ok ? ld_tau<false>(P.gin + id[u].x) : 0;
-                b[u] = ok ? ld_tau<false>(P.gin + id[u].y) : 0;
+                wx[u] = ok ? __ldcg(P.next + (id[u].x >> 5)) : 0xffffffffu;
+                wy[u] = ok ? __ldcg(P.next + (id[u].y >> 5)) : 0xffffffffu;
             }
 #pragma unroll
             for (int u = 0; u < kNotifyUnroll; ++u) {
-                if (j0 + (int64_t)u * step < je) {
-                    notify_pos(P, id[u].x, h, a[u]);
-                    notify_pos(P, id[u].y, h, b[u]);
-                }
+                if (!((wx[u] >> (id[u].x & 31)) & 1u)) notify_clear(P, id[u].x, h, ld_tau<false>(P.gin + id[u].x));
+                if (!((wy[u] >> (id[u].y & 31)) & 1u)) notify_clear(P, id[u].y, h, ld_tau<false>(P.gin + id[u].y));
             }
         }
     } else {
@@ -722,8 +727,8 @@ __global__ void __launch_bounds__(kThreads, ND_PASS_MIN_BLOCKS) k_pass_otf(Sweep
                     const int k = nd_lower_bound_n(P.col + lb, (int)(le - lb), w);
                     if (k >= (int)(le - lb) || __ldg(P.col + lb + k) != w) continue;
                     const uint32_t ps = (uint32_t)(sb + j), pl = (uint32_t)(lb + k);
-                    notify_pos(P, ps, h, ld_tau<false>(P.gin + ps));
-                    notify_pos(P, pl, h, ld_tau<false>(P.gin + pl));
+                    notify_pos(P, ps, h);
+                    notify_pos(P, pl, h);
                 }
             }
         }
