@@ -981,7 +981,7 @@ nd_status nd_build_k4_incidence(nd_incidence* h, cudaStream_t st) {
 
 nd_status nd_build_buckets(nd_incidence* h, cudaStream_t st) {
     const int64_t N = h->num_r;
-    // pass graphs hold the chunk table of the old buckets
+    // pass graphs hold the bucket ranges of the old buckets
     for (auto& row : h->pass_graph)
         for (auto& ex : row)
             if (ex) { cudaGraphExecDestroy(ex); ex = nullptr; }

@@ -30,6 +30,12 @@
 // r-clique is evaluated only if its bit is set in the current frontier; when
 // its tau drops to h it sets the next-frontier bit of every neighbour R' with
 // h <= tau(R') (Alg. 3, the orange lines).  It does not re-activate itself.
+//
+// (2,3) uses the adjacency layout: incidence entries are the CSR slots of
+// the other two edges, the gathers read a 16-bit copy of tau indexed by CSR
+// slot, and the frontier has one bit per slot.  k_pass_otf is the same update
+// with no stored incidence: it finds each edge's triangles again by
+// intersecting adjacency lists on every pass.
 #include <cooperative_groups.h>
 #include <cooperative_groups/reduce.h>
 
@@ -355,7 +361,7 @@ __device__ __forceinline__ bool in_frontier(const SweepParams& P, uint32_t R) {
 // while most neighbours need no write.)
 template <int Q>
 __device__ __forceinline__ void notify_row(const SweepParams& P, int64_t jb, int64_t je, int32_t h,
-                                           int first, int step, unsigned /*gmask*/) {
+                                           int first, int step) {
     if constexpr (Q == 2) {
         // (2,3): the entries are CSR positions; the frontier has one bit per
         // position, so the test reads the 16-bit copy and the bit sits next
@@ -398,13 +404,6 @@ __device__ __forceinline__ void notify_row(const SweepParams& P, int64_t jb, int
     }
 }
 
-template <int G>
-__device__ __forceinline__ unsigned group_mask() {
-    if (G >= 32) return 0xffffffffu;
-    const unsigned lane = threadIdx.x & 31;
-    return ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
-}
-
 __device__ __forceinline__ nd_item load_item(const nd_item* __restrict__ items, int64_t i) {
     longlong2 v = __ldg(reinterpret_cast<const longlong2*>(items) + i);
     nd_item it;
@@ -440,7 +439,7 @@ __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, 
         if (h != t0) changed++;
         if (!AND || h != t0) store_tau<Q>(P, R, h);
     }
-    if (AND && NOTIFY && h != t0) notify_row<Q>(P, jb, je, h, lane, G, group_mask<G>());
+    if (AND && NOTIFY && h != t0) notify_row<Q>(P, jb, je, h, lane, G);
 }
 
 // one r-clique per warp (rows of the warp bucket), streamed
@@ -463,7 +462,7 @@ __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item
         if (h != t0) changed++;
         if (!AND || h != t0) store_tau<Q>(P, R, h);
     }
-    if (AND && NOTIFY && h != t0) notify_row<Q>(P, jb, je, h, lane, 32, 0xffffffffu);
+    if (AND && NOTIFY && h != t0) notify_row<Q>(P, jb, je, h, lane, 32);
 }
 
 // one r-clique per CTA (rows longer than 2048 incidences)
@@ -491,7 +490,7 @@ __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int
             if (h != t0) changed++;
             if (!AND || h != t0) store_tau<Q>(P, R, h);
         }
-        if (AND && NOTIFY && h != t0) notify_row<Q>(P, jb, je, h, threadIdx.x, kThreads, 0xffffffffu);
+        if (AND && NOTIFY && h != t0) notify_row<Q>(P, jb, je, h, threadIdx.x, kThreads);
         __syncthreads();
     }
 }
@@ -764,7 +763,7 @@ pass_fn pick(const nd_incidence* h, int mode) {
 }
 
 // bucket ranges of a pass
-void plan_chunks(const nd_incidence* h, SweepParams& P) {
+void plan_buckets(const nd_incidence* h, SweepParams& P) {
     for (int b = 0; b < ND_NB; ++b) {
         P.lo[b] = h->bucket_lo[b];
         P.hi[b] = h->bucket_lo[b + 1];
@@ -1009,7 +1008,7 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
     P.ev = h->e_v;
     P.items = h->items;
     P.members = members;
-    plan_chunks(h, P);
+    plan_buckets(h, P);
     pass_fn fn = pick(h, mode);
     const int64_t units = pass_units(h, P);
     const int grid = units > 0 ? pass_grid(h, (const void*)fn, units) : 0;
