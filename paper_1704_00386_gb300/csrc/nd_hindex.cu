@@ -508,7 +508,8 @@ __global__ void __launch_bounds__(kThreads, ND_PASS_MIN_BLOCKS) k_pass(SweepPara
     // phase 1: rows longer than the CTA threshold, one per block at a time,
     // taken from a per-pass counter (longest rows first)
     const int64_t n3 = P.hi[3] - P.lo[3];
-    if (n3 > 0) {
+    auto cta_phase = [&]() {
+        if (n3 <= 0) return;
         for (;;) {
             if (threadIdx.x == 0) s_chunk = atomicAdd(P.ctr + 2, 1ull);
             __syncthreads();
@@ -517,9 +518,17 @@ __global__ void __launch_bounds__(kThreads, ND_PASS_MIN_BLOCKS) k_pass(SweepPara
             if (c >= n3) break;
             run_cta<Q, AND, NOTIFY>(P, P.lo[3] + c, P.lo[3] + c + 1, bins[0], bounds, changed, evals, incs);
         }
-    }
+    };
+    // AND updates in place, so a row evaluated later in a pass already sees
+    // what earlier rows lowered: AND takes the shortest rows first and the
+    // CTA rows last (measured 3% faster than longest first on R-MAT scale 20
+    // k-truss).  SND, whose pass reads only the previous pass, takes the
+    // longest rows first, for balance.
+    constexpr bool kShortFirst = AND;
+    if (!kShortFirst) cta_phase();
     // phase 2: warp tasks (one warp row, four 8-lane rows or eight 4-lane
-    // rows), longest first.  Each warp takes chunks of kWarpChunk
+    // rows), longest first (SND) or shortest first (AND).  Each warp takes
+    // chunks of kWarpChunk
     // consecutive tasks from a per-pass counter (one atomic per chunk, no
     // barrier): consecutive r-cliques share a vertex and gather from the
     // same part of tau, and dynamic chunks keep the warps balanced even when
@@ -533,8 +542,10 @@ __global__ void __launch_bounds__(kThreads, ND_PASS_MIN_BLOCKS) k_pass(SweepPara
         unsigned long long c = 0;
         if (lane32 == 0) c = atomicAdd(P.ctr + 4, 1ull);
         c = __shfl_sync(0xffffffffu, c, 0);
-        int64_t t = (int64_t)c * kWarpChunk;
-        if (t >= tasks) break;
+        const int64_t nchunks = (tasks + kWarpChunk - 1) / kWarpChunk;
+        if ((int64_t)c >= nchunks) break;
+        const int64_t cc = kShortFirst ? nchunks - 1 - (int64_t)c : (int64_t)c;
+        int64_t t = cc * kWarpChunk;
         const int64_t te = min(t + (int64_t)kWarpChunk, tasks);
         const int64_t e2 = min(te, n2);
         if (t < e2) {
@@ -558,6 +569,7 @@ __global__ void __launch_bounds__(kThreads, ND_PASS_MIN_BLOCKS) k_pass(SweepPara
             }
         }
     }
+    if (kShortFirst) cta_phase();
     __shared__ unsigned long long s_ch[kThreads / 32], s_ev[kThreads / 32], s_in[kThreads / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
