@@ -15,6 +15,8 @@
 // (read-only path).
 #include "nd_internal.cuh"
 
+#include <vector>
+
 namespace {
 
 constexpr int kThreads = 256;
@@ -43,12 +45,83 @@ __device__ __forceinline__ int64_t warp_count_global() {
 
 // ---- validation and degree split (one warp per vertex) -------------------
 // A row must lie inside [0, nnz], be strictly increasing, hold ids in [0, n)
-// other than its own, and every entry v of row u needs u in row v.  Writes
+// other than its own, and every entry v of row u needs u in row v (checked
+// for v > u here, and for v < u by the count 2m == nnz that follows).  Writes
 // nlow[u] = #neighbours < u and upcnt[u] = #neighbours > u.  Reads only
 // inside the bounds it has checked, so a malformed graph cannot fault.
 // With mirror (builds with r >= 2), it also records for every entry p of
 // row u the position of u in row v: the reverse entry, found by the same
 // search.
+// the checks of entries [pb, pe) of row u (which starts at b), one entry per
+// lane: the count of entries below the diagonal and whether any check failed
+__device__ __forceinline__ void validate_entries(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
+                                                 const int32_t* __restrict__ col, int64_t u, int64_t b, int64_t pb,
+                                                 int64_t pe, uint32_t* __restrict__ mirror, int& low, bool& rowbad) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t p = pb + lane; p < pe; p += 32) {
+        int32_t v = col[p];
+        if (v < 0 || v >= n || v == u) { rowbad = true; continue; }
+        if (p > b && col[p - 1] >= v) rowbad = true;
+        low += (v < u);
+        // only entries above the diagonal look for their reverse: the host
+        // then checks 2m == nnz, i.e. as many entries below the diagonal
+        // as above, so with every one above matched (injectively, distinct
+        // u in one row) every entry below is matched too
+        if (v < u) continue;
+        int64_t vb = rp[v], ve = rp[v + 1];
+        // a row longer than n - 1 cannot be simple (and would not fit the 32-bit search)
+        if (vb < 0 || ve < vb || ve > nnz || ve - vb >= n) { rowbad = true; continue; }
+        const int64_t pos = vb + nd_lower_bound_n(col + vb, (int)(ve - vb), (int32_t)u);
+        if (pos >= ve || col[pos] != (int32_t)u) { rowbad = true; continue; }
+        if (mirror) {
+            mirror[p] = (uint32_t)pos;
+            mirror[pos] = (uint32_t)p;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) low += __shfl_xor_sync(kFull, low, o);
+    rowbad = __any_sync(kFull, rowbad);
+}
+
+// Rows longer than kLongRow entries are not walked by one warp (a hub row of
+// a million entries would take a single warp tens of thousands of dependent
+// steps): the per-vertex kernels skip them, and a second launch spreads
+// their kLongSeg-entry segments over the whole grid.
+constexpr int64_t kLongRow = 4096;
+constexpr int64_t kLongSeg = 1024;
+
+__device__ __forceinline__ bool is_long_row(int64_t b, int64_t e) { return e - b > kLongRow; }
+
+// the rows (with valid bounds) longer than kLongRow, and their lengths
+__global__ void k_long_rows(int64_t n, int64_t nnz, const int64_t* __restrict__ rp, int32_t* __restrict__ rows,
+                            int64_t* __restrict__ len, unsigned long long* __restrict__ count) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = rp[u], e = rp[u + 1];
+        if (b < 0 || e < b || e > nnz || !is_long_row(b, e)) continue;
+        const unsigned long long i = atomicAdd(count, 1ull);
+        rows[i] = (int32_t)u;
+        len[i] = e - b;
+    }
+}
+
+// segment s of the long rows: row index i (seg_off[i] <= s < seg_off[i+1])
+// and the entry range [pb, pe)
+__device__ __forceinline__ void long_segment(int64_t s, const int32_t* __restrict__ rows,
+                                             const int64_t* __restrict__ seg_off, int64_t count,
+                                             const int64_t* __restrict__ rp, int64_t& u, int64_t& b, int64_t& pb,
+                                             int64_t& pe) {
+    int64_t lo = 0, hi = count;  // last i with seg_off[i] <= s
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (seg_off[mid] <= s) lo = mid; else hi = mid;
+    }
+    u = rows[lo];
+    b = rp[u];
+    const int64_t e = rp[u + 1];
+    pb = b + (s - seg_off[lo]) * kLongSeg;
+    pe = min(pb + kLongSeg, e);
+}
+
 __global__ void k_validate_split(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
                                  const int32_t* __restrict__ col, int32_t* __restrict__ nlow,
                                  int64_t* __restrict__ upcnt, int* __restrict__ err,
@@ -61,26 +134,37 @@ __global__ void k_validate_split(int64_t n, int64_t nnz, const int64_t* __restri
             if (lane == 0) { atomicOr(err, 1); nlow[u] = 0; upcnt[u] = 0; }
             continue;
         }
+        if (is_long_row(b, e)) {  // counted by k_validate_long
+            if (lane == 0) { nlow[u] = 0; upcnt[u] = 0; }
+            continue;
+        }
         int low = 0;
         bool rowbad = false;
-        for (int64_t p = b + lane; p < e; p += 32) {
-            int32_t v = col[p];
-            if (v < 0 || v >= n || v == u) { rowbad = true; continue; }
-            if (p > b && col[p - 1] >= v) rowbad = true;
-            low += (v < u);
-            int64_t vb = rp[v], ve = rp[v + 1];
-            // a row longer than n - 1 cannot be simple (and would not fit the 32-bit search)
-            if (vb < 0 || ve < vb || ve > nnz || ve - vb >= n) { rowbad = true; continue; }
-            const int64_t pos = vb + nd_lower_bound_n(col + vb, (int)(ve - vb), (int32_t)u);
-            if (pos >= ve || col[pos] != (int32_t)u) { rowbad = true; continue; }
-            if (mirror) mirror[p] = (uint32_t)pos;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) low += __shfl_xor_sync(kFull, low, o);
-        rowbad = __any_sync(kFull, rowbad);
+        validate_entries(n, nnz, rp, col, u, b, b, e, mirror, low, rowbad);
         if (lane == 0) {
             nlow[u] = low;
             upcnt[u] = (e - b) - low;
+            if (rowbad) atomicOr(err, 2);
+        }
+    }
+}
+
+// the long rows, one warp per segment; the counts add up per row
+__global__ void k_validate_long(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
+                                const int32_t* __restrict__ col, const int32_t* __restrict__ rows,
+                                const int64_t* __restrict__ seg_off, int64_t count, int64_t segs,
+                                int32_t* __restrict__ nlow, int64_t* __restrict__ upcnt, int* __restrict__ err,
+                                uint32_t* __restrict__ mirror) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t sg = warp_id_global(); sg < segs; sg += warp_count_global()) {
+        int64_t u, b, pb, pe;
+        long_segment(sg, rows, seg_off, count, rp, u, b, pb, pe);
+        int low = 0;
+        bool rowbad = false;
+        validate_entries(n, nnz, rp, col, u, b, pb, pe, mirror, low, rowbad);
+        if (lane == 0) {
+            atomicAdd(nlow + u, low);
+            atomicAdd(reinterpret_cast<unsigned long long*>(upcnt + u), (unsigned long long)((pe - pb) - low));
             if (rowbad) atomicOr(err, 2);
         }
     }
@@ -92,34 +176,57 @@ __global__ void k_validate_split(int64_t n, int64_t nnz, const int64_t* __restri
 // position p, for both directions (the reverse entry comes from mirror,
 // written by the validation, when there is one).  For the (2,3) adjacency
 // layout it also writes, per edge (x,y) with x < y, e_pos = (P(x,y), P(y,x)).
+__device__ __forceinline__ void edge_id_entries(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                const int32_t* __restrict__ nlow,
+                                                const int64_t* __restrict__ up_start, uint32_t* __restrict__ eid,
+                                                int32_t* __restrict__ e_u, int32_t* __restrict__ e_v,
+                                                const uint32_t* __restrict__ mirror, uint2* __restrict__ e_pos,
+                                                int64_t u, int64_t b, int64_t pb, int64_t pe) {
+    const int lane = threadIdx.x & 31;
+    const int64_t first_up = b + nlow[u];
+    const int64_t base = up_start[u];
+    for (int64_t p = pb + lane; p < pe; p += 32) {
+        int32_t v = col[p];
+        if (p >= first_up) {
+            int64_t id = base + (p - first_up);
+            eid[p] = (uint32_t)id;
+            e_u[id] = (int32_t)u;
+            e_v[id] = v;
+        } else {
+            const int64_t vfirst = rp[v] + nlow[v];
+            // the reverse entry: recorded by the validation when available
+            const int64_t pos = mirror ? (int64_t)mirror[p]
+                                       : lower_bound_i32(col, vfirst, rp[v + 1], (int32_t)u);
+            const int64_t id = up_start[v] + (pos - vfirst);
+            eid[p] = (uint32_t)id;
+            // edge (v,u), v < u: entry pos = P(v,u), entry p = P(u,v)
+            if (e_pos) e_pos[id] = make_uint2((uint32_t)pos, (uint32_t)p);
+        }
+    }
+}
+
 __global__ void k_edge_ids(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                            const int32_t* __restrict__ nlow, const int64_t* __restrict__ up_start,
                            uint32_t* __restrict__ eid, int32_t* __restrict__ e_u,
-                           int32_t* __restrict__ e_v, uint32_t* __restrict__ mirror,
+                           int32_t* __restrict__ e_v, const uint32_t* __restrict__ mirror,
                            uint2* __restrict__ e_pos) {
-    const int lane = threadIdx.x & 31;
     for (int64_t u = warp_id_global(); u < n; u += warp_count_global()) {
         const int64_t b = rp[u], e = rp[u + 1];
-        const int64_t first_up = b + nlow[u];
-        const int64_t base = up_start[u];
-        for (int64_t p = b + lane; p < e; p += 32) {
-            int32_t v = col[p];
-            if (p >= first_up) {
-                int64_t id = base + (p - first_up);
-                eid[p] = (uint32_t)id;
-                e_u[id] = (int32_t)u;
-                e_v[id] = v;
-            } else {
-                const int64_t vfirst = rp[v] + nlow[v];
-                // the reverse entry: recorded by the validation when available
-                const int64_t pos = mirror ? (int64_t)mirror[p]
-                                           : lower_bound_i32(col, vfirst, rp[v + 1], (int32_t)u);
-                const int64_t id = up_start[v] + (pos - vfirst);
-                eid[p] = (uint32_t)id;
-                // edge (v,u), v < u: entry pos = P(v,u), entry p = P(u,v)
-                if (e_pos) e_pos[id] = make_uint2((uint32_t)pos, (uint32_t)p);
-            }
-        }
+        if (is_long_row(b, e)) continue;  // k_edge_ids_long
+        edge_id_entries(rp, col, nlow, up_start, eid, e_u, e_v, mirror, e_pos, u, b, b, e);
+    }
+}
+
+__global__ void k_edge_ids_long(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                const int32_t* __restrict__ nlow, const int64_t* __restrict__ up_start,
+                                uint32_t* __restrict__ eid, int32_t* __restrict__ e_u, int32_t* __restrict__ e_v,
+                                const uint32_t* __restrict__ mirror, uint2* __restrict__ e_pos,
+                                const int32_t* __restrict__ rows, const int64_t* __restrict__ seg_off,
+                                int64_t count, int64_t segs) {
+    for (int64_t sg = warp_id_global(); sg < segs; sg += warp_count_global()) {
+        int64_t u, b, pb, pe;
+        long_segment(sg, rows, seg_off, count, rp, u, b, pb, pe);
+        edge_id_entries(rp, col, nlow, up_start, eid, e_u, e_v, mirror, e_pos, u, b, pb, pe);
     }
 }
 
@@ -685,6 +792,45 @@ nd_status read_i64(const int64_t* d, int64_t* hv, cudaStream_t st) {
 
 // Copy the caller's CSR into owned device buffers, validate it, split each
 // row at its own vertex and derive the canonical edge numbering offsets.
+// the rows longer than kLongRow and the offsets of their kLongSeg segments
+// (a host scan over the few such rows); kept on the handle for the edge ids
+static nd_status find_long_rows(nd_incidence* h, cudaStream_t st) {
+    h->long_count = h->long_segs = 0;
+    if (h->n == 0 || h->nnz <= kLongRow) return ND_OK;
+    const int64_t cap = h->nnz / kLongRow + 1;
+    ND_TRY(nd_alloc((void**)&h->long_rows, sizeof(int32_t) * cap, st, h));
+    nd_tmp<int64_t> len(st);
+    nd_tmp<unsigned long long> cnt(st);
+    ND_TRY(len.alloc(cap));
+    ND_TRY(cnt.alloc(1));
+    ND_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+    k_long_rows<<<nd_blocks_for(h->n, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(h->n, h->nnz, h->rp, h->long_rows,
+                                                                                     len, cnt);
+    ND_CUDA(cudaGetLastError());
+    unsigned long long c = 0;
+    ND_CUDA(cudaMemcpyAsync(&c, cnt.p, sizeof(c), cudaMemcpyDeviceToHost, st));
+    ND_TRY(nd_wait(st, 600.0));
+    if (c == 0) return ND_OK;
+    std::vector<int64_t> hl(c), off(c + 1, 0);
+    ND_CUDA(cudaMemcpyAsync(hl.data(), len.p, sizeof(int64_t) * c, cudaMemcpyDeviceToHost, st));
+    ND_TRY(nd_wait(st, 600.0));
+    for (unsigned long long i = 0; i < c; ++i) off[i + 1] = off[i] + (hl[i] + kLongSeg - 1) / kLongSeg;
+    ND_TRY(nd_alloc((void**)&h->long_seg, sizeof(int64_t) * (c + 1), st, h));
+    ND_CUDA(cudaMemcpyAsync(h->long_seg, off.data(), sizeof(int64_t) * (c + 1), cudaMemcpyHostToDevice, st));
+    ND_TRY(nd_wait(st, 600.0));  // off is a host temporary
+    h->long_count = (int64_t)c;
+    h->long_segs = off[c];
+    return ND_OK;
+}
+
+static void release_long_rows(nd_incidence* h, cudaStream_t st) {
+    nd_release(h->long_rows, st);
+    nd_release(h->long_seg, st);
+    h->long_rows = nullptr;
+    h->long_seg = nullptr;
+    h->long_count = h->long_segs = 0;
+}
+
 nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st) {
     h->n = g->n;
     h->nnz = g->nnz;
@@ -702,12 +848,19 @@ nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st) {
     ND_TRY(derr.alloc(1));
     ND_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
     ND_CUDA(cudaMemsetAsync(h->up_start, 0, sizeof(int64_t) * (g->n + 1), st));
+    ND_TRY(find_long_rows(h, st));
     if (g->n > 0) {
         nd_prof_scope ps("validate_split", st);
         int blocks = nd_blocks_for(g->n * 32, kThreads, grid_cap(h) * 4);
         k_validate_split<<<blocks, kThreads, 0, st>>>(g->n, g->nnz, h->rp, h->col, h->nlow,
                                                       h->up_start, derr, h->mirror);
         ND_CUDA(cudaGetLastError());
+        if (h->long_segs > 0) {
+            k_validate_long<<<nd_blocks_for(h->long_segs * 32, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(
+                g->n, g->nnz, h->rp, h->col, h->long_rows, h->long_seg, h->long_count, h->long_segs, h->nlow,
+                h->up_start, derr, h->mirror);
+            ND_CUDA(cudaGetLastError());
+        }
     }
     int herr = 0;
     ND_TRY(read_flag(derr, &herr, st));
@@ -720,10 +873,13 @@ nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st) {
     int64_t m = 0;
     ND_TRY(read_i64(h->up_start + g->n, &m, st));
     if (2 * m != g->nnz) {
-        nd_set_error("edge count is inconsistent with nnz");
+        // every entry above the diagonal has its reverse; a surplus below it
+        // is an entry without one
+        nd_set_error("col is not symmetric (more entries below the diagonal than above)");
         return ND_E_INVAL;
     }
     h->m = m;
+    if (h->r == 1) release_long_rows(h, st);  // no edge ids to build
     return ND_OK;
 }
 
@@ -747,7 +903,14 @@ nd_status nd_build_edges(nd_incidence* h, cudaStream_t st) {
         k_edge_ids<<<blocks, kThreads, 0, st>>>(h->n, h->rp, h->col, h->nlow, h->up_start, h->eid,
                                                 h->e_u, h->e_v, h->mirror, h->e_pos);
         ND_CUDA(cudaGetLastError());
+        if (h->long_segs > 0) {
+            k_edge_ids_long<<<nd_blocks_for(h->long_segs * 32, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(
+                h->rp, h->col, h->nlow, h->up_start, h->eid, h->e_u, h->e_v, h->mirror, h->e_pos, h->long_rows,
+                h->long_seg, h->long_count, h->long_segs);
+            ND_CUDA(cudaGetLastError());
+        }
     }
+    release_long_rows(h, st);
     if (!h->adj && h->mirror) {  // only the (2,3) build needs it further
         nd_release(h->mirror, st);
         h->mirror = nullptr;

@@ -68,9 +68,11 @@ struct SweepParams {
     const uint32_t* __restrict__ inc;
     const int32_t* tin;   // SND: tau of the previous pass; AND: same array as tout
     int32_t* tout;
-    // (2,3) gathers: tau by CSR position, 16 bits saturated at 65535 (exact
-    // for every row with d_s <= 65535, because tau <= d_s; longer rows read
-    // tin through eid).  An updated edge writes both of its entries (e_pos).
+    // gathers: a copy of tau in 16 bits saturated at 65535, exact for every
+    // row with tau(R) <= 65535 (the row only looks at min(rho, tau(R))); a
+    // row above that (a CTA row) gathers tin.  Indexed by CSR position for
+    // (2,3), where an updated edge writes both of its entries (e_pos), and by
+    // vertex for (1,2); (3,4) gathers tin.
     const uint16_t* gin;
     uint16_t* gout;
     const uint2* __restrict__ epos;
@@ -156,10 +158,14 @@ struct RhoExact2 {
 
 constexpr int32_t kTau16Max = 65535;
 
+// the gather of a row whose tau is at most 65535: the 16-bit copy for (1,2)
+// and (2,3).  (3,4) gathers int32 tau directly: its rows are not ordered, and
+// the 16-bit copy measured 3% slower there (config 3) against 6% faster for
+// a scale-24 k-core.
 template <int Q, bool RO>
 __device__ __forceinline__ auto make_rho(const SweepParams& P) {
-    if constexpr (Q == 2) return Rho<2, RO, uint16_t>{P.inc, P.gin};
-    else return Rho<Q, RO, int32_t>{P.inc, P.tin};
+    if constexpr (Q == 3) return Rho<3, RO, int32_t>{P.inc, P.tin};
+    else return Rho<Q, RO, uint16_t>{P.inc, P.gin};
 }
 
 // H({rho_j}) clipped to t, for one r-clique, by a group of G lanes; the row
@@ -312,11 +318,13 @@ __device__ __forceinline__ int32_t cta_hindex(const F& rho, int64_t jb, int64_t 
 template <int Q>
 __device__ __forceinline__ void store_tau(const SweepParams& P, uint32_t R, int32_t h) {
     P.tout[R] = h;
+    const uint16_t v = (uint16_t)min(h, kTau16Max);
     if (Q == 2) {
         const uint2 ep = __ldg(P.epos + R);
-        const uint16_t v = (uint16_t)min(h, kTau16Max);
         P.gout[ep.x] = v;
         P.gout[ep.y] = v;
+    } else if (Q == 1) {
+        P.gout[R] = v;
     }
 }
 
@@ -482,6 +490,8 @@ __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int
         int32_t h;
         if (Q == 2 && t > kTau16Max)  // only then can a saturated value matter
             h = cta_hindex(RhoExact2<!AND>{P.inc, P.eid, P.tin}, jb, je, t, bins, bounds);
+        else if (Q == 1 && t > kTau16Max)
+            h = cta_hindex(Rho<Q, !AND, int32_t>{P.inc, P.tin}, jb, je, t, bins, bounds);
         else
             h = cta_hindex(make_rho<Q, !AND>(P), jb, je, t, bins, bounds);
         if (threadIdx.x == 0) {
@@ -612,6 +622,17 @@ __global__ void k_tau_to_adj(int64_t N, const uint2* __restrict__ epos, const in
             b[ep.x] = v;
             b[ep.y] = v;
         }
+    }
+}
+
+// tau -> its 16-bit gather copies indexed by r-clique id ((1,2), (3,4))
+__global__ void k_tau_to_16(int64_t N, const int32_t* __restrict__ tau, uint16_t* __restrict__ a,
+                            uint16_t* __restrict__ b) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint16_t v = (uint16_t)min(max(tau[i], 0), kTau16Max);
+        a[i] = v;
+        if (b) b[i] = v;
     }
 }
 
@@ -805,8 +826,9 @@ nd_status ensure_state(nd_incidence* h, bool and_mode, cudaStream_t st) {
     const int64_t N = h->num_r > 0 ? h->num_r : 1;
     if (!h->tau[0]) ND_TRY(nd_alloc((void**)&h->tau[0], sizeof(int32_t) * N, st, h));
     if (!and_mode && !h->tau[1]) ND_TRY(nd_alloc((void**)&h->tau[1], sizeof(int32_t) * N, st, h));
-    if (h->adj) {
-        const int64_t E = h->nnz > 0 ? h->nnz : 1;
+    if (h->q != 3) {
+        // 16-bit gather copies: one per CSR slot for (2,3), per vertex for (1,2)
+        const int64_t E = h->adj ? (h->nnz > 0 ? h->nnz : 1) : N;
         if (!h->tg[0]) ND_TRY(nd_alloc((void**)&h->tg[0], sizeof(uint16_t) * E, st, h));
         if (!and_mode && !h->tg[1]) ND_TRY(nd_alloc((void**)&h->tg[1], sizeof(uint16_t) * E, st, h));
     }
@@ -981,9 +1003,13 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
             k_init_tau<<<blocks, kThreads, 0, st>>>(N, h->inc_ptr, h->tau[0], and_mode ? nullptr : h->tau[1]);
             ND_CUDA(cudaGetLastError());
         }
-        if (h->adj) {
+        if (h->q != 3) {
             nd_prof_scope ps("init_tau", st);
-            k_tau_to_adj<<<blocks, kThreads, 0, st>>>(N, h->e_pos, h->tau[0], h->tg[0], and_mode ? nullptr : h->tg[1]);
+            if (h->adj)
+                k_tau_to_adj<<<blocks, kThreads, 0, st>>>(N, h->e_pos, h->tau[0], h->tg[0],
+                                                          and_mode ? nullptr : h->tg[1]);
+            else
+                k_tau_to_16<<<blocks, kThreads, 0, st>>>(N, h->tau[0], h->tg[0], and_mode ? nullptr : h->tg[1]);
             ND_CUDA(cudaGetLastError());
         }
     }

@@ -82,6 +82,11 @@ struct nd_incidence {
     // sorted by w, and the passes gather tau from a 16-bit copy indexed by
     // CSR position (each edge's value at both of its entries, saturated at
     // 65535)
+    // build only: rows longer than a few thousand entries, split into
+    // segments for the per-vertex build kernels (rows, segment offsets)
+    int32_t* long_rows = nullptr;
+    int64_t* long_seg = nullptr;
+    int64_t long_count = 0, long_segs = 0;
     bool adj = false;
     uint32_t* mirror = nullptr;    // [nnz] build only: P(v,u) for the entry P(u,v)
     uint2* e_pos = nullptr;        // [m] (P(x,y), P(y,x)) of edge (x,y), x<y

@@ -185,6 +185,39 @@ def test_malformed_graph_rejected(nd, bad):
     assert e.value.status == nd.ND_E_INVAL
 
 
+def _csr_of_lists(lists):
+    rp = np.concatenate([[0], np.cumsum([len(l) for l in lists])]).astype(np.int64)
+    col = np.concatenate([np.asarray(l, np.int32) for l in lists]).astype(np.int32)
+    return rp, col
+
+
+@pytest.mark.parametrize("bad", ["unsorted", "asymmetric_below", "asymmetric_above", "selfloop"])
+def test_malformed_long_row_rejected(nd, bad):
+    """Rows longer than 4,096 entries are validated in segments by a second
+    launch; their faults must be found all the same.  A star: hub 0 and
+    6,000 leaves, plus a path through the leaves so that (2,3) has work."""
+    n = 6001
+    lists = [list(range(1, n))] + [[0] for _ in range(1, n)]
+    for leaf in range(1, n - 1):
+        lists[leaf].append(leaf + 1)
+        lists[leaf + 1].append(leaf)
+    lists = [sorted(l) for l in lists]
+    good_rp, good_col = _csr_of_lists(lists)
+    assert nd.build_incidence(good_rp, good_col, 2, 3).num_r == len(good_col) // 2
+    if bad == "unsorted":
+        lists[0][100], lists[0][101] = lists[0][101], lists[0][100]
+    elif bad == "asymmetric_above":
+        lists[4000].remove(0)        # the hub lists leaf 4000, which no longer lists it
+    elif bad == "asymmetric_below":
+        lists[0].remove(4000)        # leaf 4000 lists the hub, which no longer lists it
+    elif bad == "selfloop":
+        lists[0] = [0] + lists[0]    # the hub lists itself
+    rp, col = _csr_of_lists(lists)
+    with pytest.raises(nd.NDError) as e:
+        nd.build_incidence(rp, col, 2, 3)
+    assert e.value.status == nd.ND_E_INVAL
+
+
 def test_classic_truss_device(nd):
     k = torch.tensor([0, 3, 7], dtype=torch.int32, device="cuda")
     assert nd.truss_classic(k).cpu().tolist() == [2, 5, 9]
