@@ -283,8 +283,11 @@ __global__ void k_orient(int64_t n, const int64_t* __restrict__ rp, const int32_
 // one warp per oriented edge u -> v: the triangles {u, v, w}, w in out(u) /\ out(v).
 // ADJ: the entries are CSR positions, each pair ordered by its edge's
 // canonical endpoints (the entry of the smaller endpoint first).
+#ifndef ND_TRI_MIN_BLOCKS
+#define ND_TRI_MIN_BLOCKS 6  // resident blocks per SM for the triangle count / fill
+#endif
 template <bool FILL, bool ADJ>
-__global__ void __launch_bounds__(kThreads, 6) k_tri_oriented(int64_t m, const int64_t* __restrict__ out_ptr,
+__global__ void __launch_bounds__(kThreads, ND_TRI_MIN_BLOCKS) k_tri_oriented(int64_t m, const int64_t* __restrict__ out_ptr,
                                const int32_t* __restrict__ out_col, const uint32_t* __restrict__ out_eid,
                                const int32_t* __restrict__ out_src, const uint32_t* __restrict__ out_pos,
                                const uint32_t* __restrict__ out_mir, unsigned long long* __restrict__ ctr,
