@@ -165,7 +165,7 @@ void nd_free(nd_incidence* h) {
     cudaStreamSynchronize(st);
     void* ptrs[] = {h->nlow, h->up_start, h->eid, h->e_u, h->e_v, h->tri_ptr, h->tri_w, h->tri_e,
                     h->items, h->tau[0], h->tau[1], h->front[0], h->front[1], h->counters,
-                    h->mirror, h->e_pos, h->tg[0], h->tg[1], h->long_rows, h->long_seg};
+                    h->mirror, h->e_pos, h->tg[0], h->tg[1], h->long_rows, h->long_seg, h->to_new, h->to_old};
     for (void* p : ptrs) nd_release(p, st);
     for (auto& row : h->pass_graph)
         for (auto& ex : row)
@@ -252,6 +252,7 @@ static nd_status build_common(const nd_csr* g, int r, int s, cudaStream_t st, nd
     if (rc == ND_OK && r >= 2) rc = nd_build_edges(h, st);
     if (rc == ND_OK) {
         if (r == 1) {
+            rc = nd_relabel_by_degree(h, st);
             h->num_r = h->n;
             h->num_inc = h->nnz;
             h->inc_ptr = h->rp;
@@ -409,11 +410,21 @@ nd_status nd_s_degree(const nd_incidence* h, int32_t* out, int on_device, void* 
     cudaStream_t st = (cudaStream_t)stream;
     const_cast<nd_incidence*>(h)->last_stream = st;
     if (h->num_r == 0) return ND_OK;
-    if (on_device) return nd_init_tau(const_cast<nd_incidence*>(h), out, st);
-    nd_tmp<int32_t> tmp(st);
+    if (on_device && !h->to_new) return nd_init_tau(const_cast<nd_incidence*>(h), out, st);
+    nd_tmp<int32_t> tmp(st), tmp_old(st);
     ND_TRY(tmp.alloc(h->num_r));
     ND_TRY(nd_init_tau(const_cast<nd_incidence*>(h), tmp, st));
-    return deliver(tmp, h->num_r, out, 0, st);
+    const int32_t* res = tmp;
+    if (h->to_new) {  // internal ids -> caller's ids
+        ND_TRY(tmp_old.alloc(h->num_r));
+        ND_TRY(nd_permute_i32(h->to_new, tmp, tmp_old, h->num_r, false, st));
+        res = tmp_old;
+    }
+    if (on_device) {
+        ND_CUDA(cudaMemcpyAsync(out, res, sizeof(int32_t) * h->num_r, cudaMemcpyDeviceToDevice, st));
+        return host_wait(st);  // the temporaries are released on return
+    }
+    return deliver(res, h->num_r, out, 0, st);
 }
 
 static nd_status run_and_deliver(nd_incidence* h, int mode, int32_t max_passes, const int32_t* tau_in,
@@ -436,12 +447,23 @@ static nd_status run_and_deliver(nd_incidence* h, int mode, int32_t max_passes, 
             tin_dev = staged;
         }
     }
+    nd_tmp<int32_t> tin_new(st), res_old(st);
+    if (tin_dev && h->to_new) {  // caller's ids -> internal ids
+        ND_TRY(tin_new.alloc(h->num_r));
+        ND_TRY(nd_permute_i32(h->to_new, tin_dev, tin_new, h->num_r, true, st));
+        tin_dev = tin_new;
+    }
     int32_t* result = nullptr;
     int32_t updating = 0;
     int64_t evals = 0;
     bool converged = false;
     nd_status s = nd_run(h, mode, max_passes, tin_dev, &result, &updating, &evals, &converged, st, opts);
     if (s != ND_OK) return s;
+    if (h->to_new && h->num_r > 0) {  // internal ids -> caller's ids
+        ND_TRY(res_old.alloc(h->num_r));
+        ND_TRY(nd_permute_i32(h->to_new, result, res_old, h->num_r, false, st));
+        result = res_old;
+    }
     s = deliver(result, h->num_r, tau_out, on_device, st);
     if (s != ND_OK) return s;
     if (on_device) ND_TRY(host_wait(st));
@@ -493,7 +515,7 @@ nd_status nd_and_partial(nd_incidence* h, const uint32_t* members, int64_t count
         ND_CUDA(cudaMemcpyAsync(staged, members, sizeof(uint32_t) * count, cudaMemcpyHostToDevice, st));
         ids = staged;
     }
-    ND_TRY(nd_member_mask(ids, count, h->num_r, mask, derr, st));
+    ND_TRY(nd_member_mask(ids, count, h->num_r, mask, derr, st, h->to_new));
     int herr = 0;
     ND_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st));
     ND_CUDA(cudaStreamSynchronize(st));

@@ -170,6 +170,109 @@ __global__ void k_validate_long(int64_t n, int64_t nnz, const int64_t* __restric
     }
 }
 
+// ---- (1,2): vertices relabelled by degree class ----------------------------
+// The k-core pass gathers tau at the neighbour ids of every row.  With ids in
+// no particular order (a scrambled R-MAT), the gathers of a large graph go to
+// DRAM; most of them hit the few high-degree vertices, but those are spread
+// over the whole tau array, one value per line.  The build therefore gives
+// the vertices new ids by degree class, floor(log2 d) descending, stable
+// within a class, so that the values most gathered share lines.  Results
+// are permuted back at the boundary (nd_api.cu).
+constexpr int kClasses = 34;         // 0..31 by degree, 32: degree 0, 33: past n
+constexpr int kRelabelTile = 4096;   // vertices per block (16 rounds of 256)
+
+__device__ __forceinline__ int degree_class(int64_t d) {
+    return d == 0 ? 32 : 31 - (63 - __clzll((unsigned long long)d));  // high degree first
+}
+
+__global__ void k_class_count(int64_t n, const int64_t* __restrict__ rp, int64_t* __restrict__ cnt,
+                              int64_t nblocks) {
+    __shared__ unsigned c[kClasses];
+    for (int i = threadIdx.x; i < kClasses; i += blockDim.x) c[i] = 0;
+    __syncthreads();
+    const int64_t t0 = (int64_t)blockIdx.x * kRelabelTile;
+    for (int64_t v = t0 + threadIdx.x; v < min(t0 + kRelabelTile, n); v += blockDim.x)
+        atomicAdd(&c[degree_class(rp[v + 1] - rp[v])], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kClasses - 1; i += blockDim.x) cnt[(int64_t)i * nblocks + blockIdx.x] = c[i];
+}
+
+// new id = start of (class, block) + earlier vertices of the class in the block
+__global__ void k_class_scatter(int64_t n, const int64_t* __restrict__ rp, const int64_t* __restrict__ off,
+                                int64_t nblocks, int32_t* __restrict__ to_new, int32_t* __restrict__ to_old) {
+    __shared__ unsigned wcnt[kThreads / 32][kClasses];
+    __shared__ unsigned run[kClasses];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kClasses; i += blockDim.x) run[i] = 0;
+    const int64_t t0 = (int64_t)blockIdx.x * kRelabelTile;
+    for (int64_t r0 = t0; r0 < t0 + kRelabelTile; r0 += kThreads) {
+        const int64_t v = r0 + threadIdx.x;
+        const bool ok = v < n && v < t0 + kRelabelTile;
+        const int k = ok ? degree_class(rp[v + 1] - rp[v]) : kClasses - 1;
+        for (int i = lane; i < kClasses; i += 32) wcnt[warp][i] = 0;
+        __syncthreads();
+        const unsigned same = __match_any_sync(0xffffffffu, k);
+        const unsigned rank = __popc(same & ((1u << lane) - 1u));
+        if (rank == 0) wcnt[warp][k] = __popc(same);
+        __syncthreads();
+        if (ok) {
+            unsigned before = run[k];
+            for (int w = 0; w < warp; ++w) before += wcnt[w][k];
+            const int64_t id = off[(int64_t)k * nblocks + blockIdx.x] + before + rank;
+            to_new[v] = (int32_t)id;
+            to_old[id] = (int32_t)v;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < kClasses; i += blockDim.x) {
+            unsigned tot = 0;
+            for (int w = 0; w < kThreads / 32; ++w) tot += wcnt[w][i];
+            run[i] += tot;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_new_degrees(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ to_new,
+                              int64_t* __restrict__ len) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        len[to_new[v]] = rp[v + 1] - rp[v];
+}
+
+__device__ __forceinline__ void relabel_entries(const int32_t* __restrict__ col, const int32_t* __restrict__ to_new,
+                                                int32_t* __restrict__ ncol, int64_t b, int64_t nb, int64_t pb,
+                                                int64_t pe) {
+    for (int64_t p = pb + (threadIdx.x & 31); p < pe; p += 32) ncol[nb + (p - b)] = to_new[col[p]];
+}
+
+__global__ void k_relabel_rows(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                               const int32_t* __restrict__ to_new, const int64_t* __restrict__ nrp,
+                               int32_t* __restrict__ ncol) {
+    for (int64_t u = warp_id_global(); u < n; u += warp_count_global()) {
+        const int64_t b = rp[u], e = rp[u + 1];
+        if (is_long_row(b, e)) continue;  // k_relabel_long
+        relabel_entries(col, to_new, ncol, b, nrp[to_new[u]], b, e);
+    }
+}
+
+__global__ void k_relabel_long(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                               const int32_t* __restrict__ to_new, const int64_t* __restrict__ nrp,
+                               int32_t* __restrict__ ncol, const int32_t* __restrict__ rows,
+                               const int64_t* __restrict__ seg_off, int64_t count, int64_t segs) {
+    for (int64_t sg = warp_id_global(); sg < segs; sg += warp_count_global()) {
+        int64_t u, b, pb, pe;
+        long_segment(sg, rows, seg_off, count, rp, u, b, pb, pe);
+        relabel_entries(col, to_new, ncol, b, nrp[to_new[u]], pb, pe);
+    }
+}
+
+__global__ void k_permute_i32(int64_t n, const int32_t* __restrict__ idx, const int32_t* __restrict__ in,
+                              int32_t* __restrict__ out, int scatter) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (scatter) out[idx[i]] = in[i];
+        else out[i] = in[idx[i]];
+    }
+}
+
 // ---- canonical edge ids (one warp per vertex) ------------------------------
 // Edge (u,v), u < v, gets id up_start[u] + (rank of v among u's larger
 // neighbours): lexicographic order.  eid[p] is the id of the edge at CSR
@@ -882,7 +985,57 @@ nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st) {
         return ND_E_INVAL;
     }
     h->m = m;
-    if (h->r == 1) release_long_rows(h, st);  // no edge ids to build
+    return ND_OK;
+}
+
+nd_status nd_relabel_by_degree(nd_incidence* h, cudaStream_t st) {
+    const int64_t n = h->n, nnz = h->nnz;
+    if (n > 0) {
+        nd_prof_scope ps("relabel", st);
+        const int64_t nblocks = (n + kRelabelTile - 1) / kRelabelTile;
+        const int64_t cells = (int64_t)(kClasses - 1) * nblocks;
+        nd_tmp<int64_t> cnt(st);
+        ND_TRY(cnt.alloc(cells + 1));
+        ND_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (cells + 1), st));
+        k_class_count<<<nblocks, kThreads, 0, st>>>(n, h->rp, cnt, nblocks);
+        ND_CUDA(cudaGetLastError());
+        ND_TRY(nd_scan_i64(cnt, cells, st));
+        ND_TRY(nd_alloc((void**)&h->to_new, sizeof(int32_t) * n, st, h));
+        ND_TRY(nd_alloc((void**)&h->to_old, sizeof(int32_t) * n, st, h));
+        k_class_scatter<<<nblocks, kThreads, 0, st>>>(n, h->rp, cnt, nblocks, h->to_new, h->to_old);
+        ND_CUDA(cudaGetLastError());
+        int64_t* nrp = nullptr;
+        int32_t* ncol = nullptr;
+        ND_TRY(nd_alloc((void**)&nrp, sizeof(int64_t) * (n + 1), st, h));
+        ND_CUDA(cudaMemsetAsync(nrp + n, 0, sizeof(int64_t), st));
+        k_new_degrees<<<nd_blocks_for(n, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(n, h->rp, h->to_new, nrp);
+        ND_CUDA(cudaGetLastError());
+        ND_TRY(nd_scan_i64(nrp, n, st));
+        ND_TRY(nd_alloc((void**)&ncol, sizeof(int32_t) * (nnz > 0 ? nnz : 1), st, h));
+        if (nnz > 0) {
+            k_relabel_rows<<<nd_blocks_for(n * 32, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(
+                n, h->rp, h->col, h->to_new, nrp, ncol);
+            ND_CUDA(cudaGetLastError());
+            if (h->long_segs > 0) {
+                k_relabel_long<<<nd_blocks_for(h->long_segs * 32, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(
+                    h->rp, h->col, h->to_new, nrp, ncol, h->long_rows, h->long_seg, h->long_count, h->long_segs);
+                ND_CUDA(cudaGetLastError());
+            }
+        }
+        nd_release(h->rp, st);
+        nd_release(h->col, st);
+        h->rp = nrp;
+        h->col = ncol;
+    }
+    release_long_rows(h, st);
+    return ND_OK;
+}
+
+nd_status nd_permute_i32(const int32_t* idx, const int32_t* in, int32_t* out, int64_t n, bool scatter,
+                         cudaStream_t st) {
+    if (n == 0) return ND_OK;
+    k_permute_i32<<<nd_blocks_for(n, kThreads, 152 * 8), kThreads, 0, st>>>(n, idx, in, out, scatter ? 1 : 0);
+    ND_CUDA(cudaGetLastError());
     return ND_OK;
 }
 

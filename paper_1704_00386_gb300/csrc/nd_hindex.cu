@@ -658,10 +658,11 @@ __global__ void k_fill_front(int64_t N, uint32_t* __restrict__ f) {
 }
 
 __global__ void k_member_mask(const uint32_t* __restrict__ ids, int64_t count, int64_t N,
-                              uint32_t* __restrict__ mask, int* __restrict__ err) {
+                              uint32_t* __restrict__ mask, int* __restrict__ err, const int32_t* __restrict__ to_new) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t R = ids[i];
+        uint32_t R = ids[i];
         if ((int64_t)R >= N) { atomicOr(err, 1); continue; }
+        if (to_new) R = (uint32_t)to_new[R];  // relabelled (1,2) handle
         atomicOr(mask + (R >> 5), 1u << (R & 31));
     }
 }
@@ -946,10 +947,11 @@ nd_status nd_init_tau(nd_incidence* h, int32_t* tau, cudaStream_t st) {
     return ND_OK;
 }
 
-nd_status nd_member_mask(const uint32_t* ids, int64_t count, int64_t N, uint32_t* mask, int* err, cudaStream_t st) {
+nd_status nd_member_mask(const uint32_t* ids, int64_t count, int64_t N, uint32_t* mask, int* err, cudaStream_t st,
+                         const int32_t* to_new) {
     if (count == 0) return ND_OK;
     nd_prof_scope ps("member_mask", st);
-    k_member_mask<<<nd_blocks_for(count, kThreads, 152 * 8), kThreads, 0, st>>>(ids, count, N, mask, err);
+    k_member_mask<<<nd_blocks_for(count, kThreads, 152 * 8), kThreads, 0, st>>>(ids, count, N, mask, err, to_new);
     ND_CUDA(cudaGetLastError());
     return ND_OK;
 }

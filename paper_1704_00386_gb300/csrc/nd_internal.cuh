@@ -87,6 +87,11 @@ struct nd_incidence {
     int32_t* long_rows = nullptr;
     int64_t* long_seg = nullptr;
     int64_t long_count = 0, long_segs = 0;
+    // (1,2): vertices relabelled by degree class (nd_relabel_by_degree); rp and
+    // col hold the relabelled graph, and results are permuted back at the
+    // boundary.  Null when the handle keeps the caller's ids.
+    int32_t* to_new = nullptr;  // [n] caller's id -> internal id
+    int32_t* to_old = nullptr;  // [n] internal id -> caller's id
     bool adj = false;
     uint32_t* mirror = nullptr;    // [nnz] build only: P(v,u) for the entry P(u,v)
     uint2* e_pos = nullptr;        // [m] (P(x,y), P(y,x)) of edge (x,y), x<y
@@ -164,6 +169,10 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st);
 nd_status nd_build_triangles(nd_incidence* h, cudaStream_t st);
 nd_status nd_build_k4_incidence(nd_incidence* h, cudaStream_t st);
 nd_status nd_build_buckets(nd_incidence* h, cudaStream_t st);
+nd_status nd_relabel_by_degree(nd_incidence* h, cudaStream_t st);
+// out[idx[i]] = in[i] (scatter) or out[i] = in[idx[i]] (gather), n int32 values on st
+nd_status nd_permute_i32(const int32_t* idx, const int32_t* in, int32_t* out, int64_t n, bool scatter,
+                         cudaStream_t st);
 nd_status nd_write_r_cliques(const nd_incidence* h, int32_t* out_dev, cudaStream_t st);
 
 // batches (disjoint unions of independent graphs)
@@ -188,7 +197,8 @@ struct nd_run_opts {
 nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* tau_in_dev,
                  int32_t** tau_result, int32_t* updating, int64_t* evals, bool* converged,
                  cudaStream_t st, nd_run_opts* opts = nullptr);
-nd_status nd_member_mask(const uint32_t* ids, int64_t count, int64_t N, uint32_t* mask, int* err, cudaStream_t st);
+nd_status nd_member_mask(const uint32_t* ids, int64_t count, int64_t N, uint32_t* mask, int* err, cudaStream_t st,
+                         const int32_t* to_new = nullptr);
 nd_status nd_count_equal_dev(const int32_t* a, const int32_t* b, int64_t n, unsigned long long* out_dev,
                              cudaStream_t st);
 nd_status nd_classic_truss(const int32_t* in, int64_t n, int32_t* out, cudaStream_t st);
