@@ -399,14 +399,33 @@ __device__ __forceinline__ void notify_row(const SweepParams& P, int64_t jb, int
             }
         }
     } else {
-        for (int64_t j = jb + first; j < je; j += step) {
+        // (1,2), (3,4): ids of r-cliques; the same overlap, kNotifyUnroll
+        // entries (Q ids each) and their bit words loaded before any test
+        constexpr int U = Q == 1 ? kNotifyUnroll : 2;
+        for (int64_t j0 = jb + first; j0 < je; j0 += (int64_t)U * step) {
+            uint32_t id[U][Q], wd[U][Q];
 #pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                const uint32_t Rp = __ldg(P.inc + Q * j + k);
-                const uint32_t bit = 1u << (Rp & 31);
-                if (P.members && !(__ldg(P.members + (Rp >> 5)) & bit)) continue;  // PartialAnd
-                uint32_t* w = P.next + (Rp >> 5);
-                if ((__ldcg(w) & bit) == 0u && h <= ld_tau<false>(P.tin + Rp)) atomicOr(w, bit);
+            for (int u = 0; u < U; ++u) {
+                const int64_t j = j0 + (int64_t)u * step;
+#pragma unroll
+                for (int k = 0; k < Q; ++k) id[u][k] = j < je ? __ldg(P.inc + Q * j + k) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool ok = j0 + (int64_t)u * step < je;
+#pragma unroll
+                for (int k = 0; k < Q; ++k) wd[u][k] = ok ? __ldcg(P.next + (id[u][k] >> 5)) : 0xffffffffu;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                    const uint32_t Rp = id[u][k];
+                    const uint32_t bit = 1u << (Rp & 31);
+                    if (wd[u][k] & bit) continue;  // already active (or past the row's end)
+                    if (P.members && !(__ldg(P.members + (Rp >> 5)) & bit)) continue;  // PartialAnd
+                    if (h <= ld_tau<false>(P.tin + Rp)) atomicOr(P.next + (Rp >> 5), bit);
+                }
             }
         }
     }
