@@ -988,9 +988,13 @@ nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st) {
     return ND_OK;
 }
 
+// graphs smaller than this keep their ids: their tau fits in cache anyway,
+// and the few launches of a relabelling would dominate their build
+constexpr int64_t kRelabelMinVertices = 1 << 16;
+
 nd_status nd_relabel_by_degree(nd_incidence* h, cudaStream_t st) {
     const int64_t n = h->n, nnz = h->nnz;
-    if (n > 0) {
+    if (n >= kRelabelMinVertices) {
         nd_prof_scope ps("relabel", st);
         const int64_t nblocks = (n + kRelabelTile - 1) / kRelabelTile;
         const int64_t cells = (int64_t)(kClasses - 1) * nblocks;

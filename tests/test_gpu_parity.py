@@ -218,6 +218,34 @@ def test_malformed_long_row_rejected(nd, bad):
     assert e.value.status == nd.ND_E_INVAL
 
 
+def test_core_of_a_relabelled_graph(nd):
+    """k-core handles of 65,536 vertices or more keep their vertices in
+    degree-class order inside; every output, d_s, a caller's tau and
+    PartialAnd member ids stay in the caller's ids."""
+    n = 70000
+    s1, d1 = G.chung_lu(n, 2.2, 8.0, seed=301)
+    rp, col = G.to_csr(n, s1, d1)
+    inc = nd.build_incidence(rp, col, 1, 2)
+    g = oracle.Graph(rp, col, 1, 2)
+    np.testing.assert_array_equal(inc.s_degree(), g.s_degree())
+    np.testing.assert_array_equal(inc.r_cliques(), g.r_cliques())
+    kap = g.peel()
+    tau, iters = inc.snd()
+    np.testing.assert_array_equal(tau, kap)
+    assert iters == g.snd()[2]
+    np.testing.assert_array_equal(inc.and_()[0], kap)
+    t2 = g.snd(max_sweeps=2)[0]
+    np.testing.assert_array_equal(inc.iterate_k("snd", 2)[0], t2)
+    np.testing.assert_array_equal(inc.iterate_k("snd", 1 << 20, tau=t2)[0], kap)  # resume from caller ids
+    members = np.arange(0, n, 7, dtype=np.uint32)
+    mask = np.zeros(n, bool)
+    mask[members] = True
+    np.testing.assert_array_equal(inc.and_partial(members)[0], g.partial_and(mask)[0])
+    dev = nd.build_incidence(torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda(), 1, 2)
+    np.testing.assert_array_equal(dev.snd()[0].cpu().numpy(), kap)
+    np.testing.assert_array_equal(dev.s_degree().cpu().numpy(), g.s_degree())
+
+
 def test_classic_truss_device(nd):
     k = torch.tensor([0, 3, 7], dtype=torch.int32, device="cuda")
     assert nd.truss_classic(k).cpu().tolist() == [2, 5, 9]
