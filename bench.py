@@ -287,7 +287,8 @@ def run_ours(args, rank, world, local_rank):
     # 24 B (16 B work item, 4 B own tau, 4 B tau write; the first touch of
     # its value as a gathered tau is within the 4 B write) and, for (2,3),
     # 20 B more (8 B CSR positions of the edge, 8 B for its two copies in
-    # the gather layout, 4 B first touch of the second copy).  The q gathered
+    # the gather layout, 4 B first touch of the second copy), for (1,2) 4 B
+    # more (the 2 B write of its 16-bit copy and the first touch of it).  The q gathered
     # tau values per incidence are L2 hits while tau fits in L2, so they are
     # not DRAM bytes.
     info = infos[-1]
@@ -297,7 +298,7 @@ def run_ours(args, rank, world, local_rank):
     N_R, M, q = info["num_r"], info["M"], info["q"]
     if name in ("snd_pass", "and_pass"):
         key = "snd" if name == "snd_pass" else "and"
-        row_bytes = 44.0 if q == 2 else 24.0
+        row_bytes = 44.0 if q == 2 else (28.0 if q == 1 else 24.0)
         tot_bytes = sum(4.0 * q * sum(i[key + "_inc"]) + row_bytes * sum(i[key + "_rows"]) for i in infos)
         eff = sum(len(i[key + "_inc"]) for i in infos)
         per_launch = tot_bytes / max(eff, 1)
