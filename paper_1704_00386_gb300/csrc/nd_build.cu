@@ -389,11 +389,11 @@ __global__ void k_orient(int64_t n, const int64_t* __restrict__ rp, const int32_
 #ifndef ND_TRI_MIN_BLOCKS
 #define ND_TRI_MIN_BLOCKS 6  // resident blocks per SM for the triangle count / fill
 #endif
-template <bool FILL, bool ADJ>
+template <bool FILL, bool ADJ, typename C = unsigned long long>
 __global__ void __launch_bounds__(kThreads, ND_TRI_MIN_BLOCKS) k_tri_oriented(int64_t m, const int64_t* __restrict__ out_ptr,
                                const int32_t* __restrict__ out_col, const uint32_t* __restrict__ out_eid,
                                const int32_t* __restrict__ out_src, const uint32_t* __restrict__ out_pos,
-                               const uint32_t* __restrict__ out_mir, unsigned long long* __restrict__ ctr,
+                               const uint32_t* __restrict__ out_mir, C* __restrict__ ctr,
                                uint2* __restrict__ inc) {
     const int lane = threadIdx.x & 31;
     for (int64_t k = warp_id_global(); k < m; k += warp_count_global()) {
@@ -438,10 +438,10 @@ __global__ void __launch_bounds__(kThreads, ND_TRI_MIN_BLOCKS) k_tri_oriented(in
                         e_uw = a_is_u ? ea0 : eb;
                         e_vw = a_is_u ? eb : ea0;
                     }
-                    if (lane == 0) atomicAdd(ctr + e_uv, (unsigned long long)nf);
+                    if (lane == 0) atomicAdd(ctr + e_uv, (C)nf);
                     if (found) {
-                        atomicAdd(ctr + e_uw, 1ull);
-                        atomicAdd(ctr + e_vw, 1ull);
+                        atomicAdd(ctr + e_uw, (C)1);
+                        atomicAdd(ctr + e_vw, (C)1);
                     }
                 } else {
                     uint32_t pbp = 0, mb = 0;
@@ -455,11 +455,11 @@ __global__ void __launch_bounds__(kThreads, ND_TRI_MIN_BLOCKS) k_tri_oriented(in
                         e_vw = a_is_u ? eb : ea;
                     }
                     // the three slot reservations are independent: issue them together
-                    unsigned long long s0 = 0, s_uw = 0, s_vw = 0;
-                    if (lane == 0) s0 = atomicAdd(ctr + e_uv, (unsigned long long)nf);
+                    C s0 = 0, s_uw = 0, s_vw = 0;
+                    if (lane == 0) s0 = atomicAdd(ctr + e_uv, (C)nf);
                     if (found) {
-                        s_uw = atomicAdd(ctr + e_uw, 1ull);
-                        s_vw = atomicAdd(ctr + e_vw, 1ull);
+                        s_uw = atomicAdd(ctr + e_uw, (C)1);
+                        s_vw = atomicAdd(ctr + e_vw, (C)1);
                     }
                     s0 = __shfl_sync(kFull, s0, 0);
                     if (found) {
@@ -486,6 +486,16 @@ __global__ void __launch_bounds__(kThreads, ND_TRI_MIN_BLOCKS) k_tri_oriented(in
             if (base + 32 <= ae) lo = last_pb;
         }
     }
+}
+
+__global__ void k_widen_u32(int64_t m, const unsigned* __restrict__ in, int64_t* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int64_t)in[i];
+}
+
+__global__ void k_narrow_u32(int64_t m, const int64_t* __restrict__ in, unsigned* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (unsigned)in[i];
 }
 
 // ---- (2,3) adjacency layout: order each row by its third vertex -----------
@@ -1173,10 +1183,16 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
     ND_TRY(orient_graph(h, &o, st));
     const int eblocks = nd_blocks_for(m * 32, kThreads, grid_cap(h) * 4);
     {
-        nd_prof_scope ps("tri_count", st);
-        k_tri_oriented<false, false><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid, o.out_src,
-                                                                   nullptr, nullptr,
-                                                                   (unsigned long long*)h->inc_ptr, nullptr);
+        // per-edge counts fit 32 bits (d_s < n); 32-bit atomics, widened for the scan
+        nd_tmp<unsigned> cnt32(st);
+        ND_TRY(cnt32.alloc(m));
+        ND_CUDA(cudaMemsetAsync(cnt32, 0, sizeof(unsigned) * m, st));
+        nd_prof_scope ps("tri_count", st, 2);
+        k_tri_oriented<false, false, unsigned><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid,
+                                                                             o.out_src, nullptr, nullptr, cnt32.p,
+                                                                             nullptr);
+        ND_CUDA(cudaGetLastError());
+        k_widen_u32<<<nd_blocks_for(m, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(m, cnt32, h->inc_ptr);
         ND_CUDA(cudaGetLastError());
     }
     ND_TRY(nd_scan_i64(h->inc_ptr, m, st));
@@ -1191,15 +1207,26 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
     ND_TRY(nd_alloc((void**)&h->inc, sizeof(uint32_t) * 2 * (h->num_inc > 0 ? h->num_inc : 1), st, h));
     if (h->num_inc > 0) {
         nd_tmp<unsigned long long> cursor(st);
-        ND_TRY(cursor.alloc(m));
-        ND_CUDA(cudaMemcpyAsync(cursor, h->inc_ptr, sizeof(int64_t) * m, cudaMemcpyDeviceToDevice, st));
+        nd_tmp<unsigned> cursor32(st);
+        const bool narrow = h->adj && h->num_inc < (int64_t)UINT32_MAX;  // 32-bit slot atomics
+        if (narrow) {
+            ND_TRY(cursor32.alloc(m));
+            k_narrow_u32<<<nd_blocks_for(m, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(m, h->inc_ptr, cursor32);
+            ND_CUDA(cudaGetLastError());
+        } else {
+            ND_TRY(cursor.alloc(m));
+            ND_CUDA(cudaMemcpyAsync(cursor, h->inc_ptr, sizeof(int64_t) * m, cudaMemcpyDeviceToDevice, st));
+        }
         nd_prof_scope ps("tri_fill", st);
-        if (h->adj)
+        if (narrow)
+            k_tri_oriented<true, true, unsigned><<<eblocks, kThreads, 0, st>>>(
+                m, o.out_ptr, o.out_col, o.out_eid, o.out_src, o.out_pos, o.out_mir, cursor32.p, (uint2*)h->inc);
+        else if (h->adj)
             k_tri_oriented<true, true><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid, o.out_src,
-                                                                     o.out_pos, o.out_mir, cursor, (uint2*)h->inc);
+                                                                     o.out_pos, o.out_mir, cursor.p, (uint2*)h->inc);
         else
             k_tri_oriented<true, false><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid,
-                                                                      o.out_src, nullptr, nullptr, cursor,
+                                                                      o.out_src, nullptr, nullptr, cursor.p,
                                                                       (uint2*)h->inc);
         ND_CUDA(cudaGetLastError());
     }
