@@ -790,14 +790,15 @@ __global__ void k_k4(int64_t T, const otri* __restrict__ tris, const int64_t* __
 }
 
 // one thread per 4-clique: add it to the rows of its four triangles
-__global__ void k_k4_scatter(int64_t K, const uint4* __restrict__ k4, unsigned long long* __restrict__ cursor,
+template <typename C>
+__global__ void k_k4_scatter(int64_t K, const uint4* __restrict__ k4, C* __restrict__ cursor,
                              uint32_t* __restrict__ inc) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x) {
         const uint4 q = k4[i];
         const uint32_t id[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            uint32_t* d = inc + 3 * atomicAdd(cursor + id[k], 1ull);
+            uint32_t* d = inc + 3 * (int64_t)atomicAdd(cursor + id[k], (C)1);
             int o = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j)
@@ -1316,11 +1317,20 @@ nd_status nd_build_k4_incidence(nd_incidence* h, cudaStream_t st) {
     ND_TRY(read_i64(h->inc_ptr + T, &h->num_inc, st));
     ND_TRY(nd_alloc((void**)&h->inc, sizeof(uint32_t) * 3 * (h->num_inc > 0 ? h->num_inc : 1), st, h));
     if (K > 0) {
-        nd_tmp<unsigned long long> cursor(st);
-        ND_TRY(cursor.alloc(T));
-        ND_CUDA(cudaMemcpyAsync(cursor, h->inc_ptr, sizeof(int64_t) * T, cudaMemcpyDeviceToDevice, st));
         nd_prof_scope ps("k4_fill", st);
-        k_k4_scatter<<<nd_blocks_for(K, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(K, k4, cursor, h->inc);
+        const int kb = nd_blocks_for(K, kThreads, grid_cap(h) * 4);
+        if (h->num_inc < (int64_t)UINT32_MAX) {  // 32-bit slot atomics
+            nd_tmp<unsigned> cursor(st);
+            ND_TRY(cursor.alloc(T));
+            k_narrow_u32<<<nd_blocks_for(T, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(T, h->inc_ptr, cursor);
+            ND_CUDA(cudaGetLastError());
+            k_k4_scatter<unsigned><<<kb, kThreads, 0, st>>>(K, k4, cursor.p, h->inc);
+        } else {
+            nd_tmp<unsigned long long> cursor(st);
+            ND_TRY(cursor.alloc(T));
+            ND_CUDA(cudaMemcpyAsync(cursor, h->inc_ptr, sizeof(int64_t) * T, cudaMemcpyDeviceToDevice, st));
+            k_k4_scatter<unsigned long long><<<kb, kThreads, 0, st>>>(K, k4, cursor.p, h->inc);
+        }
         ND_CUDA(cudaGetLastError());
     }
     int herr = 0;
