@@ -77,7 +77,10 @@ typedef struct nd_incidence nd_incidence; /* opaque; owned by the library */
  * (the paper finds s-cliques through vertex neighbourhoods, Section 4.1,
  * "Time complexity"; here they are materialised once as CSR).
  * For each r-clique R the incidence lists, per s-clique S containing R, the
- * q = C(s,r) - 1 ids of the other r-cliques of S; row lengths are d_s(R).
+ * q = C(s,r) - 1 other r-cliques of S; row lengths are d_s(R).  How they are
+ * named inside the handle (edge ids, CSR slots, relabelled vertex ids) is
+ * internal: every call takes and returns r-cliques in the canonical order
+ * of nd_r_cliques.
  * The graph is validated first; a malformed graph returns ND_E_INVAL and
  * builds nothing.  Synchronises `stream` (sizes are read back to allocate).
  * On success *out owns device memory until nd_free(*out). */

@@ -4,9 +4,11 @@
 // neighbourhoods of its vertices (Section 4.1, "Time complexity": all
 // (s-r)-tuples of a neighbourhood), and recomputes them on every pass.  Here
 // they are found once, by sorted-list intersection, and stored:
-//   (1,2)  the CSR itself is the incidence (q = 1);
-//   (2,3)  triangle {u,v,w} -> one pair per edge: the ids of its other two
-//          edges (found once each, by degree orientation);
+//   (1,2)  the CSR itself is the incidence (q = 1), under ids ordered by
+//          degree class for graphs of 65,536 vertices or more;
+//   (2,3)  triangle {u,v,w} -> one pair per edge: the CSR slots of its other
+//          two edges at the edge's endpoints (found once each, by degree
+//          orientation), each row then ordered by the third vertex;
 //   (3,4)  triangle (u,v,w): x in N(u) /\ N(v) /\ N(w) -> the ids of the
 //          triangles {u,v,x}, {u,w,x}, {v,w,x}.
 // Every step is a count pass, an exclusive scan and a fill pass over the same
