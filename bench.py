@@ -40,9 +40,9 @@ UNIT = "updates/s"
 CPU_SAMPLE_SCALE = 14
 # ncu DRAM bytes per incidence of the SND pass (k-truss, q = 2), measured on the
 # current kernel on R-MAT scale 18 (dram__bytes_read.sum + dram__bytes_write.sum
-# = 2.686 GB + 59.4 MB per pass over 247,767,033 incidences); None once the
+# = 2.685 GB + 59.1 MB per pass over 247,767,033 incidences); None once the
 # kernel changes until it is measured again.
-NCU_SND_TRAFFIC_PER_INCIDENCE = (2.685624e9 + 59.436288e6) / 247767033
+NCU_SND_TRAFFIC_PER_INCIDENCE = (2.684543e9 + 59.060736e6) / 247767033
 
 
 def parse():
