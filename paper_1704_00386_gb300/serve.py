@@ -24,7 +24,10 @@ from . import nd
 
 def footprint_bytes(row_ptr: np.ndarray, col: np.ndarray, r: int) -> int:
     """Upper bound on the device bytes a request needs (graph copy, edge
-    arrays, incidence, work items, two tau buffers and frontiers).
+    arrays, incidence, work items, two tau buffers and frontiers), at the
+    build's peak: for (2,3) the incidence is written once and ranked into a
+    second buffer, next to the CSR-slot arrays; for large (1,2) graphs the
+    relabelled CSR sits next to the caller's copy.
 
     The incidence size is bounded by sum over edges of min(d_u, d_v) (common
     neighbours of an edge) for (2,3), and by that bound times the largest
@@ -33,21 +36,25 @@ def footprint_bytes(row_ptr: np.ndarray, col: np.ndarray, r: int) -> int:
     nnz = int(row_ptr[-1])
     deg = np.diff(row_ptr)
     base = 12 * (n + 1) + 8 * nnz + 16 * n
+    copies = 1  # incidence buffers alive at the build's peak
     if r == 1:
         num_r, inc = n, nnz
         q = 1
+        base += 8 * (n + 1) + 4 * nnz + 8 * n + 4 * n  # relabelled CSR, id maps, 16-bit copies
     else:
         u = np.repeat(np.arange(n), deg)
         up = u < col
         tri_bound = int(np.minimum(deg[u[up]], deg[col[up]]).astype(np.int64).sum())
         if r == 2:
             num_r, inc, q = nnz // 2, tri_bound, 2
+            copies = 2
+            base += 8 * (nnz // 2) + 4 * nnz + 4 * nnz + nnz // 4  # e_pos, 16-bit copies, reverse slots, frontier
         else:
             num_r = tri_bound // 3 + 1
             inc = tri_bound * int(deg.max() if n else 0) // 3
             q = 3
         base += 12 * (nnz // 2)
-    return int(base + 8 * (num_r + 1) + 4 * q * inc + 16 * num_r + 8 * num_r + num_r // 4 + (1 << 20))
+    return int(base + 8 * (num_r + 1) + copies * 4 * q * inc + 16 * num_r + 8 * num_r + num_r // 4 + (1 << 20))
 
 
 @dataclass(eq=False)
