@@ -241,6 +241,82 @@ def test_s_degree_matches_enumeration():
             assert g.num_incidences == sum(want)
 
 
+def _members_by_enumeration(rp, col, r, s):
+    """r-cliques (canonical order) and, per s-clique, the ids of its r-cliques,
+    from the brute-force clique enumeration."""
+    R = oracle.enumerate_cliques(rp, col, r)
+    S = oracle.enumerate_cliques(rp, col, s)
+    rid = {t: i for i, t in enumerate(R)}
+    return R, [[rid[sub] for sub in itertools.combinations(sc, r)] for sc in S]
+
+
+def _h_by_definition(vals):
+    return max(h for h in range(len(vals) + 1) if sum(v >= h for v in vals) >= h)
+
+
+def test_snd_trace_brute_force():
+    """Alg. 2 on tiny graphs, every pass checked: tau_{t+1}(R) is H, over the
+    s-cliques S containing R, of the smallest tau_t among the other r-cliques
+    of S (Def. 4), every value read from tau_t.  Written with sets and the
+    brute-force enumeration, and compared at every t, so an in-place update or
+    a dropped member changes some pass."""
+    rng = np.random.default_rng(11)
+    for rs in RS:
+        done = tries = 0
+        while done < 12 and tries < 500:
+            tries += 1
+            rp, col = _random_graph(rng, 5, 11, 36)
+            R, members = _members_by_enumeration(rp, col, *rs)
+            if not R:
+                continue
+            g = oracle.Graph(rp, col, *rs)
+            of = [[mem for mem in members if i in mem] for i in range(len(R))]
+            tau = [len(of[i]) for i in range(len(R))]     # tau_0 = d_s
+            t = 0
+            while True:
+                nxt = [_h_by_definition([min(tau[j] for j in mem if j != i) for mem in of[i]])
+                       for i in range(len(R))]
+                if nxt == tau:
+                    break
+                t += 1
+                assert list(g.snd(max_sweeps=t)[0]) == nxt, (rs, t)
+                tau = nxt
+            _, sweeps, updating, _ = g.snd()
+            assert updating == t and sweeps == t + 1
+            done += 1
+        assert done == 12, (rs, done)
+
+
+def test_degree_levels_brute_force():
+    """Def. 5 on tiny graphs with the S-degrees recounted from scratch at each
+    level: level i is every surviving r-clique of the smallest S-degree among
+    the survivors, counting only s-cliques whose r-cliques all survive; the
+    level leaves together."""
+    rng = np.random.default_rng(12)
+    for rs in RS:
+        done = tries = 0
+        while done < 12 and tries < 500:
+            tries += 1
+            rp, col = _random_graph(rng, 5, 11, 36)
+            R, members = _members_by_enumeration(rp, col, *rs)
+            if not R:
+                continue
+            alive = set(range(len(R)))
+            level = [None] * len(R)
+            k = 0
+            while alive:
+                deg = {i: sum(1 for mem in members if i in mem and all(j in alive for j in mem)) for i in alive}
+                low = min(deg.values())
+                for i in [i for i in alive if deg[i] == low]:
+                    level[i] = k
+                    alive.discard(i)
+                k += 1
+            count, lv = oracle.Graph(rp, col, *rs).degree_levels()
+            assert count == k and list(lv) == level, rs
+            done += 1
+        assert done == 12, (rs, done)
+
+
 # ---------------------------------------------------------------- theorems
 
 def _medium_graphs():
@@ -326,10 +402,23 @@ def test_networkx_core_number():
 
 
 def test_rejects_invalid_csr():
-    rp = np.array([0, 1, 1], np.int64)
-    col = np.array([1], np.int32)           # not symmetric
-    with pytest.raises(RuntimeError):
-        oracle.Graph(rp, col, 1, 2)
+    # Section 2: a simple undirected graph, here as a symmetric CSR with
+    # strictly increasing rows and no self-loops
+    bad = {
+        "not symmetric": ([0, 1, 1], [1]),
+        "self-loop": ([0, 2, 3], [0, 1, 0]),
+        "duplicate entry": ([0, 2, 4], [1, 1, 0, 0]),
+        "unsorted row": ([0, 2, 4, 6], [2, 1, 0, 2, 0, 1]),
+        "column out of range": ([0, 1, 2], [1, 2]),
+        "negative column": ([0, 1, 2], [-1, 0]),
+        "row_ptr[0] != 0": ([1, 2, 3], [1, 0]),
+        "decreasing row_ptr": ([0, 2, 1, 2], [1, 2, 0]),
+    }
+    for what, (rp, col) in bad.items():
+        for rs in RS:
+            with pytest.raises(RuntimeError):
+                oracle.Graph(np.array(rp, np.int64), np.array(col, np.int32), *rs)
+                pytest.fail(what)
     rp2, col2 = G.toy_core_graph()
     with pytest.raises(RuntimeError):
         oracle.Graph(rp2, col2, 1, 3)        # unsupported (r, s)
