@@ -180,18 +180,26 @@ static int validate(int64_t n, const int64_t *rp, const int32_t *col) {
             if (p > rp[u] && col[p - 1] >= v) return ORC_E_INVAL;
         }
     }
-    /* symmetry */
-    for (int64_t u = 0; u < n; ++u)
-        for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
-            int32_t v = col[p];
-            int64_t lo = rp[v], hi = rp[v + 1];
-            while (lo < hi) {
-                int64_t mid = lo + (hi - lo) / 2;
-                if (col[mid] < u) lo = mid + 1; else hi = mid;
-            }
-            if (lo >= rp[v + 1] || col[lo] != u) return ORC_E_INVAL;
-        }
-    return ORC_OK;
+    /* symmetry: build the transpose by a counting sort (rows visited in
+     * increasing u, so its rows come out sorted); the graph is symmetric iff
+     * the transpose equals the CSR itself */
+    const int64_t nnz = rp[n];
+    int64_t *tp = (int64_t *)calloc((size_t)n + 2, sizeof(int64_t));
+    int32_t *tc = (int32_t *)malloc(sizeof(int32_t) * ((size_t)nnz + 1));
+    if (!tp || !tc) { free(tp); free(tc); return ORC_E_NOMEM; }
+    for (int64_t p = 0; p < nnz; ++p) tp[col[p] + 1]++;
+    for (int64_t v = 0; v < n; ++v) tp[v + 1] += tp[v];
+    int st = ORC_OK;
+    for (int64_t v = 0; v <= n && st == ORC_OK; ++v)
+        if (tp[v] != rp[v]) st = ORC_E_INVAL;
+    if (st == ORC_OK) {
+        for (int64_t u = 0; u < n; ++u)
+            for (int64_t p = rp[u]; p < rp[u + 1]; ++p) tc[tp[col[p]]++] = (int32_t)u;
+        for (int64_t p = 0; p < nnz && st == ORC_OK; ++p)
+            if (tc[p] != col[p]) st = ORC_E_INVAL;
+    }
+    free(tp); free(tc);
+    return st;
 }
 
 void orc_free(orc_ctx *c) {

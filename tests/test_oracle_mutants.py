@@ -79,7 +79,8 @@ MUTANTS = {
     "accepts_unsorted_rows": ("if (p > rp[u] && col[p - 1] >= v) return ORC_E_INVAL;", ""),
     "accepts_self_loops": ("if (v < 0 || v >= n || v == u) return ORC_E_INVAL;",
                            "if (v < 0 || v >= n) return ORC_E_INVAL;"),
-    "accepts_asymmetric": ("if (lo >= rp[v + 1] || col[lo] != u) return ORC_E_INVAL;", ""),
+    "accepts_asymmetric": ("if (tc[p] != col[p]) st = ORC_E_INVAL;", ""),
+    "symmetry_ignores_row_lengths": ("if (tp[v] != rp[v]) st = ORC_E_INVAL;", ""),
     # Kendall's tau-b (Section 5.2)
     "kendall_ties_transposed": ("tx += (sx == 0);", "tx += (sy == 0);"),
     "kendall_denominator_repeats_x": ("(n0 - (double)tx) * (n0 - (double)ty)", "(n0 - (double)tx) * (n0 - (double)tx)"),

@@ -2,13 +2,17 @@
 
 * values the paper prints (worked examples in tests/golden/),
 * closed forms (cliques, cycles, stars, unions),
-* brute force on tiny graphs (Lemma 1 over all subsets; repeated deletion),
+* brute force on tiny graphs (Lemma 1 over all subsets; repeated deletion;
+  the SND trace from Def. 4 and the degree levels from Def. 5, written with
+  sets),
 * theorems (Thm. 1 monotonicity and lower bound, Thm. 3 level-by-level
   convergence, AND never slower than SND),
-* a library routine (networkx core numbers) where it is installed.
+* library routines (networkx core numbers where installed, scipy's Kendall tau),
+* rejection of malformed CSR input.
 
 A plausible slip in the oracle -- a dropped s-clique, max instead of min in
-rho, an off-by-one in H, a wrong r-clique id -- fails at least one of these.
+rho, an off-by-one in H, a wrong r-clique id -- fails at least one of these;
+test_oracle_mutants.py plants such slips one at a time to show it.
 """
 import itertools
 import json
@@ -406,6 +410,7 @@ def test_rejects_invalid_csr():
     # strictly increasing rows and no self-loops
     bad = {
         "not symmetric": ([0, 1, 1], [1]),
+        "directed cycle (in- and out-degrees match)": ([0, 1, 2, 3], [1, 2, 0]),
         "self-loop": ([0, 2, 3], [0, 1, 0]),
         "duplicate entry": ([0, 2, 4], [1, 1, 0, 0]),
         "unsorted row": ([0, 2, 4, 6], [2, 1, 0, 2, 0, 1]),
