@@ -8,6 +8,7 @@
  * fallback for it.
  *
  * Plain, slow, single-threaded C.  Every routine follows one passage:
+ *   - input: a simple undirected graph as a symmetric CSR ... Section 2
  *   - r-cliques, s-cliques and the S-degree d_s ............ Section 2, Def. 1
  *   - h-index H(K) by sorting ............................... Section 2.2, Def. 3
  *   - kappa_s by peeling (Batagelj-Zaversnik bins) .......... Section 2, Alg. 1
@@ -26,8 +27,8 @@
  *     reading that reproduces the 9 computations in 3 iterations traced for
  *     Fig. 6).
  *   - Iteration counts: `sweeps` counts every pass over the r-cliques,
- *     `updating` counts the passes that changed at least one tau (SND's
- *     "converges in two iterations" on Fig. 5 counts updating passes).
+ *     `updating` counts the passes that changed at least one tau (the two
+ *     iterations the paper gives SND on Fig. 5 are updating passes).
  *   - Canonical r-clique ids: lexicographic order of the sorted vertex tuple.
  *   - Kendall-Tau: the paper compares the ranking of the r-cliques by tau
  *     with the ranking by kappa and does not name the variant; with the many
@@ -170,6 +171,9 @@ static int64_t s_cliques_of(const orc_ctx *c, int64_t R, int32_t *buf, int32_t *
 
 /* ---- construction ---- */
 
+/* The graph of Section 2 is simple and undirected: rows strictly increasing
+ * (no duplicate edge), no self-loop, every id in range, and the adjacency
+ * symmetric.  Anything else is rejected, never repaired. */
 static int validate(int64_t n, const int64_t *rp, const int32_t *col) {
     if (n < 0 || rp[0] != 0) return ORC_E_INVAL;
     for (int64_t u = 0; u < n; ++u) {
