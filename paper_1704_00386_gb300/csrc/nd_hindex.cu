@@ -502,9 +502,9 @@ __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int
         const uint32_t R = it.R;
         if (AND && NOTIFY && !in_frontier<Q>(P, R)) continue;
         const int32_t t0 = ld_tau<!AND>(P.tin + R);
-    // H <= d_s, so tau is clipped at d_s for the search (a no-op for every
-    // valid tau, which is <= d_s); changes are detected against the stored value
-    const int32_t t = min(t0, (int32_t)it.d);
+        // H <= d_s, so tau is clipped at d_s for the search (a no-op for every
+        // valid tau, which is <= d_s); changes are detected against the stored value
+        const int32_t t = min(t0, (int32_t)it.d);
         const int64_t jb = it.jb, je = it.jb + it.d;
         int32_t h;
         if (Q == 2 && t > kTau16Max)  // only then can a saturated value matter
