@@ -373,6 +373,23 @@ def disjoint_union(*graphs):
     return np.concatenate(rps).astype(np.int64), np.concatenate(cols).astype(np.int32)
 
 
+def number_by_degree_class(row_ptr, col):
+    """The same graph with its vertices renumbered by degree class: classes
+    floor(log2(degree)) in descending order, isolated vertices last, the old
+    order kept inside a class.  Returns (row_ptr, col, new_id_of_old)."""
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    col = np.asarray(col)
+    n = row_ptr.size - 1
+    deg = np.diff(row_ptr)
+    cls = np.where(deg > 0, np.floor(np.log2(np.maximum(deg, 1))).astype(np.int64) + 1, 0)
+    order = np.lexsort((np.arange(n), -cls))       # old ids, in their new order
+    new_of_old = np.empty(n, dtype=np.int64)
+    new_of_old[order] = np.arange(n)
+    src = np.repeat(np.arange(n), deg)
+    rp, c = to_csr(n, new_of_old[src], new_of_old[col.astype(np.int64)])
+    return rp, c, new_of_old
+
+
 def workload(name: str):
     """Named synthetic workloads, each with its (r, s) job.
 
@@ -389,9 +406,13 @@ def workload(name: str):
         ef = int(name.split("_ef")[1].split("_")[0])
         n, src, dst = rmat(scale, ef, seed=2)
         rp, col = to_csr(n, src, dst)
-        return dict(name=name, r=2, s=3, row_ptr=rp, col=col,
-                    recipe=f"R-MAT scale {scale} edge factor {ef} (0.57,0.19,0.19,0.05) seed 2, "
-                           "symmetrised, deduplicated, no loops; k-truss (2,3)")
+        recipe = (f"R-MAT scale {scale} edge factor {ef} (0.57,0.19,0.19,0.05) seed 2, "
+                  "symmetrised, deduplicated, no loops; k-truss (2,3)")
+        if name.endswith("_byclass"):
+            # rmat_s{scale}_ef{ef}_byclass: the same graph, vertices numbered by degree class
+            rp, col, _ = number_by_degree_class(rp, col)
+            recipe += "; vertices renumbered by descending log2-degree class (stable)"
+        return dict(name=name, r=2, s=3, row_ptr=rp, col=col, recipe=recipe)
     if name.startswith("rmat_core_s") and "_ef" in name:
         # rmat_core_s{scale}_ef{ef}: k-core of a large R-MAT graph, generated with torch
         # (on the GPU when one is present, else on the CPU); arrays stay torch tensors

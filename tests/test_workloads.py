@@ -38,3 +38,23 @@ def test_rmat_truss_workload_shape():
     assert (w["r"], w["s"]) == (2, 3)
     assert w["row_ptr"].size - 1 == 1 << 16 and w["col"].size // 2 == 910000
     _simple(w["row_ptr"], w["col"])
+
+
+def test_degree_class_numbering_is_a_renumbering():
+    # the _byclass truss workload is the same graph with new vertex ids
+    w0 = G.workload("rmat_s12_ef16")
+    rp, col = w0["row_ptr"], w0["col"]
+    w = G.workload("rmat_s12_ef16_byclass")
+    rp2, col2 = w["row_ptr"], w["col"]
+    _simple(rp2, col2)
+    _, _, new_of_old = G.number_by_degree_class(rp, col)
+    n = rp.size - 1
+    assert sorted(new_of_old.tolist()) == list(range(n))
+    src = np.repeat(np.arange(n), np.diff(rp))
+    mapped = set(zip(new_of_old[src].tolist(), new_of_old[col].tolist()))
+    src2 = np.repeat(np.arange(n), np.diff(rp2))
+    assert mapped == set(zip(src2.tolist(), col2.tolist()))
+    # degree classes never increase along the new ids; isolated vertices last
+    deg2 = np.diff(rp2)
+    cls = np.where(deg2 > 0, np.floor(np.log2(np.maximum(deg2, 1))) + 1, 0)
+    assert (np.diff(cls) <= 0).all()
