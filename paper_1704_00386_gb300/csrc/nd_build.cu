@@ -94,13 +94,18 @@ constexpr int64_t kLongSeg = 1024;
 
 __device__ __forceinline__ bool is_long_row(int64_t b, int64_t e) { return e - b > kLongRow; }
 
-// the rows (with valid bounds) longer than kLongRow, and their lengths
+// the rows (with valid bounds) longer than kLongRow, and their lengths.  It
+// runs before validation: the rows of a valid offset array are disjoint, so
+// fewer than cap of them are long, and a count above cap (rows that overlap)
+// is written nowhere and reported by the caller.
 __global__ void k_long_rows(int64_t n, int64_t nnz, const int64_t* __restrict__ rp, int32_t* __restrict__ rows,
-                            int64_t* __restrict__ len, unsigned long long* __restrict__ count) {
+                            int64_t* __restrict__ len, unsigned long long cap,
+                            unsigned long long* __restrict__ count) {
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = rp[u], e = rp[u + 1];
         if (b < 0 || e < b || e > nnz || !is_long_row(b, e)) continue;
         const unsigned long long i = atomicAdd(count, 1ull);
+        if (i >= cap) continue;
         rows[i] = (int32_t)u;
         len[i] = e - b;
     }
@@ -923,12 +928,16 @@ static nd_status find_long_rows(nd_incidence* h, cudaStream_t st) {
     ND_TRY(len.alloc(cap));
     ND_TRY(cnt.alloc(1));
     ND_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
-    k_long_rows<<<nd_blocks_for(h->n, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(h->n, h->nnz, h->rp, h->long_rows,
-                                                                                     len, cnt);
+    k_long_rows<<<nd_blocks_for(h->n, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(
+        h->n, h->nnz, h->rp, h->long_rows, len, (unsigned long long)cap, cnt);
     ND_CUDA(cudaGetLastError());
     unsigned long long c = 0;
     ND_CUDA(cudaMemcpyAsync(&c, cnt.p, sizeof(c), cudaMemcpyDeviceToHost, st));
     ND_TRY(nd_wait(st, 600.0));
+    if (c > (unsigned long long)cap) {  // overlapping rows: not an offset array
+        nd_set_error("row_ptr is not a valid offset array");
+        return ND_E_INVAL;
+    }
     if (c == 0) return ND_OK;
     std::vector<int64_t> hl(c), off(c + 1, 0);
     ND_CUDA(cudaMemcpyAsync(hl.data(), len.p, sizeof(int64_t) * c, cudaMemcpyDeviceToHost, st));

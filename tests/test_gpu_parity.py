@@ -185,6 +185,20 @@ def test_malformed_graph_rejected(nd, bad):
     assert e.value.status == nd.ND_E_INVAL
 
 
+@pytest.mark.parametrize("rs", RS)
+def test_overlapping_long_rows_rejected(nd, rs):
+    """Long rows are listed before validation into arrays sized for disjoint
+    rows; offsets whose rows overlap (every other row runs backwards, so
+    each forward row spans the whole of col) must come back as ND_E_INVAL
+    with nothing written past those arrays."""
+    n, span = 7, 4100
+    rp = np.array([0 if u % 2 == 0 else span for u in range(n)] + [span], np.int64)
+    col = (np.arange(span) % n).astype(np.int32)
+    with pytest.raises(nd.NDError) as e:
+        nd.build_incidence(rp, col, *rs)
+    assert e.value.status == nd.ND_E_INVAL
+
+
 def _csr_of_lists(lists):
     rp = np.concatenate([[0], np.cumsum([len(l) for l in lists])]).astype(np.int64)
     col = np.concatenate([np.asarray(l, np.int32) for l in lists]).astype(np.int32)
