@@ -50,6 +50,16 @@ def _cases():
     dst += list(b + 2)
     out["book1300"] = G.to_csr(fan + 2, src, dst)
     out["hubs3000"] = G.hub_graph(3000, 6, seed=107)
+    # closed forms: K_12 minus a perfect matching (kappa = d_s everywhere), a
+    # wheel (core 3, truss 1, no 4-clique) and a windmill of 7 triangles
+    half = 6
+    cp = [(u, v) for u in range(2 * half) for v in range(u + 1, 2 * half) if v != u + half]
+    out["cocktail12"] = G.to_csr(2 * half, [a for a, _ in cp], [b for _, b in cp])
+    rim = 13
+    wheel = [(0, i) for i in range(1, rim + 1)] + [(i, i % rim + 1) for i in range(1, rim + 1)]
+    out["wheel13"] = G.to_csr(rim + 1, [a for a, _ in wheel], [b for _, b in wheel])
+    wind = [p for i in range(7) for p in ((0, 1 + 2 * i), (0, 2 + 2 * i), (1 + 2 * i, 2 + 2 * i))]
+    out["windmill7"] = G.to_csr(15, [a for a, _ in wind], [b for _, b in wind])
     return out
 
 

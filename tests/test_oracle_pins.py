@@ -1,7 +1,8 @@
 """Pins for the CPU oracle: each check ties it to something other than itself.
 
 * values the paper prints (worked examples in tests/golden/),
-* closed forms (cliques, cycles, stars, unions),
+* closed forms (cliques, cycles, stars, unions, cocktail-party graphs,
+  complete bipartite graphs, wheels, windmills, the Petersen graph),
 * brute force on tiny graphs (Lemma 1 over all subsets; repeated deletion;
   the SND trace from Def. 4 and the degree levels from Def. 5, written with
   sets),
@@ -152,6 +153,77 @@ def test_cycle(k):
 def test_star(leaves):
     rp, col = G.star_graph(leaves)
     assert (oracle.Graph(rp, col, 1, 2).peel() == 1).all()
+    assert (oracle.Graph(rp, col, 2, 3).peel() == 0).all()
+
+
+def _edges_csr(n, pairs):
+    pairs = np.asarray(pairs, np.int64).reshape(-1, 2)
+    return G.to_csr(n, pairs[:, 0], pairs[:, 1])
+
+
+@pytest.mark.parametrize("half", [3, 4, 6])
+def test_cocktail_party_graph(half):
+    # K_n minus a perfect matching (n = 2 half): every r-clique sees the same
+    # number of s-cliques, so the whole graph attains d_s and kappa = d_s:
+    # core n-2, truss n-4 (common neighbours of u,v: all but u, v and their
+    # partners), (3,4) n-6
+    n = 2 * half
+    pairs = [(u, v) for u in range(n) for v in range(u + 1, n) if v != u + half]
+    rp, col = _edges_csr(n, pairs)
+    for (r, s), want in zip(RS, (n - 2, n - 4, n - 6)):
+        g = oracle.Graph(rp, col, r, s)
+        if g.num_r == 0:
+            continue
+        assert (g.s_degree() == want).all()
+        assert (g.peel() == want).all() and (g.snd()[0] == want).all()
+
+
+@pytest.mark.parametrize("a,b", [(1, 5), (3, 3), (4, 7)])
+def test_complete_bipartite(a, b):
+    # K_{a,b}: core min(a,b), no triangles
+    rp, col = _edges_csr(a + b, [(u, a + v) for u in range(a) for v in range(b)])
+    assert (oracle.Graph(rp, col, 1, 2).peel() == min(a, b)).all()
+    assert (oracle.Graph(rp, col, 2, 3).peel() == 0).all()
+    assert oracle.Graph(rp, col, 3, 4).num_r == 0
+
+
+@pytest.mark.parametrize("rim", [5, 8, 13])
+def test_wheel(rim):
+    # hub 0 and a rim cycle: every vertex is in the 3-core and no deeper (rim
+    # degree 3); a rim edge lies in one triangle, so the 1-truss (triangle
+    # convention) is the deepest; the rim triangles lie in no 4-clique once
+    # the rim has 5 or more vertices
+    pairs = [(0, i) for i in range(1, rim + 1)] + [(i, i % rim + 1) for i in range(1, rim + 1)]
+    rp, col = _edges_csr(rim + 1, pairs)
+    assert (oracle.Graph(rp, col, 1, 2).peel() == 3).all()
+    g = oracle.Graph(rp, col, 2, 3)
+    assert (g.peel() == 1).all() and (g.snd()[0] == 1).all()
+    t = oracle.Graph(rp, col, 3, 4)
+    assert t.num_r == rim and (t.peel() == 0).all()
+
+
+@pytest.mark.parametrize("blades", [1, 2, 7])
+def test_windmill(blades):
+    # triangles sharing one vertex: core 2, every edge in exactly one triangle
+    pairs = []
+    for i in range(blades):
+        a, b = 1 + 2 * i, 2 + 2 * i
+        pairs += [(0, a), (0, b), (a, b)]
+    rp, col = _edges_csr(2 * blades + 1, pairs)
+    assert (oracle.Graph(rp, col, 1, 2).peel() == 2).all()
+    g = oracle.Graph(rp, col, 2, 3)
+    assert (g.s_degree() == 1).all() and (g.peel() == 1).all()
+    t = oracle.Graph(rp, col, 3, 4)
+    assert t.num_r == blades and (t.peel() == 0).all()
+
+
+def test_petersen_graph():
+    # 3-regular, triangle-free: core 3 everywhere, truss 0
+    outer = [(i, (i + 1) % 5) for i in range(5)]
+    spokes = [(i, i + 5) for i in range(5)]
+    inner = [(5 + i, 5 + (i + 2) % 5) for i in range(5)]
+    rp, col = _edges_csr(10, outer + spokes + inner)
+    assert (oracle.Graph(rp, col, 1, 2).peel() == 3).all()
     assert (oracle.Graph(rp, col, 2, 3).peel() == 0).all()
 
 
