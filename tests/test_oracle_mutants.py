@@ -108,7 +108,9 @@ for name, fn in inspect.getmembers(P, inspect.isfunction):
     cases = [{}]
     for m in marks:
         if m.name == "parametrize":
-            cases = [{m.args[0]: v} for v in m.args[1]]
+            names = m.args[0].split(",") if isinstance(m.args[0], str) else list(m.args[0])
+            names = [x.strip() for x in names]
+            cases = [dict(zip(names, v if len(names) > 1 else (v,))) for v in m.args[1]]
     for kw in cases:
         try:
             fn(**kw)
