@@ -553,6 +553,35 @@ def test_partial_and_pins(rs):
         assert (g.partial_snd(small)[0] == t_small).all()
 
 
+def test_partial_and_brute_force():
+    """PartialAnd (end of Section 4.3) on tiny graphs against its definition:
+    the update operator of Def. 4 applied to the members only, non-members
+    held at d_s, iterated with sets until nothing changes."""
+    rng = np.random.default_rng(29)
+    for rs in RS:
+        done = tries = 0
+        while done < 10 and tries < 500:
+            tries += 1
+            rp, col = _random_graph(rng, 5, 11, 36)
+            R, members = _members_by_enumeration(rp, col, *rs)
+            if len(R) < 2:
+                continue
+            of = [[mem for mem in members if i in mem] for i in range(len(R))]
+            mask = rng.random(len(R)) < 0.5
+            tau = [len(of[i]) for i in range(len(R))]
+            while True:
+                nxt = [(_h_by_definition([min(tau[j] for j in mem if j != i) for mem in of[i]])
+                        if mask[i] else tau[i]) for i in range(len(R))]
+                if nxt == tau:
+                    break
+                tau = nxt
+            g = oracle.Graph(rp, col, *rs)
+            assert list(g.partial_and(mask)[0]) == tau, rs
+            assert list(g.partial_and(mask, notify=False)[0]) == tau, rs
+            done += 1
+        assert done == 10, (rs, done)
+
+
 # ---- Kendall-Tau (Section 5.2, Fig. 7) --------------------------------------
 
 def test_kendall_tau_b_hand_counted():
