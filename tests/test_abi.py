@@ -104,3 +104,49 @@ def test_binding_has_no_cpu_fallback():
     for f in os.listdir(os.path.join(ROOT, "paper_1704_00386_gb300")):
         if f.endswith(".py"):
             assert "import oracle" not in open(os.path.join(ROOT, "paper_1704_00386_gb300", f)).read()
+
+
+def test_every_call_checks_its_arguments_before_touching_the_gpu():
+    """Each entry point rejects a NULL handle, a negative size or a bad
+    option with a status, before any CUDA call (none is made here: this runs
+    with no GPU)."""
+    lib = nd.load()
+    INVAL = nd.ND_E_INVAL
+    i32, i64, dbl, cint = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_int()
+    r = ctypes.byref
+    assert lib.nd_incidence_info(None, r(i64), r(i64), r(cint)) == INVAL
+    assert lib.nd_incidence_bytes(None, r(i64)) == INVAL
+    assert lib.nd_r_cliques(None, None, 0, None) == INVAL
+    assert lib.nd_s_degree(None, None, 0, None) == INVAL
+    assert lib.nd_snd(None, None, 0, 10, r(i32), None) == INVAL
+    assert lib.nd_and(None, None, 0, 1, 10, r(i32), r(i64), None) == INVAL
+    assert lib.nd_iterate_k(None, 0, -1, None, 0, 0, r(i32), None) == INVAL   # negative k
+    assert lib.nd_iterate_k(None, 0, 1, None, 0, 0, r(i32), None) == INVAL    # no handle
+    assert lib.nd_and_partial(None, None, 0, 0, None, 10, r(i32), r(i64), None) == INVAL
+    assert lib.nd_and_until(None, 0.5, None, 0, 10, r(i32), r(i64), r(cint), None) == INVAL
+    assert lib.nd_autotune(None, 1, None, None, None) == INVAL
+    assert lib.nd_last_passes(None, None, None, None, 0, r(i32)) == INVAL
+    assert lib.nd_count_equal(None, None, -1, 0, r(i64), None) == INVAL
+    assert lib.nd_count_equal(None, None, 0, 0, None, None) == INVAL            # no result slot
+    assert lib.nd_truss_classic(None, -1, None, 0, None) == INVAL
+    assert lib.nd_kendall_tau_b(None, None, -1, 0, r(dbl), None, None) == INVAL
+    # batches: a negative count, or graphs missing
+    h = ctypes.c_void_p()
+    assert lib.nd_build_incidence_batch(None, -1, 1, 2, None, r(h), None) == INVAL
+    assert lib.nd_build_incidence_batch(None, 2, 1, 2, None, r(h), None) == INVAL
+    assert lib.nd_build_incidence_batch(None, 0, 2, 5, None, r(h), None) == nd.ND_E_UNSUPPORTED_RS
+    # no build flag outside the documented ones, the high bit included
+    import numpy as np
+    rp = np.array([0, 1, 2], np.int64)
+    col = np.array([1, 0], np.int32)
+    csr = nd._CSR(2, 2, nd._ptr(rp).value, nd._ptr(col).value, 0)
+    assert lib.nd_build_incidence_ex(r(csr), 2, 3, 1 << 31, None, r(h)) == INVAL
+    assert not h.value
+    # the allocation-free core call: sizes first
+    assert lib.nd_core_snd_noalloc(None, None, -1, 0, None, 10, r(i32), None) == INVAL
+    assert lib.nd_core_snd_noalloc(None, None, (1 << 20) + 1, 0, None, 10, r(i32), None) == nd.ND_E_TOO_LARGE
+    assert lib.nd_core_snd_noalloc(None, None, 0, 0, None, 10, r(i32), None) == nd.ND_OK  # empty graph
+    # every status has a message; an unknown one says so
+    for st in (nd.ND_OK, nd.ND_E_INVAL, nd.ND_E_UNSUPPORTED_RS, nd.ND_E_TOO_LARGE):
+        assert nd.strerror(st)
+    assert lib.nd_strerror(999) == b"unknown status"
