@@ -213,6 +213,10 @@ void orc_free(orc_ctx *c) {
     free(c);
 }
 
+/* The r-cliques of the graph and, with with_incidence, the s-cliques of each
+ * (Def. 1): vertices for r = 1; edges u < v in lexicographic order for r = 2;
+ * for r = 3 the triangles u < v < w, grouped by their edge (u, v) and listed
+ * by w.  Each s-clique of R is stored as the ids of its q other r-cliques. */
 int orc_create(int64_t n, const int64_t *rp, const int32_t *col, int r, int s, int with_incidence,
                orc_ctx **out) {
     *out = NULL;
@@ -297,7 +301,8 @@ int64_t orc_num_r(const orc_ctx *c) { return c->num_r; }
 int64_t orc_num_s_incidences(const orc_ctx *c) { return c->inc_off ? c->inc_off[c->num_r] : -1; }
 int orc_q(const orc_ctx *c) { return c->q; }
 
-/* r-clique vertex tuples in canonical (lexicographic) order */
+/* r-clique vertex tuples in canonical order: the lexicographic order of the
+ * sorted vertex tuples (the id convention both implementations share) */
 void orc_r_tuples(const orc_ctx *c, int32_t *out) {
     if (c->r == 1) {
         for (int64_t u = 0; u < c->n; ++u) out[u] = (int32_t)u;
@@ -404,6 +409,8 @@ static int32_t update_one(const orc_ctx *c, int64_t R, const int32_t *src, int32
     return orc_hindex(L, e - b);
 }
 
+/* tau_0 = d_s (Alg. 2 and Alg. 3 start from the S-degrees); with
+ * init_from_ds = 0 the caller's tau is the start (any kappa <= tau <= d_s) */
 static int init_tau(const orc_ctx *c, int32_t *tau, int init_from_ds) {
     if (!c->inc_off) return ORC_E_INVAL;
     if (init_from_ds)
