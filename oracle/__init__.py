@@ -106,6 +106,9 @@ class Graph:
         self.col = np.ascontiguousarray(col, dtype=np.int32)
         self.n = self.row_ptr.size - 1
         self.r, self.s = r, s
+        if self.row_ptr.size == 0 or int(self.row_ptr[-1]) != self.col.size:
+            # the C side cannot see the length of col: its offsets must end there
+            raise RuntimeError("oracle: invalid input (row_ptr must end at len(col))")
         h = ctypes.c_void_p()
         _check(lib.orc_create(self.n, _ptr(self.row_ptr), _ptr(self.col), r, s, int(incidence),
                               ctypes.byref(h)))

@@ -176,8 +176,10 @@ static int64_t s_cliques_of(const orc_ctx *c, int64_t R, int32_t *buf, int32_t *
  * symmetric.  Anything else is rejected, never repaired. */
 static int validate(int64_t n, const int64_t *rp, const int32_t *col) {
     if (n < 0 || rp[0] != 0) return ORC_E_INVAL;
-    for (int64_t u = 0; u < n; ++u) {
+    /* offsets first: non-decreasing, so every row lies inside col[0, rp[n]) */
+    for (int64_t u = 0; u < n; ++u)
         if (rp[u + 1] < rp[u]) return ORC_E_INVAL;
+    for (int64_t u = 0; u < n; ++u) {
         for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
             int32_t v = col[p];
             if (v < 0 || v >= n || v == u) return ORC_E_INVAL;

@@ -511,8 +511,10 @@ def test_rejects_invalid_csr():
         "unsorted row": ([0, 2, 4, 6], [2, 1, 0, 2, 0, 1]),
         "column out of range": ([0, 1, 2], [1, 2]),
         "negative column": ([0, 1, 2], [-1, 0]),
-        "row_ptr[0] != 0": ([1, 2, 3], [1, 0]),
-        "decreasing row_ptr": ([0, 2, 1, 2], [1, 2, 0]),
+        "row_ptr[0] != 0": ([1, 2, 3], [1, 0, 0]),
+        "decreasing row_ptr": ([0, 2, 1, 2], [1, 2]),
+        "a row past the end of col": ([0, 100, 2], [1, 0]),
+        "row_ptr ends before col": ([0, 1, 1], [1, 0]),
     }
     for what, (rp, col) in bad.items():
         for rs in RS:
