@@ -209,6 +209,33 @@ def test_overlapping_long_rows_rejected(nd, rs):
     assert e.value.status == nd.ND_E_INVAL
 
 
+def test_rows_past_the_16_bit_copy(nd):
+    """A book of 70,000 pages: spine edge (0,1) in 70,000 triangles and two
+    spine vertices of degree 70,001, so the first pass evaluates them with
+    tau above 65,535, where the gathers read exact int32 values instead of
+    the saturated 16-bit copy.  Closed forms (the oracle's linear merges with
+    the spine rows would take minutes): every vertex in the 2-core, every
+    edge in exactly the 1-truss (one triangle each off the spine), and no
+    4-clique."""
+    pages = 70000
+    w = np.arange(2, pages + 2)
+    rp, col = G.to_csr(pages + 2, np.concatenate([[0], np.zeros(pages, int), np.ones(pages, int)]),
+                       np.concatenate([[1], w, w]))
+    core = nd.build_incidence(rp, col, 1, 2)
+    assert (core.s_degree()[:2] == pages + 1).all()
+    assert (core.snd()[0] == 2).all() and (core.and_()[0] == 2).all()
+    for on_the_fly in (False, True):
+        truss = nd.build_incidence(rp, col, 2, 3, on_the_fly=on_the_fly)
+        assert truss.num_r == 2 * pages + 1
+        ds = truss.s_degree()
+        assert ds[0] == pages and (ds[1:] == 1).all()      # edge (0,1) comes first
+        tau, iters = truss.snd()
+        assert (tau == 1).all() and iters == 1
+        assert (truss.and_()[0] == 1).all()
+    nucleus = nd.build_incidence(rp, col, 3, 4)
+    assert nucleus.num_r == pages and (nucleus.snd()[0] == 0).all()
+
+
 def _csr_of_lists(lists):
     rp = np.concatenate([[0], np.cumsum([len(l) for l in lists])]).astype(np.int64)
     col = np.concatenate([np.asarray(l, np.int32) for l in lists]).astype(np.int32)
