@@ -15,8 +15,15 @@ value = h-index evaluations (SND + AND) / device time of the steps.
 step; each rank decomposes its own copy), launched by torchrun; value is the
 evaluations of all ranks / the slowest rank's time.
 
---impl reference: the CPU oracle (plain single-threaded C) on a bounded
-sample of the same workload (R-MAT scale 14, same generator), rank 0 only.
+--impl reference: the CPU oracle on the same graph, rank 0 only: its SND
+(Alg. 2, the oracle's arithmetic) with the loop over r-cliques split over
+every host core, one full pass per step, the incidence built once before
+the timed steps.
+
+After the timed region the default run also measures, without touching the
+headline: the R-MAT scale-26 k-core (one step), 256 graphs of the batched
+workload (one disjoint-union batch, autotuned, against one graph per
+launch) and a short Poisson request stream (p50 / p99), under "extra".
 """
 from __future__ import annotations
 
@@ -37,7 +44,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "r-clique h-index updates/sec to convergence; HBM GB/s vs peak; batched p99"
 UNIT = "updates/s"
-CPU_SAMPLE_SCALE = 14
+PEEL_SAMPLE_SCALE = 14    # the single-threaded peeling oracle, timed on a bounded sample
+CPU_SND_SECONDS = 10.0    # time budget of the multi-threaded SND passes of the CPU baseline
 # ncu DRAM bytes per incidence of the SND pass (k-truss, q = 2), measured on the
 # current kernel on R-MAT scale 18 (dram__bytes_read.sum + dram__bytes_write.sum
 # = 2.685 GB + 59.1 MB per pass over 247,767,033 incidences); None once the
@@ -61,6 +69,9 @@ def parse():
                         "accuracy of the early-stopped iterates against kappa")
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--requests", type=int, default=192)
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the measurements after the timed region (scale-26 k-core, batch, serve)")
+    p.add_argument("--cpu-threads", type=int, default=0, help="threads of the CPU baseline (0 = all)")
     return p.parse_args()
 
 
@@ -133,19 +144,74 @@ def sha(a: np.ndarray) -> str:
     return hashlib.sha256(np.ascontiguousarray(a, dtype="<i4").tobytes()).hexdigest()
 
 
-def cpu_oracle_sample(scale: int = CPU_SAMPLE_SCALE):
-    """The oracle's whole path (its own incidence build, SND, AND with
-    notification) on R-MAT scale `scale`, single-threaded."""
+def workload_config(w, rp_h, num_r=None, incidences=None, world=1):
+    """The config block both arms print for the same workload."""
+    cfg = {"workload": w["name"], "recipe": w["recipe"], "r": w["r"], "s": w["s"],
+           "n": int(rp_h.size - 1), "edges": int(rp_h[-1] // 2),
+           "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"}
+    if num_r is not None:
+        cfg["r_cliques"] = int(num_r)
+    if incidences is not None:
+        cfg["incidences"] = int(incidences)
+    return cfg
+
+
+class CpuSND:
+    """The oracle's SND on all host cores (oracle.ParallelSND: Alg. 2 with the
+    loop over r-cliques split over threads), on the graph of the workload
+    itself.  The incidence is built once (its seconds are reported)."""
+
+    def __init__(self, rp, col, r, threads=0):
+        import oracle
+        t0 = time.perf_counter()
+        self.g = oracle.ParallelSND(rp, col, r, threads=threads)
+        self.build_s = time.perf_counter() - t0
+        self.tau = None
+        self.passes = 0
+
+    def step(self):
+        """One full SND pass from the current tau (d_s at first); the same
+        pass again once converged (Alg. 2 evaluates every r-clique per pass).
+        Returns (evaluations, seconds)."""
+        t0 = time.perf_counter()
+        tau, sweeps, _, ev = self.g.snd(tau=self.tau, max_sweeps=1)
+        dt = time.perf_counter() - t0
+        self.tau = tau
+        self.passes += sweeps
+        return ev, dt
+
+
+def peel_sample(scale: int = PEEL_SAMPLE_SCALE):
+    """The single-threaded peeling oracle (Alg. 1) on R-MAT scale `scale`
+    (k-truss), the bounded sample of the exact kappa computation."""
     import oracle
     from paper_1704_00386_gb300 import graphs as G
     n, s, d = G.rmat(scale, 16, seed=2)
     rp, col = G.to_csr(n, s, d)
     t0 = time.perf_counter()
-    g = oracle.Graph(rp, col, 2, 3, incidence=True)
-    _, sw, _, ev_s = g.snd()
-    _, _, _, ev_a = g.and_(notify=True)
+    g = oracle.Graph(rp, col, 2, 3, incidence=False)
+    g.peel()
     dt = time.perf_counter() - t0
-    return (ev_s + ev_a) / dt, dt, ev_s + ev_a, f"R-MAT scale {scale} EF16 (2,3), oracle build+SND+AND"
+    return {"seconds": dt, "r_cliques": g.num_r, "r_cliques_per_s": g.num_r / dt, "threads": 1,
+            "sample": f"R-MAT scale {scale} EF16 k-truss, oracle peeling (Alg. 1, Batagelj-Zaversnik bins)"}
+
+
+def cpu_baseline(w, rp_h, col_h, threads=0, seconds=CPU_SND_SECONDS):
+    """SND passes of the oracle on all host cores on the workload's own graph,
+    for about `seconds` (at least one pass), plus the peeling sample."""
+    cpu = CpuSND(rp_h, col_h, w["r"], threads)
+    ev_tot, dt_tot = 0, 0.0
+    while dt_tot < seconds or cpu.passes == 0:
+        ev, dt = cpu.step()
+        ev_tot += ev
+        dt_tot += dt
+    peel = peel_sample()
+    return {"value": ev_tot / dt_tot, "unit": UNIT, "cores": cpu.g.threads, "kind": "oracle",
+            "sample": f"{w['name']} ({w['r']},{w['s']}) itself: {cpu.passes} full SND passes from d_s "
+                      f"(oracle arithmetic, loop over r-cliques on {cpu.g.threads} threads); incidence "
+                      f"built once beforehand in {cpu.build_s:.1f} s (not timed)",
+            "seconds": dt_tot, "evaluations": ev_tot, "incidence_build_s": cpu.build_s,
+            "nproc": os.cpu_count(), "peel": peel}
 
 
 # ------------------------------------------------------------- replicas
@@ -168,26 +234,35 @@ def job_rate(local_ms: float, local_units: float, dist=None, device="cpu"):
 # ----------------------------------------------------------- reference arm
 
 def run_reference(args, rank, world):
+    """The oracle on the same graph as our arm: each step is one full SND pass
+    (Alg. 2) on all host cores; warm-up passes are untimed."""
     if rank != 0:
         return 0
-    rates, times = [], []
-    sample = ""
+    from paper_1704_00386_gb300 import graphs as G
+    w = G.workload(args.workload)
+    if not isinstance(w["row_ptr"], np.ndarray):  # generated on a device: bring it to the host
+        w = dict(w, row_ptr=w["row_ptr"].cpu().numpy(), col=w["col"].cpu().numpy())
+    rp_h, col_h = w["row_ptr"], w["col"]
+    cpu = CpuSND(rp_h, col_h, w["r"], args.cpu_threads)
+    times, evs = [], []
     for i in range(args.warmup + args.steps):
-        rate, dt, ev, sample = cpu_oracle_sample()
+        ev, dt = cpu.step()
         if i >= args.warmup:
-            rates.append(rate)
             times.append(dt)
-    total_ev_rate = sum(r * t for r, t in zip(rates, times)) / sum(times)
+            evs.append(ev)
+    value = sum(evs) / sum(times)
+    sample = (f"{w['name']} ({w['r']},{w['s']}) itself: one full SND pass per step (oracle arithmetic, "
+              f"loop over r-cliques on {cpu.g.threads} threads), continuing from the previous pass; "
+              f"incidence built once beforehand in {cpu.build_s:.1f} s (not timed)")
     line = {
-        "impl": "reference", "metric": METRIC, "value": total_ev_rate, "unit": UNIT,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * sum(times) / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": args.workload, "sample": sample},
-        "cpu_baseline": {"value": total_ev_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
-        "e2e": {"value": total_ev_rate, "unit": UNIT, "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 0},
+        "config": workload_config(w, rp_h, cpu.g.num_r, cpu.g.num_incidences, world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu.g.threads, "kind": "oracle",
+                         "sample": sample, "nproc": os.cpu_count()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -219,6 +294,12 @@ def run_ours(args, rank, world, local_rank):
         rp_h, col_h = rp_d.cpu().numpy(), col_d.cpu().numpy()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # 512 MB > 129 MB L2
     stream = torch.cuda.current_stream(dev)
+    # r-cliques in no s-clique (d_s = 0): counted as evaluated in every SND pass
+    # and in the first AND pass, as in the paper's loops, but never launched
+    probe = nd.build_incidence(rp_d, col_d, r, s)
+    num_zero = int((probe.s_degree() == 0).sum().item())
+    probe.free()
+    del probe
 
     def one_step():
         inc = nd.build_incidence(rp_d, col_d, r, s)
@@ -316,10 +397,30 @@ def run_ours(args, rank, world, local_rank):
     traffic = None
     if name == "snd_pass" and q == 2 and NCU_SND_TRAFFIC_PER_INCIDENCE is not None:
         traffic = NCU_SND_TRAFFIC_PER_INCIDENCE * M
+    # Three byte models of the same pass, each over its measured average time:
+    #   frac       compulsory DRAM bytes: 4q B per incidence streamed + the per-row
+    #              bytes above (the gathered tau values are L2 hits);
+    #   frac_survey every operand counted once, gathers included:
+    #              16 B per r-clique + 8q B per incidence (4 B id + 4 B gathered tau);
+    #   frac_dram  the DRAM bytes ncu measured (traffic), when known.
+    survey_bytes = None
+    if name in ("snd_pass", "and_pass"):
+        key = "snd" if name == "snd_pass" else "and"
+        sb = sum(8.0 * q * sum(i[key + "_inc"]) + 16.0 * sum(i[key + "_rows"]) for i in infos)
+        survey_bytes = sb / max(eff, 1)
+    survey_gbs = survey_bytes / (avg_ms / 1000.0) / 1e9 if survey_bytes else None
+    dram_gbs = traffic / (avg_ms / 1000.0) / 1e9 if traffic else None
     roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "bytes_per_launch": per_launch, "launches_effective": eff, "avg_launch_ms": avg_ms,
                 "units": units,
+                "frac_survey": survey_gbs / peak if survey_gbs else None,
+                "achieved_survey": survey_gbs,
+                "bytes_per_launch_survey": survey_bytes,
+                "units_survey": "16 B x r-cliques evaluated + 8q B x incidences streamed (4 B id + 4 B gathered tau)",
+                "frac_dram": dram_gbs / peak if dram_gbs else None,
+                "achieved_dram": dram_gbs,
+                "units_dram": "ncu dram__bytes_read.sum + dram__bytes_write.sum per pass (traffic) / average pass time",
                 "note": "gather-bound: the L1 wavefronts of the q tau gathers per incidence set the pace, not DRAM"}
 
     # ----- end to end through the public API with host buffers
@@ -346,11 +447,18 @@ def run_ours(args, rank, world, local_rank):
                "h2d_bytes_per_step": int(rp_pin.nbytes + col_pin.nbytes),
                "d2h_bytes_per_step": int(out_s.nbytes + out_a.nbytes)}
 
+    # launched evaluations: without the d_s = 0 rows of every SND pass and of the first AND pass
+    launched = sum(i["snd_evals"] - num_zero * len(i["snd_rows"]) + i["and_evals"] - num_zero * (1 if i["and_rows"] else 0)
+                   for i in infos)
+    value_launched, _, _ = job_rate(total_ms, launched, dist, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, dt, ev, sample = cpu_oracle_sample()
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-               "seconds": dt}
+        cpu = cpu_baseline(w, rp_h, col_h, args.cpu_threads)
+
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        extra = run_extras(args, dev)
 
     if rank == 0:
         phases = {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
@@ -359,17 +467,20 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "recipe": w["recipe"], "r": r, "s": s,
-                       "n": int(rp_h.size - 1), "edges": int(rp_h[-1] // 2), "r_cliques": N_R,
-                       "incidences": M, "l2": "flushed between steps (512 MB write)",
-                       "parallelism": f"replicas x{world}"},
+            "config": workload_config(w, rp_h, N_R, M, world),
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
             "gpu_launches": int(sum(v[0] for v in prof.values())),
             "clocks": clk,
             "per_step": {"snd_iters": info["snd_iters"], "and_iters": info["and_iters"],
                          "snd_evals": info["snd_evals"], "and_evals": info["and_evals"],
                          "and_incidences": sum(info["and_inc"]), "snd_incidences": sum(info["snd_inc"]),
+                         "zero_ds_r_cliques": num_zero,
+                         "launched_evals": (info["snd_evals"] - num_zero * len(info["snd_rows"]) +
+                                            info["and_evals"] - num_zero * (1 if info["and_rows"] else 0)),
                          "step_ms": step_ms},
+            "value_launched": value_launched,
+            "value_launched_note": "h-index evaluations actually launched (d_s = 0 rows excluded) / device time",
+            "extra": extra,
             "kernels": phases,
             "parity_vs_oracle_digest": parity, "snd_equals_and": same,
         }
@@ -383,22 +494,119 @@ def _evals_of(inc, and_evals):
 
 
 def run_batch(args):
-    """Config-4 shape: independent graphs (ER / Chung-Lu / R-MAT, n in
-    [100, 50000]), core and truss numbers for each.  One graph per launch
-    against the whole list as one disjoint-union batch, same GPU."""
+    """Config-4 shape, the whole list (default 4,096 graphs): one
+    disjoint-union batch against one graph per launch, same GPU."""
     import torch
-    from paper_1704_00386_gb300 import graphs as G
     from paper_1704_00386_gb300 import nd
     torch.cuda.set_device(0)
     nd.load(build_if_missing=False)
+    print(json.dumps(batch_measure(args.batch_count, steps=args.steps, autotune=True)), flush=True)
+    return 0
+
+
+SERVE_BUDGET = 64 << 30
+
+
+def serve_requests(count: int, seed: int = 5):
+    """Config-5a shape: graphs with 1K-2M edges (log-uniform), family uniform
+    over ER / Chung-Lu / R-MAT, job uniform over (1,2) / (2,3) / (3,4) ((3,4)
+    only where the footprint bound fits an eighth of the budget, else (2,3))."""
+    from paper_1704_00386_gb300 import graphs as G
+    from paper_1704_00386_gb300 import serve
+    rng = np.random.Generator(np.random.PCG64(seed))
+    edges = np.exp(rng.uniform(np.log(1e3), np.log(2e6), size=count))
+    reqs = []
+    for i, e in enumerate(edges):
+        fam = int(rng.integers(0, 3))
+        n = max(16, int(e * 2 / 8))
+        sd = 5_000_000 + i
+        if fam == 0:
+            a, b = G.erdos_renyi(n, 8.0 / (n - 1), seed=sd)
+        elif fam == 1:
+            a, b = G.chung_lu(n, 2.2, 8.0, seed=sd)
+        else:
+            _, a, b = G.rmat(max(1, int(np.ceil(np.log2(n)))), 8, seed=sd, n_limit=n)
+        rp, col = G.to_csr(n, a, b)
+        r, s_ = [(1, 2), (2, 3), (3, 4)][int(rng.integers(0, 3))]
+        if (r, s_) == (3, 4) and serve.footprint_bytes(rp, col, 3) > SERVE_BUDGET // 8:
+            r, s_ = 2, 3
+        reqs.append((rp, col, r, s_))
+    return reqs
+
+
+def serve_measure(reqs, loads=(0.5, 0.7, 0.9)):
+    """Saturated throughput, then p50/p99 latency at each load (a fraction of
+    saturation), against one-request-at-a-time service; every result checked
+    against the result served alone."""
+    from paper_1704_00386_gb300 import serve
+
+    def run_stream(arrivals, workers, batching=True):
+        srv = serve.Server(budget_bytes=SERVE_BUDGET, workers=workers, batch_bytes=(1 << 30) if batching else 1,
+                           max_batch=64 if batching else 1)
+        hs = []
+        t0 = time.perf_counter()
+        for (rp, col, r, s_), at in zip(reqs, arrivals):
+            d = t0 + at - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            hs.append(srv.submit(rp, col, r, s_, "and"))
+        srv.close()
+        span = max(h.finish for h in hs) - t0
+        return hs, span
+
+    zero = np.zeros(len(reqs))
+    run_stream(zero[:8], 4)                               # warm-up
+    hs, span = run_stream(zero, 4)
+    sat = len(reqs) / span
+    base_hs, base_span = run_stream(zero, 1, batching=False)
+    alone = {i: h.result for i, h in enumerate(base_hs)}
+    same = all(np.array_equal(h.result, alone[i]) for i, h in enumerate(hs))
+    out = {"metric": METRIC, "mode": "serve", "requests": len(reqs),
+           "edges_total": int(sum(int(rp[-1]) // 2 for rp, _, _, _ in reqs)),
+           "saturated_requests_per_s": sat, "one_at_a_time_requests_per_s": len(reqs) / base_span,
+           "saturated_latency": serve.latency_stats(hs), "results_identical_to_one_at_a_time": bool(same),
+           "load": {}}
+    for frac in loads:
+        arr = serve.poisson_arrivals(frac * sat, len(reqs), seed=int(frac * 100))
+        hs2, span2 = run_stream(arr, 4)
+        same2 = all(np.array_equal(h.result, alone[i]) for i, h in enumerate(hs2))
+        out["load"][str(frac)] = {"rate_per_s": frac * sat, "throughput_per_s": len(reqs) / span2,
+                                  "latency": serve.latency_stats(hs2), "results_identical": bool(same2),
+                                  "batched_requests": int(sum(h.batched_with > 1 for h in hs2))}
+    return out
+
+
+def run_serve(args):
+    """Config-5a shape: a Poisson stream of graphs with 1K-2M edges, mixed
+    jobs; saturated throughput, then p50/p99 latency at 0.5 / 0.7 / 0.9 of
+    it; one-request-at-a-time service as the baseline."""
+    import torch
+    from paper_1704_00386_gb300 import nd
+    torch.cuda.set_device(0)
+    nd.load(build_if_missing=False)
+    print(json.dumps(serve_measure(serve_requests(args.requests))), flush=True)
+    return 0
+
+
+def batch_measure(count: int, steps: int = 1, autotune: bool = False):
+    """Config-4 shape: `count` independent graphs (ER / Chung-Lu / R-MAT, n
+    in [100, 50000]), core and truss numbers for each: one disjoint-union
+    batch against one graph per launch, same GPU, results compared.  With
+    autotune, the batch handle's buckets are tuned (nd_autotune) first; the
+    tuned thresholds are cached for the size class and every later build of
+    the batch starts with them."""
+    import torch
+    from paper_1704_00386_gb300 import graphs as G
+    from paper_1704_00386_gb300 import nd
     workers = max(1, min(16, os.cpu_count() or 1))
     t0 = time.perf_counter()
-    gs = G.batch_graphs(args.batch_count, seed=4, workers=workers)
+    gs = G.batch_graphs(count, seed=4, workers=workers)
     gen_s = time.perf_counter() - t0
     dev = [(torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda()) for rp, col, _ in gs]
     stream = torch.cuda.current_stream()
     out = {"metric": METRIC, "unit": UNIT, "mode": "batch", "graphs": len(gs),
-           "edges": int(sum(int(rp[-1]) // 2 for rp, _, _ in gs)), "generation_s": gen_s, "jobs": {}}
+           "edges": int(sum(int(rp[-1]) // 2 for rp, _, _ in gs)), "generation_s": gen_s,
+           "autotuned": bool(autotune), "jobs": {}}
 
     def timed(fn):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -430,10 +638,15 @@ def run_batch(args):
             inc.free()
             return ev_s + ev_a, (t, offs)
 
+        thr = None
+        if autotune:
+            inc, _ = nd.build_incidence_batch(dev, r, s)
+            thr, _ = inc.autotune(passes=2)
+            inc.free()
         batched()                                 # warm-up
         (ev_b, (tb, offs)), ms_b = timed(batched)
         ms_bs = [ms_b]
-        for _ in range(max(0, args.steps - 1)):
+        for _ in range(max(0, steps - 1)):
             _, ms = timed(batched)
             ms_bs.append(ms)
         plain()                                   # warm-up
@@ -445,77 +658,69 @@ def run_batch(args):
             "batched_graphs_per_s": len(dev) / (ms_b / 1e3),
             "plain_ms": ms_p, "plain_updates_per_s": ev_p / (ms_p / 1e3),
             "plain_graphs_per_s": len(dev) / (ms_p / 1e3),
-            "speedup": ms_p / ms_b, "results_identical": bool(same)}
-    print(json.dumps(out), flush=True)
-    return 0
+            "speedup": ms_p / ms_b, "results_identical": bool(same),
+            "thresholds": list(thr) if thr else None}
+    return out
 
 
-def run_serve(args):
-    """Config-5a shape: a Poisson stream of graphs with 1K-2M edges
-    (log-uniform), family uniform over ER / Chung-Lu / R-MAT, job uniform
-    over (1,2) / (2,3) / (3,4) ((3,4) only where the footprint bound fits the
-    budget, else (2,3)).  Saturated throughput first, then p50/p99 latency at
-    0.5 / 0.7 / 0.9 of it; one-request-at-a-time service as the baseline."""
+def core26_measure(steps: int = 1):
+    """Config-5b: the k-core of R-MAT scale 26, EF 16 (67M vertices, 2.1G CSR
+    entries), generated on the device: build + SND + AND per step."""
     import torch
     from paper_1704_00386_gb300 import graphs as G
-    from paper_1704_00386_gb300 import nd, serve
-    torch.cuda.set_device(0)
-    nd.load(build_if_missing=False)
-    rng = np.random.Generator(np.random.PCG64(5))
-    budget = 64 << 30
-    edges = np.exp(rng.uniform(np.log(1e3), np.log(2e6), size=args.requests))
-    reqs = []
-    for i, e in enumerate(edges):
-        fam = int(rng.integers(0, 3))
-        n = max(16, int(e * 2 / 8))
-        sd = 5_000_000 + i
-        if fam == 0:
-            a, b = G.erdos_renyi(n, 8.0 / (n - 1), seed=sd)
-        elif fam == 1:
-            a, b = G.chung_lu(n, 2.2, 8.0, seed=sd)
-        else:
-            _, a, b = G.rmat(max(1, int(np.ceil(np.log2(n)))), 8, seed=sd, n_limit=n)
-        rp, col = G.to_csr(n, a, b)
-        r, s_ = [(1, 2), (2, 3), (3, 4)][int(rng.integers(0, 3))]
-        if (r, s_) == (3, 4) and serve.footprint_bytes(rp, col, 3) > budget // 8:
-            r, s_ = 2, 3
-        reqs.append((rp, col, r, s_))
+    from paper_1704_00386_gb300 import nd
+    t0 = time.perf_counter()
+    w = G.workload("rmat_core_s26_ef16")
+    rp, col = w["row_ptr"].cuda(), w["col"].cuda()
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
 
-    def run_stream(arrivals, workers, batching=True):
-        srv = serve.Server(budget_bytes=budget, workers=workers, batch_bytes=(1 << 30) if batching else 1,
-                           max_batch=64 if batching else 1)
-        hs = []
+    def one():
+        inc = nd.build_incidence(rp, col, 1, 2)
+        t_s, it_s = inc.snd()
+        _, ev = inc.last_passes()
+        t_a, it_a, ev_a = inc.and_(notify=True)
+        inc.free()
+        return int(ev.sum()) + ev_a, it_s, it_a, t_s, t_a
+
+    one()                                         # warm-up
+    ms, res = [], None
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = one()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    ev, it_s, it_a, t_s, t_a = res
+    out = {"workload": w["name"], "recipe": w["recipe"], "n": int(rp.numel() - 1), "nnz": int(col.numel()),
+           "generation_s": gen_s, "ms_per_step": statistics.median(ms), "steps": steps,
+           "updates_per_s": ev / (statistics.median(ms) / 1e3), "snd_iters": it_s, "and_iters": it_a,
+           "snd_equals_and": bool(torch.equal(t_s, t_a))}
+    del rp, col, w
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_extras(args, dev):
+    """After the timed region: one scale-26 k-core step, a 256-graph batch
+    (autotuned) against one graph per launch, and a 64-request stream at half
+    of its saturated rate.  Each is reported, none changes the headline."""
+    import torch
+    extra = {}
+    for key, fn in (("rmat_core_s26_ef16", lambda: core26_measure(1)),
+                    ("batch_256", lambda: batch_measure(256, steps=1, autotune=True)),
+                    ("serve_64", lambda: serve_measure(serve_requests(64), loads=(0.5,)))):
         t0 = time.perf_counter()
-        for (rp, col, r, s_), at in zip(reqs, arrivals):
-            d = t0 + at - time.perf_counter()
-            if d > 0:
-                time.sleep(d)
-            hs.append(srv.submit(rp, col, r, s_, "and"))
-        srv.close()
-        span = max(h.finish for h in hs) - t0
-        return hs, span
-
-    zero = np.zeros(len(reqs))
-    run_stream(zero[:8], 4)                               # warm-up
-    hs, span = run_stream(zero, 4)
-    sat = len(reqs) / span
-    base_hs, base_span = run_stream(zero, 1, batching=False)
-    alone = {i: h.result for i, h in enumerate(base_hs)}
-    same = all(np.array_equal(h.result, alone[i]) for i, h in enumerate(hs))
-    out = {"metric": METRIC, "mode": "serve", "requests": len(reqs),
-           "edges_total": int(sum(int(rp[-1]) // 2 for rp, _, _, _ in reqs)),
-           "saturated_requests_per_s": sat, "one_at_a_time_requests_per_s": len(reqs) / base_span,
-           "saturated_latency": serve.latency_stats(hs), "results_identical_to_one_at_a_time": bool(same),
-           "load": {}}
-    for frac in (0.5, 0.7, 0.9):
-        arr = serve.poisson_arrivals(frac * sat, len(reqs), seed=int(frac * 100))
-        hs2, span2 = run_stream(arr, 4)
-        same2 = all(np.array_equal(h.result, alone[i]) for i, h in enumerate(hs2))
-        out["load"][str(frac)] = {"rate_per_s": frac * sat, "throughput_per_s": len(reqs) / span2,
-                                  "latency": serve.latency_stats(hs2), "results_identical": bool(same2),
-                                  "batched_requests": int(sum(h.batched_with > 1 for h in hs2))}
-    print(json.dumps(out), flush=True)
-    return 0
+        try:
+            extra[key] = fn()
+        except Exception as e:  # reported, never fatal to the headline
+            extra[key] = {"error": f"{type(e).__name__}: {e}"}
+        extra[key]["wall_s"] = time.perf_counter() - t0
+        torch.cuda.synchronize(dev)
+    return extra
 
 
 def run_otf(args):

@@ -53,7 +53,9 @@ typedef enum {
     ND_E_CUDA = 4,            /* a CUDA runtime call failed (message in nd_last_error) */
     ND_E_NOT_CONVERGED = 5,   /* the iteration cap was reached; tau is still a valid upper bound */
     ND_E_TIMEOUT = 6,         /* a host-side wait exceeded its limit */
-    ND_E_TOO_LARGE = 7        /* more r-cliques than the 32-bit id space, or a size limit */
+    ND_E_TOO_LARGE = 7,       /* more r-cliques than the 32-bit id space, or a size limit */
+    ND_E_BUSY = 8             /* another call is using the same handle (calls on one handle
+                                 must not overlap; the refused call did nothing) */
 } nd_status;
 
 typedef enum { ND_SND = 0, ND_AND = 1, ND_AND_NN = 2 } nd_mode;
@@ -70,6 +72,24 @@ typedef struct {
 } nd_csr;
 
 typedef struct nd_incidence nd_incidence; /* opaque; owned by the library */
+
+/* Edge list -> the simple undirected graph of Section 2, as the CSR that
+ * nd_build_incidence takes.  src[m], dst[m] (int64; host or device per
+ * on_device) are arbitrary vertex pairs in [0, n): each pair (a, b) with
+ * a != b is the undirected edge {a, b}; self-loops (a == b) are dropped and
+ * a pair given more than once, in either direction, is one edge.
+ * Output (caller-owned, the same kind of memory as the input):
+ *   row_ptr_out[n+1] int64; col_out[col_capacity] int32, where 2m always
+ *   suffices; *nnz_out = entries written = 2|E|.  Every row is strictly
+ *   increasing and the adjacency is symmetric.
+ * An id outside [0, n) gives ND_E_INVAL.  If col_capacity is below the
+ * result's size, the call returns ND_E_INVAL with the size needed in
+ * *nnz_out and writes no output.  Runs on this GPU (a stable radix sort of
+ * the 2m directed pairs); temporary device memory is about 40 B per pair
+ * (plus 16 B per pair for host input).  Synchronises `stream`. */
+nd_status nd_normalize(const int64_t* src, const int64_t* dst, int64_t m, int64_t n, int on_device,
+                       int64_t* row_ptr_out, int32_t* col_out, int64_t col_capacity, int64_t* nnz_out,
+                       void* stream);
 
 /* Build the r-clique -> s-clique incidence of g (Def. 1) on this GPU:
  * degree split and canonical edge ids, then triangle enumeration for r = 2
@@ -242,17 +262,44 @@ nd_status nd_incidence_bytes(const nd_incidence* inc, int64_t* bytes);
  *   core_out[n]: device pointer; receives the core numbers.
  *   n must be at most 1,048,576; larger graphs get ND_E_TOO_LARGE.
  *   max_iters caps the passes as for nd_snd; *iters_out (may be NULL) =
- *   passes that changed a value.  Synchronises `stream`.
+ *   passes that changed a value.  Synchronises `stream` before returning.
  * Scratch: one file-scope device array of 4 MiB + 1 KiB (a previous-pass
- * tau buffer and per-pass counters).  Every GPU that loads the library
- * holds it until the process exits.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  All calls share the array and it keeps the
- * last call's contents (the counters are cleared at the start of each
- * call): calls that overlap on the GPU -- on two streams, or from two
- * threads -- race and must be serialised by the caller. */
+ * tau buffer and per-pass counters).
+ * Set-up: CUDA loads this entry point's device code and array onto a GPU
+ * lazily, and that load takes device memory.  The first call on a device
+ * (with that device current) does the load and looks up the array's device
+ * address (cudaGetSymbolAddress); a call with n = 0 does only that (row_ptr,
+ * col and core_out may be NULL) and returns its status.  A caller whose
+ * allocator reserves the device's memory makes that n = 0 call first,
+ * before the reservation, and before any stream capture.  A failed set-up
+ * is not remembered: the next call tries again.  After it the device holds
+ * the array until the process exits, and no call allocates device memory.
+ * All calls share the array and it keeps the last call's contents (the
+ * counters are cleared at the start of each call): calls that overlap on
+ * the GPU -- on two streams, or from two threads -- race and must be
+ * serialised by the caller. */
 nd_status nd_core_snd_noalloc(const int64_t* row_ptr, const int32_t* col, int64_t n, int64_t nnz,
                               int32_t* core_out, int32_t max_iters, int32_t* iters_out, void* stream);
+
+/* Limit of every host-side wait (default 600 s; process-wide).  A call that
+ * waits for its stream polls it and returns ND_E_TIMEOUT once the limit has
+ * passed; the work it enqueued keeps running, and the handle is usable again
+ * once the stream has drained.  seconds must be > 0. */
+nd_status nd_set_wait_limit(double seconds);
+
+/* Limit on the device memory one handle may hold (nd_incidence_bytes;
+ * process-wide; 0 = none, the default).  A build or iteration call that
+ * would take a handle past it returns ND_E_NOMEM; a failed build frees what
+ * it took.  Lets a server that admits work by memory footprint enforce its
+ * budget per request.  bytes must be >= 0. */
+nd_status nd_set_handle_memory_limit(int64_t bytes);
+
+/* Calls on one handle must not overlap (a handle holds one iteration state).
+ * Every call that uses a handle's state (nd_snd, nd_and, nd_iterate_k,
+ * nd_and_partial, nd_and_until, nd_autotune, nd_last_passes) marks the
+ * handle in use while it runs; a second such call that comes in meanwhile,
+ * from another thread, returns ND_E_BUSY at once and does nothing.  Calls on
+ * different handles may run concurrently on different streams. */
 
 void nd_free(nd_incidence* inc);
 const char* nd_strerror(nd_status st);

@@ -5,7 +5,10 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 its Python binding) never imports it, and it never imports them.
 
 The arithmetic lives in ``oracle.c`` (plain single-threaded C, compiled here
-with gcc); this module only marshals numpy arrays through ctypes.  The
+with gcc); this module only marshals numpy arrays through ctypes.
+``snd_mt.c`` is the same SND (Alg. 2, Def. 4, Def. 3 by sorting) with its
+loops split over OpenMP threads, used to time the CPU baseline on all host
+cores; a CPU test pins it pass by pass against the single-threaded one.  The
 brute-force search of Lemma 1 is written in Python because it only runs on
 graphs with a handful of r-cliques.
 
@@ -27,20 +30,31 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB_PATH = os.path.join(_LIBDIR, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.c")
+_MT_PATH = os.path.join(_LIBDIR, "liboracle_mt.so")
+_MT_SRC = os.path.join(_HERE, "snd_mt.c")
 _lock = threading.Lock()
 _lib = None
+_mt = None
 
 ERRORS = {0: "ok", -1: "invalid input", -2: "out of memory",
           -3: "an update raised tau (Thm. 1 violated)", -4: "unsupported (r,s)"}
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into a shared library with gcc (plain -O2)."""
+    """Compile oracle.c into a shared library with gcc (plain -O2), and
+    snd_mt.c into a second one with OpenMP (without it, if the compiler has
+    none: the routine then runs on one thread and says so)."""
     os.makedirs(_LIBDIR, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
+    if force or not os.path.exists(_MT_PATH) or os.path.getmtime(_MT_PATH) < os.path.getmtime(_MT_SRC):
+        tmp = _MT_PATH + f".{os.getpid()}.tmp"
+        base = ["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _MT_SRC]
+        if subprocess.call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base)
+        os.replace(tmp, _MT_PATH)
     return _LIB_PATH
 
 
@@ -208,6 +222,67 @@ class Graph:
         if k < 0:
             _check(k)
         return k, lv
+
+
+def _load_mt():
+    global _mt
+    with _lock:
+        if _mt is not None:
+            return _mt
+        build()
+        lib = ctypes.CDLL(_MT_PATH)
+        i64, i32, vp, ci = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int
+        lib.omt_create.argtypes = [i64, vp, vp, ci, ci, ctypes.POINTER(vp)]
+        lib.omt_free.argtypes = [vp]
+        lib.omt_free.restype = None
+        lib.omt_num_r.argtypes = [vp]
+        lib.omt_num_r.restype = i64
+        lib.omt_num_incidences.argtypes = [vp]
+        lib.omt_num_incidences.restype = i64
+        lib.omt_snd.argtypes = [vp, vp, ci, i32, ci, vp, vp, vp]
+        lib.omt_max_threads.restype = ci
+        _mt = lib
+        return lib
+
+
+class ParallelSND:
+    """SND (Alg. 2) on all host cores, for timing the CPU baseline: the
+    oracle's arithmetic (Def. 4, H by sorting) with the loop over r-clique
+    split over OpenMP threads, and its own incidence construction (Def. 1),
+    also threaded.  (1,2) and (2,3).  The graph is validated by the
+    single-threaded oracle first."""
+
+    def __init__(self, row_ptr, col, r: int, threads: int = 0, validate: bool = True):
+        self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        self.col = np.ascontiguousarray(col, dtype=np.int32)
+        if validate:
+            Graph(self.row_ptr, self.col, r, r + 1, incidence=False)  # raises on a malformed graph
+        lib = _load_mt()
+        self._lib = lib
+        self.threads = int(threads) if threads > 0 else int(lib.omt_max_threads())
+        h = ctypes.c_void_p()
+        _check(lib.omt_create(self.row_ptr.size - 1, _ptr(self.row_ptr), _ptr(self.col), r, self.threads,
+                              ctypes.byref(h)))
+        self._h = h
+        self.r = r
+        self.num_r = int(lib.omt_num_r(h))
+        self.num_incidences = int(lib.omt_num_incidences(h))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.omt_free(h)
+            self._h = None
+
+    def snd(self, tau=None, max_sweeps: int = 1 << 30):
+        """At most max_sweeps SND passes from d_s (or from tau).
+        Returns (tau, sweeps, updating_sweeps, evaluations), as Graph.snd."""
+        t = np.zeros(self.num_r, dtype=np.int32) if tau is None else \
+            np.ascontiguousarray(np.asarray(tau, dtype=np.int32).copy())
+        sw, up, ev = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(self._lib.omt_snd(self._h, _ptr(t), int(tau is None), int(max_sweeps), self.threads,
+                                 ctypes.byref(sw), ctypes.byref(up), ctypes.byref(ev)))
+        return t, sw.value, up.value, ev.value
 
 
 def kendall_tau_b(x, y):

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libnd.so")
-SOURCES = ["nd_api.cu", "nd_build.cu", "nd_hindex.cu", "nd_scan.cu", "nd_noalloc.cu", "nd_eval.cu"]
+SOURCES = ["nd_api.cu", "nd_build.cu", "nd_hindex.cu", "nd_scan.cu", "nd_noalloc.cu", "nd_eval.cu", "nd_normalize.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

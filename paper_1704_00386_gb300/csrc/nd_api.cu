@@ -6,6 +6,7 @@
 #include <map>
 #include <tuple>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -84,8 +85,20 @@ nd_prof_scope::~nd_prof_scope() {
 // ---------------------------------------------------------------------------
 // device memory (stream-ordered; the pool keeps freed blocks for reuse)
 // ---------------------------------------------------------------------------
+// per-handle device memory limit (nd_set_handle_memory_limit; 0 = none)
+static std::atomic<int64_t> g_handle_limit{0};
+
 nd_status nd_alloc(void** p, size_t bytes, cudaStream_t st, nd_incidence* owner) {
     if (bytes == 0) bytes = 16;
+    const int64_t limit = g_handle_limit.load();
+    if (owner && limit > 0 && owner->bytes + (int64_t)bytes > limit) {
+        *p = nullptr;
+        char buf[200];
+        snprintf(buf, sizeof(buf), "the handle would hold %lld bytes of device memory, above its limit of %lld",
+                 (long long)(owner->bytes + (int64_t)bytes), (long long)limit);
+        nd_set_error(buf);
+        return ND_E_NOMEM;
+    }
     cudaError_t e = cudaMallocAsync(p, bytes, st);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -116,7 +129,10 @@ static void keep_pool(int dev) {
 }
 
 // bounded wait: poll the stream instead of blocking forever
-nd_status nd_wait(cudaStream_t st, double seconds) {
+static std::atomic<double> g_wait_limit{600.0};
+
+nd_status nd_wait(cudaStream_t st) {
+    const double seconds = g_wait_limit.load();
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
         cudaError_t e = cudaStreamQuery(st);
@@ -124,15 +140,13 @@ nd_status nd_wait(cudaStream_t st, double seconds) {
         if (e != cudaErrorNotReady) return nd_cuda_fail(e, "cudaStreamQuery", __FILE__, __LINE__);
         if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > seconds) {
             char buf[96];
-            snprintf(buf, sizeof(buf), "stream did not finish within %.0f s", seconds);
+            snprintf(buf, sizeof(buf), "stream did not finish within %g s", seconds);
             nd_set_error(buf);
             return ND_E_TIMEOUT;
         }
         std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
 }
-
-static nd_status host_wait(cudaStream_t st) { return nd_wait(st, 1800.0); }
 
 // ---------------------------------------------------------------------------
 // C ABI
@@ -150,12 +164,25 @@ const char* nd_strerror(nd_status st) {
         case ND_E_CUDA: return "CUDA runtime error";
         case ND_E_NOT_CONVERGED: return "iteration cap reached before convergence";
         case ND_E_TIMEOUT: return "timed out";
-        case ND_E_TOO_LARGE: return "problem exceeds the 32-bit id space";
+        case ND_E_TOO_LARGE: return "problem exceeds the 32-bit id space or a size limit";
+        case ND_E_BUSY: return "another call is using this handle";
     }
     return "unknown status";
 }
 
 const char* nd_last_error(void) { return g_last_error.c_str(); }
+
+nd_status nd_set_wait_limit(double seconds) {
+    if (!(seconds > 0.0)) { nd_set_error("the wait limit must be > 0 seconds"); return ND_E_INVAL; }
+    g_wait_limit.store(seconds);
+    return ND_OK;
+}
+
+nd_status nd_set_handle_memory_limit(int64_t bytes) {
+    if (bytes < 0) { nd_set_error("negative memory limit"); return ND_E_INVAL; }
+    g_handle_limit.store(bytes);
+    return ND_OK;
+}
 
 void nd_free(nd_incidence* h) {
     if (!h) return;
@@ -267,7 +294,7 @@ static nd_status build_common(const nd_csr* g, int r, int s, cudaStream_t st, nd
     }
     if (rc == ND_OK) apply_tuned(h, dev);
     if (rc == ND_OK) rc = nd_build_buckets(h, st);
-    if (rc == ND_OK) rc = host_wait(st);
+    if (rc == ND_OK) rc = nd_wait(st);
     if (rc != ND_OK) {
         std::string keep = g_last_error;
         cudaStreamSynchronize(st);
@@ -389,7 +416,7 @@ static nd_status deliver(const int32_t* src_dev, int64_t count, int32_t* dst, in
         return ND_OK;
     }
     ND_CUDA(cudaMemcpyAsync(dst, src_dev, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, st));
-    return host_wait(st);
+    return nd_wait(st);
 }
 
 nd_status nd_r_cliques(const nd_incidence* h, int32_t* out, int on_device, void* stream) {
@@ -422,7 +449,7 @@ nd_status nd_s_degree(const nd_incidence* h, int32_t* out, int on_device, void* 
     }
     if (on_device) {
         ND_CUDA(cudaMemcpyAsync(out, res, sizeof(int32_t) * h->num_r, cudaMemcpyDeviceToDevice, st));
-        return host_wait(st);  // the temporaries are released on return
+        return nd_wait(st);  // the temporaries are released on return
     }
     return deliver(res, h->num_r, out, 0, st);
 }
@@ -466,7 +493,7 @@ static nd_status run_and_deliver(nd_incidence* h, int mode, int32_t max_passes, 
     }
     s = deliver(result, h->num_r, tau_out, on_device, st);
     if (s != ND_OK) return s;
-    if (on_device) ND_TRY(host_wait(st));
+    if (on_device) ND_TRY(nd_wait(st));
     if (iters_out) *iters_out = updating;
     if (evals_out) *evals_out = evals;
     if (require_convergence && !converged && !(opts && opts->stopped)) {
@@ -478,12 +505,16 @@ static nd_status run_and_deliver(nd_incidence* h, int mode, int32_t max_passes, 
 
 nd_status nd_snd(nd_incidence* h, int32_t* tau_out, int on_device, int32_t max_iters,
                  int32_t* iters_out, void* stream) {
+    if (!h) { nd_set_error("handle is NULL"); return ND_E_INVAL; }
+    ND_CLAIM(h);
     return run_and_deliver(h, ND_SND, max_iters, nullptr, 0, tau_out, on_device, iters_out, nullptr, true,
                            (cudaStream_t)stream);
 }
 
 nd_status nd_and(nd_incidence* h, int32_t* tau_out, int on_device, int notify, int32_t max_iters,
                  int32_t* iters_out, int64_t* evals_out, void* stream) {
+    if (!h) { nd_set_error("handle is NULL"); return ND_E_INVAL; }
+    ND_CLAIM(h);
     return run_and_deliver(h, notify ? ND_AND : ND_AND_NN, max_iters, nullptr, 0, tau_out, on_device,
                            iters_out, evals_out, true, (cudaStream_t)stream);
 }
@@ -491,6 +522,8 @@ nd_status nd_and(nd_incidence* h, int32_t* tau_out, int on_device, int notify, i
 nd_status nd_iterate_k(nd_incidence* h, int mode, int32_t k, int32_t* tau_inout, int tau_init_given,
                        int on_device, int32_t* updating_out, void* stream) {
     if (k < 0) { nd_set_error("negative k"); return ND_E_INVAL; }
+    if (!h) { nd_set_error("handle is NULL"); return ND_E_INVAL; }
+    ND_CLAIM(h);
     return run_and_deliver(h, mode, k, tau_init_given ? tau_inout : nullptr, on_device, tau_inout,
                            on_device, updating_out, nullptr, false, (cudaStream_t)stream);
 }
@@ -500,6 +533,7 @@ nd_status nd_and_partial(nd_incidence* h, const uint32_t* members, int64_t count
                          void* stream) {
     if (!h) { nd_set_error("handle is NULL"); return ND_E_INVAL; }
     if (count < 0 || (count > 0 && !members)) { nd_set_error("bad member list"); return ND_E_INVAL; }
+    ND_CLAIM(h);
     cudaStream_t st = (cudaStream_t)stream;
     h->last_stream = st;
     const int64_t words = (h->num_r + 31) / 32;
@@ -518,7 +552,7 @@ nd_status nd_and_partial(nd_incidence* h, const uint32_t* members, int64_t count
     ND_TRY(nd_member_mask(ids, count, h->num_r, mask, derr, st, h->to_new));
     int herr = 0;
     ND_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st));
-    ND_CUDA(cudaStreamSynchronize(st));
+    ND_TRY(nd_wait(st));
     if (herr) { nd_set_error("a member id is not an r-clique id"); return ND_E_INVAL; }
     nd_run_opts opts;
     opts.members = mask;
@@ -530,6 +564,7 @@ nd_status nd_and_until(nd_incidence* h, double active_ratio, int32_t* tau_out, i
                        int32_t* iters_out, int64_t* evals_out, int* stopped_out, void* stream) {
     if (!h) { nd_set_error("handle is NULL"); return ND_E_INVAL; }
     if (!(active_ratio >= 0.0 && active_ratio <= 1.0)) { nd_set_error("active_ratio must be in [0,1]"); return ND_E_INVAL; }
+    ND_CLAIM(h);
     nd_run_opts opts;
     opts.stop_active = active_ratio;
     nd_status rc = run_and_deliver(h, ND_AND, max_iters, nullptr, 0, tau_out, on_device, iters_out, evals_out,
@@ -557,7 +592,7 @@ nd_status nd_count_equal(const int32_t* a, const int32_t* b, int64_t n, int on_d
     ND_TRY(nd_count_equal_dev(da, db, n, dout, st));
     unsigned long long hv = 0;
     ND_CUDA(cudaMemcpyAsync(&hv, dout, sizeof(hv), cudaMemcpyDeviceToHost, st));
-    ND_CUDA(cudaStreamSynchronize(st));
+    ND_TRY(nd_wait(st));
     *equal_out = (int64_t)hv;
     return ND_OK;
 }
@@ -574,7 +609,7 @@ nd_status nd_truss_classic(const int32_t* kappa3, int64_t num_edges, int32_t* ou
     ND_CUDA(cudaMemcpyAsync(din, kappa3, sizeof(int32_t) * num_edges, cudaMemcpyHostToDevice, st));
     ND_TRY(nd_classic_truss(din, num_edges, dout, st));
     ND_CUDA(cudaMemcpyAsync(out, dout, sizeof(int32_t) * num_edges, cudaMemcpyDeviceToHost, st));
-    ND_CUDA(cudaStreamSynchronize(st));
+    ND_TRY(nd_wait(st));
     return ND_OK;
 }
 
@@ -601,6 +636,7 @@ nd_status nd_kendall_tau_b(const int32_t* x, const int32_t* y, int64_t n, int on
 nd_status nd_autotune(nd_incidence* h, int32_t passes, void* stream, int32_t* thr_out, double* best_ms_out) {
     if (!h) { nd_set_error("handle is NULL"); return ND_E_INVAL; }
     if (passes < 1) passes = 2;
+    ND_CLAIM(h);
     cudaStream_t st = (cudaStream_t)stream;
     h->last_stream = st;
     int dev = 0;
@@ -651,6 +687,7 @@ nd_status nd_autotune(nd_incidence* h, int32_t passes, void* stream, int32_t* th
 nd_status nd_last_passes(const nd_incidence* h, int64_t* changed, int64_t* evaluated, int64_t* incidences,
                          int32_t cap, int32_t* passes) {
     if (!h || !passes) { nd_set_error("NULL argument"); return ND_E_INVAL; }
+    ND_CLAIM(const_cast<nd_incidence*>(h));
     const int32_t n = (int32_t)h->last_changed.size();
     *passes = n;
     for (int32_t i = 0; i < n && i < cap; ++i) {

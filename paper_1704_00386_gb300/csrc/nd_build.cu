@@ -902,13 +902,13 @@ int grid_cap(const nd_incidence* h) { return (h->sm_count > 0 ? h->sm_count : 15
 
 nd_status read_flag(int* dflag, int* hval, cudaStream_t st) {
     ND_CUDA(cudaMemcpyAsync(hval, dflag, sizeof(int), cudaMemcpyDeviceToHost, st));
-    ND_CUDA(cudaStreamSynchronize(st));
+    ND_TRY(nd_wait(st));
     return ND_OK;
 }
 
 nd_status read_i64(const int64_t* d, int64_t* hv, cudaStream_t st) {
     ND_CUDA(cudaMemcpyAsync(hv, d, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    ND_CUDA(cudaStreamSynchronize(st));
+    ND_TRY(nd_wait(st));
     return ND_OK;
 }
 
@@ -933,7 +933,7 @@ static nd_status find_long_rows(nd_incidence* h, cudaStream_t st) {
     ND_CUDA(cudaGetLastError());
     unsigned long long c = 0;
     ND_CUDA(cudaMemcpyAsync(&c, cnt.p, sizeof(c), cudaMemcpyDeviceToHost, st));
-    ND_TRY(nd_wait(st, 600.0));
+    ND_TRY(nd_wait(st));
     if (c > (unsigned long long)cap) {  // overlapping rows: not an offset array
         nd_set_error("row_ptr is not a valid offset array");
         return ND_E_INVAL;
@@ -941,11 +941,11 @@ static nd_status find_long_rows(nd_incidence* h, cudaStream_t st) {
     if (c == 0) return ND_OK;
     std::vector<int64_t> hl(c), off(c + 1, 0);
     ND_CUDA(cudaMemcpyAsync(hl.data(), len.p, sizeof(int64_t) * c, cudaMemcpyDeviceToHost, st));
-    ND_TRY(nd_wait(st, 600.0));
+    ND_TRY(nd_wait(st));
     for (unsigned long long i = 0; i < c; ++i) off[i + 1] = off[i] + (hl[i] + kLongSeg - 1) / kLongSeg;
     ND_TRY(nd_alloc((void**)&h->long_seg, sizeof(int64_t) * (c + 1), st, h));
     ND_CUDA(cudaMemcpyAsync(h->long_seg, off.data(), sizeof(int64_t) * (c + 1), cudaMemcpyHostToDevice, st));
-    ND_TRY(nd_wait(st, 600.0));  // off is a host temporary
+    ND_TRY(nd_wait(st));  // off is a host temporary
     h->long_count = (int64_t)c;
     h->long_segs = off[c];
     return ND_OK;
@@ -1167,7 +1167,7 @@ static nd_status sort_tri_rows(nd_incidence* h, cudaStream_t st) {
     }
     unsigned long long hc[2] = {0, 0};
     ND_CUDA(cudaMemcpyAsync(hc, over_ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
-    ND_TRY(nd_wait(st, 600.0));
+    ND_TRY(nd_wait(st));
     if (hc[0] > 0) {
         // rows whose shorter adjacency list needs more than kRankWords words
         const int warps = 64;
@@ -1387,7 +1387,7 @@ nd_status nd_build_buckets(nd_incidence* h, cudaStream_t st) {
     h->bucket_lo[ND_NB] = lo;
     unsigned long long hs[ND_NB] = {0, 0, 0, 0};
     ND_CUDA(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, st));
-    ND_CUDA(cudaStreamSynchronize(st));
+    ND_TRY(nd_wait(st));
     for (int b = 0; b < ND_NB; ++b) h->bucket_inc[b] = (int64_t)hs[b];
     h->num_zero = N - lo;
     return ND_OK;
@@ -1450,6 +1450,6 @@ nd_status nd_batch_offsets(const nd_incidence* h, const int64_t* vertex_off /* c
         res = didx;
     }
     ND_CUDA(cudaMemcpyAsync(r_off, res, sizeof(int64_t) * (count + 1), cudaMemcpyDeviceToHost, st));
-    ND_CUDA(cudaStreamSynchronize(st));
+    ND_TRY(nd_wait(st));
     return ND_OK;
 }

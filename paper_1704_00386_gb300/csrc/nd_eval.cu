@@ -146,7 +146,7 @@ nd_status nd_kendall_dev(const int32_t* x, const int32_t* y, int64_t n, int sm_c
     }
     int h_mm[4];
     ND_CUDA(cudaMemcpyAsync(h_mm, mm.p, sizeof(h_mm), cudaMemcpyDeviceToHost, st));
-    ND_TRY(nd_wait(st, 600.0));
+    ND_TRY(nd_wait(st));
     const int64_t Vx = (int64_t)h_mm[1] - h_mm[0] + 1, Vy = (int64_t)h_mm[3] - h_mm[2] + 1;
     const int64_t W = Vy + 1;
     if ((double)(Vx + 1) * (double)W > (double)kMaxCells) {
@@ -171,7 +171,7 @@ nd_status nd_kendall_dev(const int32_t* x, const int32_t* y, int64_t n, int sm_c
     }
     unsigned long long h_out[3];
     ND_CUDA(cudaMemcpyAsync(h_out, out.p, sizeof(h_out), cudaMemcpyDeviceToHost, st));
-    ND_TRY(nd_wait(st, 600.0));
+    ND_TRY(nd_wait(st));
     const long long S = (long long)h_out[0];
     if (counts_out) {
         counts_out[0] = S;

@@ -1120,7 +1120,7 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
             ND_CUDA(cudaMemcpyAsync(h->h_counters + ND_SLOT * base, h->counters + ND_SLOT * base,
                                     sizeof(unsigned long long) * ND_SLOT * nb, cudaMemcpyDeviceToHost, st));
         }
-        ND_TRY(nd_wait(st, 600.0));
+        ND_TRY(nd_wait(st));
         for (int k = 0; k < nb; ++k) {
             const int32_t p = start + k;
             unsigned long long ch = h->h_counters[ND_SLOT * (base + k)];

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -120,14 +121,40 @@ struct nd_incidence {
     cudaGraphExec_t pass_graph[3][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr},
                                         {nullptr, nullptr, nullptr}};
     bool pass_graph_failed[3][3] = {{false, false, false}, {false, false, false}, {false, false, false}};
+    // set while a call uses the iteration state (nd_claim); a second call
+    // meanwhile gets ND_E_BUSY
+    std::atomic<int> busy{0};
 };
+
+// marks a handle in use for the lifetime of the object; ok == false if
+// another call holds it (the caller then returns ND_E_BUSY)
+struct nd_claim {
+    nd_incidence* h;
+    bool ok;
+    explicit nd_claim(nd_incidence* hh) : h(hh), ok(false) {
+        int expect = 0;
+        ok = h != nullptr && h->busy.compare_exchange_strong(expect, 1);
+    }
+    ~nd_claim() {
+        if (ok) h->busy.store(0);
+    }
+    nd_claim(const nd_claim&) = delete;
+    nd_claim& operator=(const nd_claim&) = delete;
+};
+
+#define ND_CLAIM(handle)                                                      \
+    nd_claim nd_claim_((handle));                                             \
+    if (!nd_claim_.ok) {                                                      \
+        nd_set_error("another call is using this handle");                    \
+        return ND_E_BUSY;                                                     \
+    }
 
 // passes are enqueued in batches of ND_BATCH; the per-pass counters (ND_SLOT
 // u64 each) live in two halves of ND_BATCH slots used by alternate batches
 enum { ND_BATCH = 16, ND_RING = 2 * ND_BATCH, ND_SLOT = 6 };
 
 // wait for a stream with a time limit (ND_E_TIMEOUT past it)
-nd_status nd_wait(cudaStream_t st, double seconds);
+nd_status nd_wait(cudaStream_t st);
 
 // a stream-ordered device temporary, released when it goes out of scope
 // (also on every early error return)

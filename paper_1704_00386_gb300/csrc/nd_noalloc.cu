@@ -7,8 +7,15 @@
 // nd_core_snd_noalloc serves them.  It computes the same core numbers as
 // nd_build_incidence(g, 1, 2) followed by nd_snd, straight from a device
 // CSR, and its only scratch is the file-scope array below (one previous-pass
-// tau buffer and a ring of per-pass counters).  Every GPU that loads this
-// library holds that array until the process exits.
+// tau buffer and a ring of per-pass counters).
+//
+// The array belongs to this file's device code, which CUDA loads onto a GPU
+// lazily (by default): the first call on a device that looks up the array,
+// or launches one of the kernels below, loads the code and creates the array
+// there, and that step itself takes device memory.  A call with n = 0 does
+// exactly that and nothing else, so a caller whose allocator reserves the
+// device up front makes that call first.  From then on the device holds the
+// array until the process exits, and no call allocates.
 #include <mutex>
 
 #include "nd_internal.cuh"
@@ -27,10 +34,10 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // Per-device address of g_scratch as seen by kernels.  In host code the name
 // g_scratch is only a host-side stand-in, so the address must be fetched
-// with cudaGetSymbolAddress, once per device, with that device current.
-std::once_flag g_once[64];
+// with cudaGetSymbolAddress, once per device, with that device current.  A
+// failed set-up is not remembered: the next call tries again.
+std::mutex g_mu;
 void* g_addr[64];
-cudaError_t g_addr_err[64];
 
 __global__ void k_core_init(int64_t n, int64_t nnz, const int64_t* __restrict__ rp, int32_t* __restrict__ a,
                             int32_t* __restrict__ b, unsigned long long* __restrict__ err) {
@@ -107,15 +114,22 @@ __global__ void __launch_bounds__(kThreads) k_core_pass(int64_t n, int64_t nnz, 
     }
 }
 
+// Set-up on the current device, once: the array's address, and the two
+// kernels loaded (cudaFuncGetAttributes loads a lazily loaded kernel), so
+// that no later call loads code or data onto the device.
 nd_status scratch_for_current_device(unsigned char** out) {
     int dev = 0;
     ND_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) { nd_set_error("device ordinal out of range"); return ND_E_INVAL; }
-    std::call_once(g_once[dev], [dev]() {
-        g_addr_err[dev] = cudaGetSymbolAddress(&g_addr[dev], g_scratch);
-    });
-    if (g_addr_err[dev] != cudaSuccess)
-        return nd_cuda_fail(g_addr_err[dev], "cudaGetSymbolAddress(g_scratch)", __FILE__, __LINE__);
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr[dev]) {
+        void* addr = nullptr;
+        ND_CUDA(cudaGetSymbolAddress(&addr, g_scratch));
+        cudaFuncAttributes fa;
+        ND_CUDA(cudaFuncGetAttributes(&fa, k_core_init));
+        ND_CUDA(cudaFuncGetAttributes(&fa, k_core_pass));
+        g_addr[dev] = addr;
+    }
     *out = static_cast<unsigned char*>(g_addr[dev]);
     return ND_OK;
 }
@@ -131,17 +145,17 @@ extern "C" nd_status nd_core_snd_noalloc(const int64_t* row_ptr, const int32_t* 
         return ND_E_TOO_LARGE;
     }
     if (iters_out) *iters_out = 0;
+    unsigned char* scratch = nullptr;
+    ND_TRY(scratch_for_current_device(&scratch));  // the set-up; all a call with n = 0 does
     if (n == 0) return ND_OK;
     if (!row_ptr || !core_out || (nnz > 0 && !col)) { nd_set_error("NULL pointer"); return ND_E_INVAL; }
     cudaStream_t st = (cudaStream_t)stream;
-    unsigned char* scratch = nullptr;
-    ND_TRY(scratch_for_current_device(&scratch));
     int32_t* tprev = reinterpret_cast<int32_t*>(scratch);
     unsigned long long* ring = reinterpret_cast<unsigned long long*>(scratch + kTauBytes);
     int sms = 152;
     int dev = 0;
     ND_CUDA(cudaGetDevice(&dev));
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    ND_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int grid = nd_blocks_for(n * 32, kThreads, sms * 8);
     // the array keeps the previous call's contents: clear every counter first
     ND_CUDA(cudaMemsetAsync(ring, 0, sizeof(unsigned long long) * 2 * kRing, st));
@@ -168,7 +182,7 @@ extern "C" nd_status nd_core_snd_noalloc(const int64_t* row_ptr, const int32_t* 
         unsigned long long host[2 * kBatch];
         ND_CUDA(cudaMemcpyAsync(host, ring + 2 * slot0, sizeof(unsigned long long) * 2 * nb,
                                 cudaMemcpyDeviceToHost, st));
-        ND_CUDA(cudaStreamSynchronize(st));
+        ND_TRY(nd_wait(st));
         for (int k = 0; k < nb; ++k) {
             if (host[2 * k + 1]) bad = true;
             newest = ((start + k) & 1) ^ 1;
@@ -180,11 +194,11 @@ extern "C" nd_status nd_core_snd_noalloc(const int64_t* row_ptr, const int32_t* 
     // the error flag of the initialisation lives in slot 0
     unsigned long long init_bad = 0;
     ND_CUDA(cudaMemcpyAsync(&init_bad, ring + 1, sizeof(init_bad), cudaMemcpyDeviceToHost, st));
-    ND_CUDA(cudaStreamSynchronize(st));
+    ND_TRY(nd_wait(st));
     if (bad || init_bad) { nd_set_error("row_ptr / col out of range"); return ND_E_INVAL; }
     if (pass > 0 && buf[newest] != core_out)
         ND_CUDA(cudaMemcpyAsync(core_out, buf[newest], sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
-    ND_CUDA(cudaStreamSynchronize(st));
+    ND_TRY(nd_wait(st));
     if (iters_out) *iters_out = updating;
     if (!done) { nd_set_error("iteration cap reached before a pass without change"); return ND_E_NOT_CONVERGED; }
     return ND_OK;

@@ -20,14 +20,15 @@ import numpy as np
 from . import _build
 
 ND_OK, ND_E_INVAL, ND_E_UNSUPPORTED_RS, ND_E_NOMEM, ND_E_CUDA, ND_E_NOT_CONVERGED, \
-    ND_E_TIMEOUT, ND_E_TOO_LARGE = range(8)
+    ND_E_TIMEOUT, ND_E_TOO_LARGE, ND_E_BUSY = range(9)
 ND_SND, ND_AND, ND_AND_NN = 0, 1, 2
 MODES = {"snd": ND_SND, "and": ND_AND, "and_nn": ND_AND_NN}
 
 SYMBOLS = ["nd_build_incidence", "nd_build_incidence_ex", "nd_build_incidence_batch", "nd_incidence_info", "nd_r_cliques", "nd_s_degree", "nd_snd",
            "nd_and", "nd_iterate_k", "nd_truss_classic", "nd_prof_enable", "nd_prof_read",
            "nd_last_passes", "nd_autotune", "nd_and_partial", "nd_and_until", "nd_count_equal", "nd_kendall_tau_b", "nd_incidence_bytes", "nd_free", "nd_strerror", "nd_last_error",
-           "nd_abi_version", "nd_core_snd_noalloc"]
+           "nd_abi_version", "nd_core_snd_noalloc", "nd_normalize", "nd_set_wait_limit",
+           "nd_set_handle_memory_limit"]
 
 _lock = threading.Lock()
 _lib = None
@@ -82,6 +83,9 @@ def load(build_if_missing: bool = True):
         lib.nd_kendall_tau_b.argtypes = [vp, vp, i64, ci, P(ctypes.c_double), vp, vp]
         lib.nd_incidence_bytes.argtypes = [vp, P(i64)]
         lib.nd_core_snd_noalloc.argtypes = [vp, vp, i64, i64, vp, i32, P(i32), vp]
+        lib.nd_normalize.argtypes = [vp, vp, i64, i64, ci, vp, vp, i64, P(i64), vp]
+        lib.nd_set_wait_limit.argtypes = [ctypes.c_double]
+        lib.nd_set_handle_memory_limit.argtypes = [i64]
         lib.nd_free.argtypes = [vp]
         lib.nd_free.restype = None
         lib.nd_strerror.argtypes = [ci]
@@ -331,6 +335,45 @@ def build_incidence_batch(graphs, r: int, s: int, stream=None):
     _check(lib.nd_build_incidence_batch(arr, count, int(r), int(s), _stream_ptr(stream), ctypes.byref(h),
                                         _ptr(offs)), "nd_build_incidence_batch")
     return Incidence(h, r, s, bool(on_device), device, stream), offs
+
+
+def normalize(src, dst, n: int, stream=None):
+    """nd_normalize: the simple undirected CSR (Section 2) of an arbitrary
+    list of vertex pairs -- self-loops dropped, every pair symmetrised,
+    repeats removed, rows sorted.  src, dst: int64 numpy arrays (host) or
+    CUDA tensors.  Returns (row_ptr int64[n+1], col int32[nnz]) in the same
+    kind of memory."""
+    on_device = _is_torch(src)
+    if on_device != _is_torch(dst):
+        raise ValueError("src and dst must both be host arrays or both CUDA tensors")
+    if on_device:
+        import torch
+        src = src.to(torch.int64).contiguous()
+        dst = dst.to(torch.int64).contiguous()
+        m = src.numel()
+    else:
+        src = np.ascontiguousarray(src, dtype=np.int64).ravel()
+        dst = np.ascontiguousarray(dst, dtype=np.int64).ravel()
+        m = src.size
+    if (dst.numel() if on_device else dst.size) != m:
+        raise ValueError("src and dst differ in length")
+    rp = _empty(int(n) + 1, on_device, src.device if on_device else None, "int64")
+    col = _empty(max(2 * m, 1), on_device, src.device if on_device else None, "int32")
+    nnz = ctypes.c_int64()
+    _check(load().nd_normalize(_ptr(src) if m else None, _ptr(dst) if m else None, m, int(n), int(on_device),
+                               _ptr(rp), _ptr(col), 2 * m, ctypes.byref(nnz), _stream_ptr(stream)),
+           "nd_normalize")
+    return rp, col[:nnz.value]
+
+
+def set_wait_limit(seconds: float):
+    """nd_set_wait_limit: limit of every host-side wait of the library."""
+    _check(load().nd_set_wait_limit(float(seconds)), "nd_set_wait_limit")
+
+
+def set_handle_memory_limit(nbytes: int):
+    """nd_set_handle_memory_limit: device bytes one handle may hold (0 = no limit)."""
+    _check(load().nd_set_handle_memory_limit(int(nbytes)), "nd_set_handle_memory_limit")
 
 
 def core_snd_noalloc(row_ptr, col, out=None, max_iters: int = 1 << 30, stream=None):

@@ -81,10 +81,11 @@ class Server:
     while requests run; close() waits for everything submitted."""
 
     def __init__(self, budget_bytes: int, workers: int = 4, batch_bytes: int = 1 << 30,
-                 max_batch: int = 64, device: int = 0):
+                 max_batch: int = 64, device: int = 0, max_wait_s: float = 1.0):
         import torch
         self.torch = torch
         self.device = device
+        self.max_wait_s = float(max_wait_s)
         self.budget = int(budget_bytes)
         self.batch_bytes = int(batch_bytes)
         self.max_batch = int(max_batch)
@@ -117,6 +118,21 @@ class Server:
             self.cv.notify_all()
         return req
 
+    def cancel(self, req: Request) -> bool:
+        """Withdraw a request that is still waiting.  Returns True if it was
+        removed (its error is then "cancelled" and it counts as done); False
+        if a worker has already taken it (it runs to completion) or it has
+        finished."""
+        with self.cv:
+            if req not in self.queue:
+                return False
+            self.queue.remove(req)
+            req.error = "cancelled"
+            req.finish = time.perf_counter()
+            self.cv.notify_all()
+        req.done.set()
+        return True
+
     def close(self):
         with self.cv:
             self.closing = True
@@ -125,10 +141,19 @@ class Server:
             t.join()
 
     # ------------------------------------------------------------- workers
-    def _take(self) -> list[Request]:
+    def _take(self, now: float | None = None) -> list[Request]:
         """Oldest admissible request, plus every waiting request of the same
         job and mode that fits the batch cap and the budget (FIFO within a
-        job, so no request waits behind a later one of its own job)."""
+        job, so no request waits behind a later one of its own job).
+
+        Aging: once the oldest waiting request has waited longer than
+        max_wait_s without fitting, nothing else is admitted until it fits,
+        so a stream of small requests cannot starve a large one."""
+        if self.queue:
+            oldest = self.queue[0]
+            now = time.perf_counter() if now is None else now
+            if now - oldest.arrival > self.max_wait_s and self.used + oldest.footprint > self.budget:
+                return []
         for i, head in enumerate(self.queue):
             if self.used + head.footprint > self.budget:
                 continue

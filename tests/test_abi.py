@@ -145,8 +145,22 @@ def test_every_call_checks_its_arguments_before_touching_the_gpu():
     # the allocation-free core call: sizes first
     assert lib.nd_core_snd_noalloc(None, None, -1, 0, None, 10, r(i32), None) == INVAL
     assert lib.nd_core_snd_noalloc(None, None, (1 << 20) + 1, 0, None, 10, r(i32), None) == nd.ND_E_TOO_LARGE
-    assert lib.nd_core_snd_noalloc(None, None, 0, 0, None, 10, r(i32), None) == nd.ND_OK  # empty graph
+    # n = 0 is the entry point's set-up call: it needs a device (none here)
+    assert lib.nd_core_snd_noalloc(None, None, 0, 0, None, 10, r(i32), None) == nd.ND_E_CUDA
+    # normalisation: sizes and pointers first
+    nnz = ctypes.c_int64()
+    assert lib.nd_normalize(None, None, -1, 5, 0, None, None, 0, r(nnz), None) == INVAL
+    assert lib.nd_normalize(None, None, 3, 5, 0, None, None, 6, r(nnz), None) == INVAL     # no pairs given
+    assert lib.nd_normalize(None, None, 0, 1 << 31, 0, None, None, 0, r(nnz), None) == nd.ND_E_TOO_LARGE
+    assert lib.nd_normalize(None, None, 2, 0, 0, None, None, 4, r(nnz), None) == INVAL     # edges, no vertices
+    # process-wide limits: values checked, defaults restored
+    assert lib.nd_set_wait_limit(0.0) == INVAL
+    assert lib.nd_set_wait_limit(-1.0) == INVAL
+    assert lib.nd_set_wait_limit(600.0) == nd.ND_OK
+    assert lib.nd_set_handle_memory_limit(-1) == INVAL
+    assert lib.nd_set_handle_memory_limit(0) == nd.ND_OK
     # every status has a message; an unknown one says so
-    for st in (nd.ND_OK, nd.ND_E_INVAL, nd.ND_E_UNSUPPORTED_RS, nd.ND_E_TOO_LARGE):
-        assert nd.strerror(st)
+    for st in range(nd.ND_E_BUSY + 1):
+        assert nd.strerror(st) != "unknown status"
+    assert "handle" in nd.strerror(nd.ND_E_BUSY)
     assert lib.nd_strerror(999) == b"unknown status"

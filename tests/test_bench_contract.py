@@ -21,11 +21,12 @@ def _run(args, timeout):
 
 
 def test_reference_arm_line():
-    d = _run(["--impl", "reference", "--steps", "1", "--warmup", "0"], 600)
+    d = _run(["--impl", "reference", "--workload", "rmat_s14_ef8", "--steps", "2", "--warmup", "1"], 600)
     assert d["impl"] == "reference"
     assert d["value"] > 0 and d["unit"] == "updates/s" and d["higher_is_better"] is True
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["config"]["workload"] == "rmat_s14_ef8" and d["config"]["r_cliques"] > 0
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
@@ -34,7 +35,8 @@ def test_our_arm_line():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    d = _run(["--workload", "rmat_s14_ef8", "--steps", "2", "--warmup", "3", "--no-cpu-baseline"], 900)
+    d = _run(["--workload", "rmat_s14_ef8", "--steps", "2", "--warmup", "3", "--no-cpu-baseline", "--no-extras"],
+             900)
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
               "scaling", "vs_baseline", "dtype", "data", "config", "e2e", "roofline", "clocks", "gpu_launches"):
         assert k in d, k
@@ -47,3 +49,9 @@ def test_our_arm_line():
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] > 0
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert d["parity_vs_oracle_digest"] in (True, None) and d["snd_equals_and"] is True
+    if r["kernel"] in ("snd_pass", "and_pass"):
+        assert r["frac_survey"] > r["frac"] > 0   # the survey model also counts the gathered tau
+    assert r["frac_dram"] is None or r["frac_dram"] > 0
+    assert 0 < d["value_launched"] <= d["value"]
+    ref = _run(["--impl", "reference", "--workload", "rmat_s14_ef8", "--steps", "1", "--warmup", "0"], 600)
+    assert ref["config"] == d["config"]   # both arms decompose the same graph

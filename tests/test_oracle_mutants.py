@@ -136,6 +136,7 @@ def _run(name, workdir):
     pkg = os.path.join(mut_dir, "oracle")
     os.makedirs(pkg)
     shutil.copy(os.path.join(ORACLE, "__init__.py"), pkg)
+    shutil.copy(os.path.join(ORACLE, "snd_mt.c"), pkg)
     with open(os.path.join(pkg, "oracle.c"), "w") as f:
         f.write(src)
     p = subprocess.run([sys.executable, "-c", RUNNER, mut_dir, ROOT, TESTS], capture_output=True,

@@ -11,9 +11,9 @@ from paper_1704_00386_gb300 import graphs as G
 from paper_1704_00386_gb300.serve import Request, Server, footprint_bytes
 
 
-def _bare_server(budget, batch_bytes=1 << 30, max_batch=64):
+def _bare_server(budget, batch_bytes=1 << 30, max_batch=64, max_wait_s=1e9):
     srv = Server.__new__(Server)  # no workers, no device
-    srv.budget, srv.batch_bytes, srv.max_batch = budget, batch_bytes, max_batch
+    srv.budget, srv.batch_bytes, srv.max_batch, srv.max_wait_s = budget, batch_bytes, max_batch, max_wait_s
     srv.used, srv.queue, srv.cv, srv.closing, srv.next_id, srv.completed = 0, [], threading.Condition(), False, 0, []
     return srv
 
@@ -61,3 +61,41 @@ def test_submit_rejects_a_request_larger_than_the_budget():
     rp, col = G.complete_graph(30)
     req = srv.submit(rp, col, 3, 4)
     assert req.done.is_set() and "budget" in req.error and srv.queue == []
+
+
+def test_aging_stops_small_requests_from_starving_a_large_one():
+    """Once the oldest request has waited past max_wait_s and still does not
+    fit, later requests are held back until it does."""
+    srv = _bare_server(budget=1000, max_wait_s=0.5)
+    srv.used = 600
+    big = _req(2, 3, "and", 800, 0)
+    big.arrival = 10.0
+    small = [_req(1, 2, "and", 100, i) for i in range(1, 4)]
+    for q in small:
+        q.arrival = 10.1
+    srv.queue = [big] + small
+    assert [g.rid for g in srv._take(now=10.2)] == [1, 2, 3]  # still young: the small ones go ahead
+    assert srv.used == 900
+    srv.queue.extend(_req(1, 2, "and", 100, i) for i in range(4, 6))
+    for q in srv.queue[1:]:
+        q.arrival = 10.9
+    srv.used = 600
+    assert srv._take(now=11.0) == []                         # the big one is old: reserve for it
+    srv.used = 200                                           # running work finishes
+    assert [g.rid for g in srv._take(now=11.1)] == [0]       # it fits now and goes first
+    assert [g.rid for g in srv._take(now=11.1)] == []        # nothing else fits next to it
+    srv.used = 0
+    assert [g.rid for g in srv._take(now=11.2)] == [4, 5]
+
+
+def test_cancel_withdraws_a_waiting_request_only():
+    srv = _bare_server(budget=1000)
+    a, b = _req(2, 3, "and", 100, 0), _req(2, 3, "and", 100, 1)
+    srv.queue = [a, b]
+    assert srv.cancel(a) is True
+    assert a.done.is_set() and a.error == "cancelled" and srv.queue == [b]
+    assert srv.cancel(a) is False                            # not waiting any more
+    taken = srv._take()
+    assert taken == [b]
+    assert srv.cancel(b) is False                            # a worker has it: it runs to completion
+    assert not b.done.is_set() and b.error is None

@@ -6,8 +6,10 @@ they cannot take the device synchronisation that cudaMalloc / cudaFree
 imply.  Its only scratch is a fixed file-scope device array, shared by every
 call, so these tests check that consecutive calls on different graphs give
 exactly the core numbers of the allocating path (nd_build_incidence(g, 1, 2)
-+ nd_snd) -- integers, so the comparison is exact -- and that oversized
-graphs are refused.  This file is collected last on purpose.
++ nd_snd) and of the CPU oracle -- integers, so the comparisons are exact --
+that oversized graphs are refused, and that after the size-0 set-up call
+two more calls change the device's free memory by nothing.  This file is
+collected last on purpose.
 """
 import ctypes
 
@@ -57,6 +59,51 @@ def test_noalloc_matches_allocating_snd_on_consecutive_calls():
         torch.cuda.synchronize()
         assert torch.equal(out, want)
         assert iters == want_iters
+
+
+def test_noalloc_matches_the_oracle_directly():
+    import oracle
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_00386_gb300 import nd
+    lib = nd.load()
+    for rp, col in _graphs()[:3]:
+        rp_d = torch.from_numpy(rp).cuda()
+        col_d = torch.from_numpy(col).cuda()
+        out = torch.full((rp.size - 1,), -7, dtype=torch.int32, device="cuda")
+        st, _ = _call_noalloc(lib, rp_d, col_d, out)
+        assert st == nd.ND_OK, lib.nd_last_error().decode()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy(), oracle.decompose(rp, col, 1, 2))
+
+
+def test_noalloc_allocates_nothing_after_its_set_up_call():
+    """A call with n = 0 loads the entry point's code and scratch array onto
+    the device; after it, calls take no device memory: the free memory the
+    driver reports is the same before and after two calls in a row."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_00386_gb300 import nd
+    lib = nd.load()
+    w = G.workload("chunglu_n2000_g2.5_d10")
+    n, s, d = G.rmat(14, 16, seed=43)
+    rp2, col2 = G.to_csr(n, s, d)
+    args = []
+    for rp, col in ((w["row_ptr"], w["col"]), (rp2, col2)):
+        rp_d = torch.from_numpy(rp).cuda()
+        col_d = torch.from_numpy(col).cuda()
+        out = torch.empty(rp.size - 1, dtype=torch.int32, device="cuda")
+        args.append((rp_d, col_d, out))
+    it = ctypes.c_int32()
+    assert lib.nd_core_snd_noalloc(None, None, 0, 0, None, 0, ctypes.byref(it), None) == nd.ND_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for rp_d, col_d, out in args:
+        st, _ = _call_noalloc(lib, rp_d, col_d, out)
+        assert st == nd.ND_OK, lib.nd_last_error().decode()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
 
 
 def test_noalloc_iteration_cap_and_size_limit():
