@@ -396,12 +396,22 @@ __global__ void k_orient(int64_t n, const int64_t* __restrict__ rp, const int32_
 #ifndef ND_TRI_MIN_BLOCKS
 #define ND_TRI_MIN_BLOCKS 6  // resident blocks per SM for the triangle count / fill
 #endif
+// The count pass can also record every triangle it finds (rec != nullptr):
+// one uint2 (k, i << 16 | j) per triangle, k the oriented edge, i and j the
+// offsets of w in the shorter and the longer of the two out-lists.  Under
+// the degree orientation an out-list holds at most sqrt(2m) entries (each
+// out-neighbour has at least as many neighbours), so i, j < 2^16 for m <
+// 2^31.  k_tri_scatter then fills the incidence from the records without
+// searching again.  Records past rec_cap are dropped (the caller checks the
+// count and falls back to the searching fill).
 template <bool FILL, bool ADJ, typename C = unsigned long long>
 __global__ void __launch_bounds__(kThreads, ND_TRI_MIN_BLOCKS) k_tri_oriented(int64_t m, const int64_t* __restrict__ out_ptr,
                                const int32_t* __restrict__ out_col, const uint32_t* __restrict__ out_eid,
                                const int32_t* __restrict__ out_src, const uint32_t* __restrict__ out_pos,
                                const uint32_t* __restrict__ out_mir, C* __restrict__ ctr,
-                               uint2* __restrict__ inc) {
+                               uint2* __restrict__ inc, uint2* __restrict__ rec = nullptr,
+                               unsigned long long* __restrict__ rec_ctr = nullptr,
+                               unsigned long long rec_cap = 0) {
     const int lane = threadIdx.x & 31;
     for (int64_t k = warp_id_global(); k < m; k += warp_count_global()) {
         const int32_t u = out_src[k], v = out_col[k];
@@ -450,6 +460,14 @@ __global__ void __launch_bounds__(kThreads, ND_TRI_MIN_BLOCKS) k_tri_oriented(in
                         atomicAdd(ctr + e_uw, (C)1);
                         atomicAdd(ctr + e_vw, (C)1);
                     }
+                    if (rec) {
+                        unsigned long long rb = 0;
+                        if (lane == 0) rb = atomicAdd(rec_ctr, (unsigned long long)nf);
+                        rb = __shfl_sync(kFull, rb, 0);
+                        const unsigned long long slot = rb + (unsigned long long)__popc(bal & lanemask_lt());
+                        if (found && slot < rec_cap)
+                            rec[slot] = make_uint2((uint32_t)k, ((uint32_t)(p - ab) << 16) | (uint32_t)(pb - bb));
+                    }
                 } else {
                     uint32_t pbp = 0, mb = 0;
                     if (found) {
@@ -491,6 +509,83 @@ __global__ void __launch_bounds__(kThreads, ND_TRI_MIN_BLOCKS) k_tri_oriented(in
             }
             const int64_t last_pb = __shfl_sync(kFull, pb, 31);
             if (base + 32 <= ae) lo = last_pb;
+        }
+    }
+}
+
+// upper bound on the triangles: each is found once, as an element of the
+// shorter out-list of its oriented edge
+__global__ void k_tri_bound(int64_t m, const int64_t* __restrict__ out_ptr, const int32_t* __restrict__ out_src,
+                            const int32_t* __restrict__ out_col, unsigned long long* __restrict__ sum) {
+    unsigned long long acc = 0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = out_src[k], v = out_col[k];
+        const int64_t du = out_ptr[u + 1] - out_ptr[u], dv = out_ptr[v + 1] - out_ptr[v];
+        acc += (unsigned long long)(du < dv ? du : dv);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(sum, acc);
+}
+
+// The fill from the count pass's triangle records: the same three entries
+// per triangle as k_tri_oriented<true, true>, at slots from the same
+// cursors, with no search.  The slot of the oriented edge's own entry is
+// reserved once for all records of the warp that share it.
+template <typename C>
+__global__ void __launch_bounds__(kThreads) k_tri_scatter(int64_t T, const uint2* __restrict__ rec,
+                                                          const int64_t* __restrict__ out_ptr,
+                                                          const int32_t* __restrict__ out_col,
+                                                          const uint32_t* __restrict__ out_eid,
+                                                          const int32_t* __restrict__ out_src,
+                                                          const uint32_t* __restrict__ out_pos,
+                                                          const uint32_t* __restrict__ out_mir, C* __restrict__ ctr,
+                                                          uint2* __restrict__ inc) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t trips = (T + stride - 1) / stride;  // the same for every lane: the warp stays converged
+    for (int64_t it = 0; it < trips; ++it) {
+        const int64_t t = first + it * stride;
+        const bool ok = t < T;
+        uint32_t e_uv = 0xffffffffu, e_uw = 0, e_vw = 0;
+        uint2 r_uv = make_uint2(0u, 0u), r_uw = r_uv, r_vw = r_uv;
+        if (ok) {
+            const uint2 rc = __ldcs(rec + t);
+            const int64_t k = rc.x;
+            const int32_t u = __ldg(out_src + k), v = __ldg(out_col + k);
+            e_uv = __ldg(out_eid + k);
+            const uint32_t Puv = __ldg(out_pos + k), Pvu = __ldg(out_mir + k);
+            const int64_t ub = __ldg(out_ptr + u), ue = __ldg(out_ptr + u + 1);
+            const int64_t vb = __ldg(out_ptr + v), ve = __ldg(out_ptr + v + 1);
+            const bool a_is_u = (ue - ub) <= (ve - vb);  // the count pass searched the shorter list's entries
+            const int64_t p = (a_is_u ? ub : vb) + (rc.y >> 16);
+            const int64_t pb = (a_is_u ? vb : ub) + (rc.y & 0xffffu);
+            const int32_t x = __ldg(out_col + p);
+            const uint32_t ea = __ldg(out_eid + p), pa = __ldg(out_pos + p), ma = __ldg(out_mir + p);
+            const uint32_t eb = __ldg(out_eid + pb), pbp = __ldg(out_pos + pb), mb = __ldg(out_mir + pb);
+            e_uw = a_is_u ? ea : eb;
+            e_vw = a_is_u ? eb : ea;
+            const uint32_t Puw = a_is_u ? pa : pbp, Pwu = a_is_u ? ma : mb;
+            const uint32_t Pvw = a_is_u ? pbp : pa, Pwv = a_is_u ? mb : ma;
+            r_uv = u < v ? make_uint2(Puw, Pvw) : make_uint2(Pvw, Puw);
+            r_uw = u < x ? make_uint2(Puv, Pwv) : make_uint2(Pwv, Puv);
+            r_vw = v < x ? make_uint2(Pvu, Pwu) : make_uint2(Pwu, Pvu);
+        }
+        // e_uv < 2^32 - 1 is a real edge; the idle lanes share the key 2^32 - 1
+        const unsigned peers = __match_any_sync(kFull, e_uv);
+        const int leader = __ffs(peers) - 1;
+        C s0 = 0, s_uw = 0, s_vw = 0;
+        if (ok && lane == leader) s0 = atomicAdd(ctr + e_uv, (C)__popc(peers));
+        if (ok) {
+            s_uw = atomicAdd(ctr + e_uw, (C)1);
+            s_vw = atomicAdd(ctr + e_vw, (C)1);
+        }
+        s0 = __shfl_sync(kFull, s0, leader);
+        if (ok) {
+            inc[(int64_t)s0 + __popc(peers & lanemask_lt())] = r_uv;
+            inc[s_uw] = r_uw;
+            inc[s_vw] = r_vw;
         }
     }
 }
@@ -1194,6 +1289,30 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
     nd_oriented o(st);
     ND_TRY(orient_graph(h, &o, st));
     const int eblocks = nd_blocks_for(m * 32, kThreads, grid_cap(h) * 4);
+    // triangle records for the stored adjacency layout (see k_tri_oriented),
+    // when a buffer of the upper bound fits; otherwise the fill searches again
+    nd_tmp<unsigned long long> rec_ctr(st);
+    uint2* rec = nullptr;
+    unsigned long long rec_cap = 0;
+    if (h->adj && !h->otf && m < ((int64_t)1 << 31)) {
+        ND_TRY(rec_ctr.alloc(2));
+        ND_CUDA(cudaMemsetAsync(rec_ctr, 0, sizeof(unsigned long long) * 2, st));
+        {
+            nd_prof_scope ps("tri_count", st);
+            k_tri_bound<<<nd_blocks_for(m, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(m, o.out_ptr, o.out_src,
+                                                                                       o.out_col, rec_ctr.p + 1);
+            ND_CUDA(cudaGetLastError());
+        }
+        unsigned long long bound = 0;
+        ND_CUDA(cudaMemcpyAsync(&bound, rec_ctr.p + 1, sizeof(bound), cudaMemcpyDeviceToHost, st));
+        ND_TRY(nd_wait(st));
+        if (bound > 0 && cudaMallocAsync((void**)&rec, sizeof(uint2) * (size_t)bound, st) == cudaSuccess) {
+            rec_cap = bound;
+        } else {
+            cudaGetLastError();
+            rec = nullptr;
+        }
+    }
     {
         // per-edge counts fit 32 bits (d_s < n); 32-bit atomics, widened for the scan
         nd_tmp<unsigned> cnt32(st);
@@ -1202,13 +1321,22 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
         nd_prof_scope ps("tri_count", st, 2);
         k_tri_oriented<false, false, unsigned><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid,
                                                                              o.out_src, nullptr, nullptr, cnt32.p,
-                                                                             nullptr);
+                                                                             nullptr, rec, rec_ctr.p, rec_cap);
         ND_CUDA(cudaGetLastError());
         k_widen_u32<<<nd_blocks_for(m, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(m, cnt32, h->inc_ptr);
         ND_CUDA(cudaGetLastError());
     }
     ND_TRY(nd_scan_i64(h->inc_ptr, m, st));
+    unsigned long long recorded = 0;
+    if (rec) ND_CUDA(cudaMemcpyAsync(&recorded, rec_ctr.p, sizeof(recorded), cudaMemcpyDeviceToHost, st));
     ND_TRY(read_i64(h->inc_ptr + m, &h->num_inc, st));
+    // records are usable if every triangle was kept (3 incidences each)
+    const bool use_rec = rec && recorded <= rec_cap && (int64_t)recorded * 3 == h->num_inc;
+    struct rec_free {
+        uint2*& p;
+        cudaStream_t s;
+        ~rec_free() { if (p) cudaFreeAsync(p, s); }
+    } rec_guard{rec, st};
     if (h->otf) {
         // no stored incidence: the counts (d_s, tau_0 and the buckets) are all
         // that is kept; every pass finds the triangles again
@@ -1230,7 +1358,17 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
             ND_CUDA(cudaMemcpyAsync(cursor, h->inc_ptr, sizeof(int64_t) * m, cudaMemcpyDeviceToDevice, st));
         }
         nd_prof_scope ps("tri_fill", st);
-        if (narrow)
+        const int rblocks = nd_blocks_for((int64_t)recorded, kThreads, grid_cap(h) * 4);
+        if (use_rec && narrow)
+            k_tri_scatter<unsigned><<<rblocks, kThreads, 0, st>>>((int64_t)recorded, rec, o.out_ptr, o.out_col,
+                                                                  o.out_eid, o.out_src, o.out_pos, o.out_mir,
+                                                                  cursor32.p, (uint2*)h->inc);
+        else if (use_rec)
+            k_tri_scatter<unsigned long long><<<rblocks, kThreads, 0, st>>>((int64_t)recorded, rec, o.out_ptr,
+                                                                            o.out_col, o.out_eid, o.out_src,
+                                                                            o.out_pos, o.out_mir, cursor.p,
+                                                                            (uint2*)h->inc);
+        else if (narrow)
             k_tri_oriented<true, true, unsigned><<<eblocks, kThreads, 0, st>>>(
                 m, o.out_ptr, o.out_col, o.out_eid, o.out_src, o.out_pos, o.out_mir, cursor32.p, (uint2*)h->inc);
         else if (h->adj)
@@ -1241,6 +1379,10 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
                                                                       o.out_src, nullptr, nullptr, cursor.p,
                                                                       (uint2*)h->inc);
         ND_CUDA(cudaGetLastError());
+    }
+    if (rec) {  // stream-ordered: released once the fill has read it
+        cudaFreeAsync(rec, st);
+        rec = nullptr;
     }
     if (h->adj) {
         nd_release(h->mirror, st);  // build only

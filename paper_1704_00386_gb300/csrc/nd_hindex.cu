@@ -431,6 +431,33 @@ __device__ __forceinline__ void notify_row(const SweepParams& P, int64_t jb, int
     }
 }
 
+// notification for one incidence entry j of a row whose tau dropped to h:
+// the same test as notify_row, for a single entry (the merged walk of group
+// rows below gives each lane entries of different rows)
+template <int Q>
+__device__ __forceinline__ void notify_entry(const SweepParams& P, int64_t j, int32_t h) {
+    if constexpr (Q == 2) {
+        const uint2 id = __ldg(reinterpret_cast<const uint2*>(P.inc) + j);
+        const uint32_t wx = __ldcg(P.next + (id.x >> 5)), wy = __ldcg(P.next + (id.y >> 5));
+        if (!((wx >> (id.x & 31)) & 1u)) notify_clear(P, id.x, h, ld_tau<false>(P.gin + id.x));
+        if (!((wy >> (id.y & 31)) & 1u)) notify_clear(P, id.y, h, ld_tau<false>(P.gin + id.y));
+    } else {
+        uint32_t id[Q], wd[Q];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) id[k] = __ldg(P.inc + Q * j + k);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) wd[k] = __ldcg(P.next + (id[k] >> 5));
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const uint32_t Rp = id[k];
+            const uint32_t bit = 1u << (Rp & 31);
+            if (wd[k] & bit) continue;
+            if (P.members && !(__ldg(P.members + (Rp >> 5)) & bit)) continue;  // PartialAnd
+            if (h <= ld_tau<false>(P.tin + Rp)) atomicOr(P.next + (Rp >> 5), bit);
+        }
+    }
+}
+
 __device__ __forceinline__ nd_item load_item(const nd_item* __restrict__ items, int64_t i) {
     longlong2 v = __ldg(reinterpret_cast<const longlong2*>(items) + i);
     nd_item it;
@@ -469,14 +496,15 @@ __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, 
     if (AND && NOTIFY && h != t0) notify_row<Q>(P, jb, je, h, lane, G);
 }
 
-// one r-clique per warp (rows of the warp bucket), streamed
-template <int Q, bool AND, bool NOTIFY>
+// one r-clique per warp (rows of the warp bucket), streamed.  CHECK: test
+// the frontier here (false when the caller has already selected active rows)
+template <int Q, bool AND, bool NOTIFY, bool CHECK = true>
 __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item& it, unsigned* bins,
                                              unsigned long long& changed, unsigned long long& evals,
                                              unsigned long long& incs) {
     const int lane = threadIdx.x & 31;
     const uint32_t R = it.R;
-    if (AND && NOTIFY && !in_frontier<Q>(P, R)) return;
+    if (CHECK && AND && NOTIFY && !in_frontier<Q>(P, R)) return;
     const int32_t t0 = ld_tau<!AND>(P.tin + R);
     // H <= d_s, so tau is clipped at d_s for the search (a no-op for every
     // valid tau, which is <= d_s); changes are detected against the stored value
@@ -524,11 +552,127 @@ __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int
     }
 }
 
-template <int Q, bool AND, bool NOTIFY>
+// AND with notification: the frontier bits of the rows [a, b) of a warp
+// chunk (at most 32 * W rows), tested by all lanes at once (one row per lane
+// per word, every load issued before any test) and returned as W ballots.
+template <int Q, int W>
+__device__ __forceinline__ void active_masks(const SweepParams& P, int64_t a, int64_t b, unsigned (&mask)[W]) {
+    const int lane = threadIdx.x & 31;
+    uint32_t R[W];
+    bool ok[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const int64_t i = a + (int64_t)w * 32 + lane;
+        ok[w] = i < b;
+        R[w] = ok[w] ? __ldg(reinterpret_cast<const uint32_t*>(P.items + i) + 2) : 0u;  // nd_item::R
+    }
+    if constexpr (Q == 2) {
+        uint2 ep[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) ep[w] = ok[w] ? __ldg(P.epos + R[w]) : make_uint2(0u, 0u);
+        uint32_t bx[W], by[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            bx[w] = __ldg(P.cur + (ep[w].x >> 5));
+            by[w] = __ldg(P.cur + (ep[w].y >> 5));
+        }
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            mask[w] = __ballot_sync(0xffffffffu, ok[w] && (((bx[w] >> (ep[w].x & 31)) | (by[w] >> (ep[w].y & 31))) & 1u));
+    } else {
+        uint32_t bw[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) bw[w] = __ldg(P.cur + (R[w] >> 5));
+#pragma unroll
+        for (int w = 0; w < W; ++w) mask[w] = __ballot_sync(0xffffffffu, ok[w] && ((bw[w] >> (R[w] & 31)) & 1u));
+    }
+}
+
+// position of the k-th (0-based) set bit of m, for k < popc(m): halves by popcount
+__device__ __forceinline__ int nth_set_bit(unsigned m, int k) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const unsigned low = m & ((1u << w) - 1u);
+        const int c = __popc(low);
+        if (k >= c) {
+            k -= c;
+            m >>= w;
+            pos += w;
+        } else {
+            m = low;
+        }
+    }
+    return pos;
+}
+
+// AND with notification, group rows: the active rows among the 32 rows
+// a + {bits of mask}, packed densely onto the 32/G groups of the warp (no
+// group idles on an inactive row).  After each round the entries of every
+// row that changed are walked by all 32 lanes together (the merged
+// notification), instead of by each row's own G lanes while the groups whose
+// rows did not change wait.
+template <int Q, int G, int C>
+__device__ __forceinline__ void run_groups_active(const SweepParams& P, int64_t a, unsigned mask,
+                                                  unsigned long long& changed, unsigned long long& evals,
+                                                  unsigned long long& incs) {
+    constexpr int NG = 32 / G;
+    auto g = cg::tiled_partition<G>(cg::this_thread_block());
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / G;
+    const int cnt = __popc(mask);
+    for (int base = 0; base < cnt; base += NG) {
+        const int k = base + grp;  // this group's k-th active row
+        int64_t jb = 0;
+        int32_t h = 0, dn = 0;
+        if (k < cnt) {  // uniform inside the group
+            const int64_t i = a + nth_set_bit(mask, k);
+            const nd_item it = load_item(P.items, i);
+            const int32_t t0 = ld_tau<false>(P.tin + it.R);
+            const int32_t t = min(t0, (int32_t)it.d);
+            jb = it.jb;
+            h = group_hindex<G, C>(g, make_rho<Q, false>(P), jb, jb + it.d, t);
+            if (g.thread_rank() == 0) {
+                evals++;
+                incs += it.d;
+                if (h != t0) {
+                    changed++;
+                    store_tau<Q>(P, it.R, h);
+                }
+            }
+            dn = (h != t0) ? (int32_t)it.d : 0;
+        }
+        // merged notification over the changed rows of this round
+        int tot = 0;
+#pragma unroll
+        for (int q = 0; q < NG; ++q) tot += __shfl_sync(0xffffffffu, dn, q * G);
+        for (int e0 = 0; e0 < tot; e0 += 32) {
+            const int e = e0 + lane;
+            int64_t j = 0;
+            int32_t hh = 0;
+            int run = 0;
+#pragma unroll
+            for (int q = 0; q < NG; ++q) {
+                const int v = __shfl_sync(0xffffffffu, dn, q * G);
+                const int64_t jq = __shfl_sync(0xffffffffu, jb, q * G);
+                const int32_t hq = __shfl_sync(0xffffffffu, h, q * G);
+                if (e >= run && e < run + v) { j = jq + (e - run); hh = hq; }
+                run += v;
+            }
+            if (e < tot) notify_entry<Q>(P, j, hh);
+        }
+    }
+}
+
 #ifndef ND_PASS_MIN_BLOCKS
 #define ND_PASS_MIN_BLOCKS 6  // resident blocks per SM the register budget targets (6 measured best)
 #endif
-__global__ void __launch_bounds__(kThreads, ND_PASS_MIN_BLOCKS) k_pass(SweepParams P) {
+#ifndef ND_AND_MIN_BLOCKS
+#define ND_AND_MIN_BLOCKS 6   // the same for the AND pass with notification
+#endif
+template <int Q, bool AND, bool NOTIFY>
+__global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS : ND_PASS_MIN_BLOCKS)
+    k_pass(SweepParams P) {
     if (P.prev != nullptr && *(volatile const unsigned long long*)P.prev == 0ull) return;  // converged
     __shared__ unsigned bins[kThreads / 32][260];  // k-ary search bins, one set per warp
     __shared__ int bounds[2];
@@ -576,6 +720,44 @@ __global__ void __launch_bounds__(kThreads, ND_PASS_MIN_BLOCKS) k_pass(SweepPara
         const int64_t cc = kShortFirst ? nchunks - 1 - (int64_t)c : (int64_t)c;
         int64_t t = cc * kWarpChunk;
         const int64_t te = min(t + (int64_t)kWarpChunk, tasks);
+        if constexpr (AND && NOTIFY) {
+            // the chunk's rows per bucket, their frontier bits tested up front;
+            // only active rows are evaluated
+            static_assert(kWarpChunk <= 32, "one mask word of warp rows per chunk");
+            const int64_t w_hi = min(te, n2);
+            if (t < w_hi) {
+                unsigned m2[1];
+                active_masks<Q, 1>(P, P.lo[2] + t, P.lo[2] + w_hi, m2);
+                unsigned mm = m2[0];
+                while (mm) {
+                    const int b = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    const nd_item it = load_item(P.items, P.lo[2] + t + b);
+                    run_warp_row<Q, AND, NOTIFY, false>(P, it, bins[threadIdx.x >> 5], changed, evals, incs);
+                }
+            }
+            const int64_t t1_lo = max(t, n2), t1_hi = min(te, n2 + t1);
+            if (t1_lo < t1_hi) {
+                constexpr int W1 = (kWarpChunk * 4 + 31) / 32;
+                const int64_t a = P.lo[1] + 4 * (t1_lo - n2), b = min(P.lo[1] + 4 * (t1_hi - n2), P.hi[1]);
+                unsigned mk[W1];
+                active_masks<Q, W1>(P, a, b, mk);
+#pragma unroll
+                for (int w = 0; w < W1; ++w)
+                    if (mk[w]) run_groups_active<Q, 8, 8>(P, a + 32 * w, mk[w], changed, evals, incs);
+            }
+            const int64_t t0_lo = max(t, n2 + t1);
+            if (t0_lo < te) {
+                constexpr int W0 = (kWarpChunk * 8 + 31) / 32;
+                const int64_t a = P.lo[0] + 8 * (t0_lo - n2 - t1), b = min(P.lo[0] + 8 * (te - n2 - t1), P.hi[0]);
+                unsigned mk[W0];
+                active_masks<Q, W0>(P, a, b, mk);
+#pragma unroll
+                for (int w = 0; w < W0; ++w)
+                    if (mk[w]) run_groups_active<Q, 4, 2>(P, a + 32 * w, mk[w], changed, evals, incs);
+            }
+            continue;
+        }
         const int64_t e2 = min(te, n2);
         if (t < e2) {
             // warp rows: the next row's work item is loaded before this one runs

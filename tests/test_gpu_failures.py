@@ -98,7 +98,7 @@ def test_handle_memory_limit_refuses_the_build():
     rp, col = _graph()
     rp_d, col_d = torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda()
     try:
-        nd.set_handle_memory_limit(1 << 20)      # 1 MB: far below this graph's incidence
+        nd.set_handle_memory_limit(64 << 10)     # 64 KB: below even the k-core handle (CSR copy 150 KB)
         for r, s in ((1, 2), (2, 3), (3, 4)):
             with pytest.raises(nd.NDError) as e:
                 nd.build_incidence(rp_d, col_d, r, s)
