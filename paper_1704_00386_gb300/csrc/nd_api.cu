@@ -192,7 +192,8 @@ void nd_free(nd_incidence* h) {
     cudaStreamSynchronize(st);
     void* ptrs[] = {h->nlow, h->up_start, h->eid, h->e_u, h->e_v, h->tri_ptr, h->tri_w, h->tri_e,
                     h->items, h->tau[0], h->tau[1], h->front[0], h->front[1], h->counters,
-                    h->mirror, h->e_pos, h->tg[0], h->tg[1], h->long_rows, h->long_seg, h->to_new, h->to_old};
+                    h->mirror, h->e_pos, h->tg[0], h->tg[1], h->long_rows, h->long_seg, h->to_new, h->to_old,
+                    h->vto_old, h->c_rp, h->c_up, h->c_col, h->c_nlow};
     for (void* p : ptrs) nd_release(p, st);
     for (auto& row : h->pass_graph)
         for (auto& ex : row)
@@ -261,8 +262,10 @@ static nd_status check_limits(const nd_csr* g, int r) {
     return ND_OK;
 }
 
+// relabel: single-graph builds may renumber a large (2,3) graph by degree
+// class; a batch keeps its ids (each graph's vertices stay contiguous)
 static nd_status build_common(const nd_csr* g, int r, int s, cudaStream_t st, nd_incidence** out,
-                              unsigned flags = 0) {
+                              unsigned flags = 0, bool relabel = true) {
     int dev = 0;
     ND_CUDA(cudaGetDevice(&dev));
     keep_pool(dev);
@@ -276,7 +279,9 @@ static nd_status build_common(const nd_csr* g, int r, int s, cudaStream_t st, nd
         h->sm_count = 152;
     h->last_stream = st;
     nd_status rc = nd_build_graph(h, g, st);
+    if (rc == ND_OK && r == 2 && !h->otf && relabel) rc = nd_relabel_truss_graph(h, st);
     if (rc == ND_OK && r >= 2) rc = nd_build_edges(h, st);
+    if (rc == ND_OK && r == 2) rc = nd_relabel_truss_edges(h, st);
     if (rc == ND_OK) {
         if (r == 1) {
             rc = nd_relabel_by_degree(h, st);
@@ -380,7 +385,7 @@ nd_status nd_build_incidence_batch(const nd_csr* graphs, int count, int r, int s
         hrp[n] = nnz;
         if (rc == ND_OK) {
             nd_csr u{n, nnz, hrp.data(), hcol.data(), 0};
-            rc = build_common(&u, r, s, st, out);
+            rc = build_common(&u, r, s, st, out, 0, false);
         }
         if (rc == ND_OK && r_offsets) rc = nd_batch_offsets(*out, voff.data(), count, r_offsets, st);
         if (rc != ND_OK && *out) { nd_free(*out); *out = nullptr; }
@@ -388,7 +393,7 @@ nd_status nd_build_incidence_batch(const nd_csr* graphs, int count, int r, int s
     }
     if (rc == ND_OK) {
         nd_csr u{n, nnz, urp, ucol, 1};
-        rc = build_common(&u, r, s, st, out);
+        rc = build_common(&u, r, s, st, out, 0, false);
     }
     if (rc == ND_OK && r_offsets) rc = nd_batch_offsets(*out, voff.data(), count, r_offsets, st);
     if (rc != ND_OK && *out) { nd_free(*out); *out = nullptr; }

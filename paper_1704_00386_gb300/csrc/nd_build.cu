@@ -280,6 +280,75 @@ __global__ void k_permute_i32(int64_t n, const int32_t* __restrict__ idx, const 
     }
 }
 
+// (2,3) relabelling: the key (new u, new v) of every entry, at its own
+// position (the sort that follows fixes the order)
+__device__ __forceinline__ void relabel_key_entries(const int32_t* __restrict__ col, const int32_t* __restrict__ to_new,
+                                                    int bits, unsigned long long* __restrict__ keys, int64_t u,
+                                                    int64_t pb, int64_t pe) {
+    const unsigned long long hi = (unsigned long long)to_new[u] << bits;
+    for (int64_t p = pb + (threadIdx.x & 31); p < pe; p += 32) keys[p] = hi | (unsigned long long)to_new[col[p]];
+}
+
+__global__ void k_relabel_keys(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                               const int32_t* __restrict__ to_new, int bits, unsigned long long* __restrict__ keys) {
+    for (int64_t u = warp_id_global(); u < n; u += warp_count_global()) {
+        const int64_t b = rp[u], e = rp[u + 1];
+        if (is_long_row(b, e)) continue;  // k_relabel_keys_long
+        relabel_key_entries(col, to_new, bits, keys, u, b, e);
+    }
+}
+
+__global__ void k_relabel_keys_long(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                    const int32_t* __restrict__ to_new, int bits, unsigned long long* __restrict__ keys,
+                                    const int32_t* __restrict__ rows, const int64_t* __restrict__ seg_off,
+                                    int64_t count, int64_t segs) {
+    for (int64_t sg = warp_id_global(); sg < segs; sg += warp_count_global()) {
+        int64_t u, b, pb, pe;
+        long_segment(sg, rows, seg_off, count, rp, u, b, pb, pe);
+        relabel_key_entries(col, to_new, bits, keys, u, pb, pe);
+    }
+}
+
+__global__ void k_keys_to_col(int64_t nnz, const unsigned long long* __restrict__ keys, int bits,
+                              int32_t* __restrict__ col) {
+    const unsigned long long mask = (1ull << bits) - 1ull;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz; j += (int64_t)gridDim.x * blockDim.x)
+        col[j] = (int32_t)(keys[j] & mask);
+}
+
+// new edge e = (e_u[e], e_v[e]) -> the caller's edge id: its endpoints in
+// caller ids, smaller first, and the rank of the larger among the smaller
+// one's larger neighbours in the caller's CSR
+__global__ void k_edge_map(int64_t m, const int32_t* __restrict__ e_u, const int32_t* __restrict__ e_v,
+                           const int32_t* __restrict__ vto_old, const int64_t* __restrict__ c_rp,
+                           const int32_t* __restrict__ c_col, const int32_t* __restrict__ c_nlow,
+                           const int64_t* __restrict__ c_up, int32_t* __restrict__ to_new,
+                           int32_t* __restrict__ to_old, int* __restrict__ err) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = vto_old[e_u[e]], b = vto_old[e_v[e]];
+        const int32_t x = a < b ? a : b, y = a < b ? b : a;
+        const int64_t first = c_rp[x] + c_nlow[x], end = c_rp[x + 1];
+        const int64_t pos = lower_bound_i32(c_col, first, end, y);
+        if (pos >= end || c_col[pos] != y) { atomicOr(err, 1); continue; }
+        const int64_t cid = c_up[x] + (pos - first);
+        to_old[e] = (int32_t)cid;
+        to_new[cid] = (int32_t)e;
+    }
+}
+
+// r-clique tuples of a relabelled (2,3) handle: caller vertex ids, at the
+// caller's edge ids
+__global__ void k_r_cliques_mapped(int64_t N, const int32_t* __restrict__ e_u, const int32_t* __restrict__ e_v,
+                                   const int32_t* __restrict__ vto_old, const int32_t* __restrict__ to_old,
+                                   int32_t* __restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = vto_old[e_u[e]], b = vto_old[e_v[e]];
+        const int64_t c = to_old[e];
+        out[2 * c] = a < b ? a : b;
+        out[2 * c + 1] = a < b ? b : a;
+    }
+}
+
 // ---- canonical edge ids (one warp per vertex) ------------------------------
 // Edge (u,v), u < v, gets id up_start[u] + (rank of v among u's larger
 // neighbours): lexicographic order.  eid[p] is the id of the edge at CSR
@@ -396,22 +465,12 @@ __global__ void k_orient(int64_t n, const int64_t* __restrict__ rp, const int32_
 #ifndef ND_TRI_MIN_BLOCKS
 #define ND_TRI_MIN_BLOCKS 6  // resident blocks per SM for the triangle count / fill
 #endif
-// The count pass can also record every triangle it finds (rec != nullptr):
-// one uint2 (k, i << 16 | j) per triangle, k the oriented edge, i and j the
-// offsets of w in the shorter and the longer of the two out-lists.  Under
-// the degree orientation an out-list holds at most sqrt(2m) entries (each
-// out-neighbour has at least as many neighbours), so i, j < 2^16 for m <
-// 2^31.  k_tri_scatter then fills the incidence from the records without
-// searching again.  Records past rec_cap are dropped (the caller checks the
-// count and falls back to the searching fill).
 template <bool FILL, bool ADJ, typename C = unsigned long long>
 __global__ void __launch_bounds__(kThreads, ND_TRI_MIN_BLOCKS) k_tri_oriented(int64_t m, const int64_t* __restrict__ out_ptr,
                                const int32_t* __restrict__ out_col, const uint32_t* __restrict__ out_eid,
                                const int32_t* __restrict__ out_src, const uint32_t* __restrict__ out_pos,
                                const uint32_t* __restrict__ out_mir, C* __restrict__ ctr,
-                               uint2* __restrict__ inc, uint2* __restrict__ rec = nullptr,
-                               unsigned long long* __restrict__ rec_ctr = nullptr,
-                               unsigned long long rec_cap = 0) {
+                               uint2* __restrict__ inc) {
     const int lane = threadIdx.x & 31;
     for (int64_t k = warp_id_global(); k < m; k += warp_count_global()) {
         const int32_t u = out_src[k], v = out_col[k];
@@ -460,14 +519,6 @@ __global__ void __launch_bounds__(kThreads, ND_TRI_MIN_BLOCKS) k_tri_oriented(in
                         atomicAdd(ctr + e_uw, (C)1);
                         atomicAdd(ctr + e_vw, (C)1);
                     }
-                    if (rec) {
-                        unsigned long long rb = 0;
-                        if (lane == 0) rb = atomicAdd(rec_ctr, (unsigned long long)nf);
-                        rb = __shfl_sync(kFull, rb, 0);
-                        const unsigned long long slot = rb + (unsigned long long)__popc(bal & lanemask_lt());
-                        if (found && slot < rec_cap)
-                            rec[slot] = make_uint2((uint32_t)k, ((uint32_t)(p - ab) << 16) | (uint32_t)(pb - bb));
-                    }
                 } else {
                     uint32_t pbp = 0, mb = 0;
                     if (found) {
@@ -509,83 +560,6 @@ __global__ void __launch_bounds__(kThreads, ND_TRI_MIN_BLOCKS) k_tri_oriented(in
             }
             const int64_t last_pb = __shfl_sync(kFull, pb, 31);
             if (base + 32 <= ae) lo = last_pb;
-        }
-    }
-}
-
-// upper bound on the triangles: each is found once, as an element of the
-// shorter out-list of its oriented edge
-__global__ void k_tri_bound(int64_t m, const int64_t* __restrict__ out_ptr, const int32_t* __restrict__ out_src,
-                            const int32_t* __restrict__ out_col, unsigned long long* __restrict__ sum) {
-    unsigned long long acc = 0;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t u = out_src[k], v = out_col[k];
-        const int64_t du = out_ptr[u + 1] - out_ptr[u], dv = out_ptr[v + 1] - out_ptr[v];
-        acc += (unsigned long long)(du < dv ? du : dv);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(sum, acc);
-}
-
-// The fill from the count pass's triangle records: the same three entries
-// per triangle as k_tri_oriented<true, true>, at slots from the same
-// cursors, with no search.  The slot of the oriented edge's own entry is
-// reserved once for all records of the warp that share it.
-template <typename C>
-__global__ void __launch_bounds__(kThreads) k_tri_scatter(int64_t T, const uint2* __restrict__ rec,
-                                                          const int64_t* __restrict__ out_ptr,
-                                                          const int32_t* __restrict__ out_col,
-                                                          const uint32_t* __restrict__ out_eid,
-                                                          const int32_t* __restrict__ out_src,
-                                                          const uint32_t* __restrict__ out_pos,
-                                                          const uint32_t* __restrict__ out_mir, C* __restrict__ ctr,
-                                                          uint2* __restrict__ inc) {
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t trips = (T + stride - 1) / stride;  // the same for every lane: the warp stays converged
-    for (int64_t it = 0; it < trips; ++it) {
-        const int64_t t = first + it * stride;
-        const bool ok = t < T;
-        uint32_t e_uv = 0xffffffffu, e_uw = 0, e_vw = 0;
-        uint2 r_uv = make_uint2(0u, 0u), r_uw = r_uv, r_vw = r_uv;
-        if (ok) {
-            const uint2 rc = __ldcs(rec + t);
-            const int64_t k = rc.x;
-            const int32_t u = __ldg(out_src + k), v = __ldg(out_col + k);
-            e_uv = __ldg(out_eid + k);
-            const uint32_t Puv = __ldg(out_pos + k), Pvu = __ldg(out_mir + k);
-            const int64_t ub = __ldg(out_ptr + u), ue = __ldg(out_ptr + u + 1);
-            const int64_t vb = __ldg(out_ptr + v), ve = __ldg(out_ptr + v + 1);
-            const bool a_is_u = (ue - ub) <= (ve - vb);  // the count pass searched the shorter list's entries
-            const int64_t p = (a_is_u ? ub : vb) + (rc.y >> 16);
-            const int64_t pb = (a_is_u ? vb : ub) + (rc.y & 0xffffu);
-            const int32_t x = __ldg(out_col + p);
-            const uint32_t ea = __ldg(out_eid + p), pa = __ldg(out_pos + p), ma = __ldg(out_mir + p);
-            const uint32_t eb = __ldg(out_eid + pb), pbp = __ldg(out_pos + pb), mb = __ldg(out_mir + pb);
-            e_uw = a_is_u ? ea : eb;
-            e_vw = a_is_u ? eb : ea;
-            const uint32_t Puw = a_is_u ? pa : pbp, Pwu = a_is_u ? ma : mb;
-            const uint32_t Pvw = a_is_u ? pbp : pa, Pwv = a_is_u ? mb : ma;
-            r_uv = u < v ? make_uint2(Puw, Pvw) : make_uint2(Pvw, Puw);
-            r_uw = u < x ? make_uint2(Puv, Pwv) : make_uint2(Pwv, Puv);
-            r_vw = v < x ? make_uint2(Pvu, Pwu) : make_uint2(Pwu, Pvu);
-        }
-        // e_uv < 2^32 - 1 is a real edge; the idle lanes share the key 2^32 - 1
-        const unsigned peers = __match_any_sync(kFull, e_uv);
-        const int leader = __ffs(peers) - 1;
-        C s0 = 0, s_uw = 0, s_vw = 0;
-        if (ok && lane == leader) s0 = atomicAdd(ctr + e_uv, (C)__popc(peers));
-        if (ok) {
-            s_uw = atomicAdd(ctr + e_uw, (C)1);
-            s_vw = atomicAdd(ctr + e_vw, (C)1);
-        }
-        s0 = __shfl_sync(kFull, s0, leader);
-        if (ok) {
-            inc[(int64_t)s0 + __popc(peers & lanemask_lt())] = r_uv;
-            inc[s_uw] = r_uw;
-            inc[s_vw] = r_vw;
         }
     }
 }
@@ -1054,14 +1028,11 @@ static void release_long_rows(nd_incidence* h, cudaStream_t st) {
     h->long_count = h->long_segs = 0;
 }
 
-nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st) {
-    h->n = g->n;
-    h->nnz = g->nnz;
-    ND_TRY(nd_alloc((void**)&h->rp, sizeof(int64_t) * (g->n + 1), st, h));
-    ND_TRY(nd_alloc((void**)&h->col, sizeof(int32_t) * (g->nnz > 0 ? g->nnz : 1), st, h));
-    cudaMemcpyKind kind = g->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    ND_CUDA(cudaMemcpyAsync(h->rp, g->row_ptr, sizeof(int64_t) * (g->n + 1), kind, st));
-    if (g->nnz > 0) ND_CUDA(cudaMemcpyAsync(h->col, g->col, sizeof(int32_t) * g->nnz, kind, st));
+// validation and degree split of the handle's CSR (h->rp, h->col): nlow,
+// up_start, the long rows, for r >= 2 the reverse entries, and h->m
+static nd_status validate_split(nd_incidence* h, cudaStream_t st) {
+    const nd_csr gg{h->n, h->nnz, h->rp, h->col, 1};
+    const nd_csr* g = &gg;
     ND_TRY(nd_alloc((void**)&h->nlow, sizeof(int32_t) * (g->n > 0 ? g->n : 1), st, h));
     ND_TRY(nd_alloc((void**)&h->up_start, sizeof(int64_t) * (g->n + 1), st, h));
     // reverse entries for the edge ids and the (2,3) adjacency layout (build only)
@@ -1105,9 +1076,137 @@ nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st) {
     return ND_OK;
 }
 
+nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st) {
+    h->n = g->n;
+    h->nnz = g->nnz;
+    ND_TRY(nd_alloc((void**)&h->rp, sizeof(int64_t) * (g->n + 1), st, h));
+    ND_TRY(nd_alloc((void**)&h->col, sizeof(int32_t) * (g->nnz > 0 ? g->nnz : 1), st, h));
+    cudaMemcpyKind kind = g->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    ND_CUDA(cudaMemcpyAsync(h->rp, g->row_ptr, sizeof(int64_t) * (g->n + 1), kind, st));
+    if (g->nnz > 0) ND_CUDA(cudaMemcpyAsync(h->col, g->col, sizeof(int32_t) * g->nnz, kind, st));
+    return validate_split(h, st);
+}
+
 // graphs smaller than this keep their ids: their tau fits in cache anyway,
 // and the few launches of a relabelling would dominate their build
 constexpr int64_t kRelabelMinVertices = 1 << 16;
+
+// vertex ids by degree class (k_class_count / k_class_scatter) for the graph
+// in h->rp: to_new[caller id] = new id, to_old[new id] = caller id
+static nd_status class_ids(nd_incidence* h, int32_t* to_new, int32_t* to_old, cudaStream_t st) {
+    const int64_t n = h->n;
+    const int64_t nblocks = (n + kRelabelTile - 1) / kRelabelTile;
+    const int64_t cells = (int64_t)(kClasses - 1) * nblocks;
+    nd_tmp<int64_t> cnt(st);
+    ND_TRY(cnt.alloc(cells + 1));
+    ND_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (cells + 1), st));
+    k_class_count<<<nblocks, kThreads, 0, st>>>(n, h->rp, cnt, nblocks);
+    ND_CUDA(cudaGetLastError());
+    ND_TRY(nd_scan_i64(cnt, cells, st));
+    k_class_scatter<<<nblocks, kThreads, 0, st>>>(n, h->rp, cnt, nblocks, to_new, to_old);
+    ND_CUDA(cudaGetLastError());
+    return ND_OK;
+}
+
+// (2,3), step 1 of the relabelling (after validation, before the edge ids):
+// vertices renumbered by degree class, the graph rewritten under the new ids
+// with every row sorted again (a radix sort of the keys (new u, new v) of
+// all entries, which is the new CSR in row order), then validated and split
+// again.  The caller's CSR and its split are kept until step 2 has mapped
+// the edges.  Graphs below kRelabelMinVertices keep their ids.
+nd_status nd_relabel_truss_graph(nd_incidence* h, cudaStream_t st) {
+    const int64_t n = h->n, nnz = h->nnz;
+    if (n < kRelabelMinVertices || h->r != 2) return ND_OK;
+    nd_prof_scope ps("relabel", st);
+    int32_t* vto_new = nullptr;
+    ND_TRY(nd_alloc((void**)&vto_new, sizeof(int32_t) * n, st, h));
+    ND_TRY(nd_alloc((void**)&h->vto_old, sizeof(int32_t) * n, st, h));
+    nd_status rc = class_ids(h, vto_new, h->vto_old, st);
+    int64_t* nrp = nullptr;
+    int32_t* ncol = nullptr;
+    if (rc == ND_OK) rc = nd_alloc((void**)&nrp, sizeof(int64_t) * (n + 1), st, h);
+    if (rc == ND_OK) rc = nd_alloc((void**)&ncol, sizeof(int32_t) * (nnz > 0 ? nnz : 1), st, h);
+    if (rc == ND_OK && nnz > 0) {
+        nd_tmp<unsigned long long> keys(st), alt(st);
+        rc = keys.alloc(nnz);
+        if (rc == ND_OK) rc = alt.alloc(nnz);
+        const int bits = nd_id_bits(n);
+        if (rc == ND_OK) {
+            k_relabel_keys<<<nd_blocks_for(n * 32, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(
+                n, h->rp, h->col, vto_new, bits, keys);
+            if (h->long_segs > 0)
+                k_relabel_keys_long<<<nd_blocks_for(h->long_segs * 32, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(
+                    h->rp, h->col, vto_new, bits, keys, h->long_rows, h->long_seg, h->long_count, h->long_segs);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) rc = nd_cuda_fail(e, "k_relabel_keys", __FILE__, __LINE__);
+        }
+        unsigned long long* sorted = nullptr;
+        if (rc == ND_OK) rc = nd_sort_u64(keys, alt, nnz, 2 * bits, &sorted, st);
+        if (rc == ND_OK) {
+            k_keys_to_col<<<nd_blocks_for(nnz, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(nnz, sorted, bits, ncol);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) rc = nd_cuda_fail(e, "k_keys_to_col", __FILE__, __LINE__);
+        }
+    }
+    if (rc == ND_OK) {
+        ND_CUDA(cudaMemsetAsync(nrp + n, 0, sizeof(int64_t), st));
+        k_new_degrees<<<nd_blocks_for(n, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(n, h->rp, vto_new, nrp);
+        ND_CUDA(cudaGetLastError());
+        rc = nd_scan_i64(nrp, n, st);
+    }
+    nd_release(vto_new, st);
+    if (rc != ND_OK) {
+        nd_release(nrp, st);
+        nd_release(ncol, st);
+        return rc;
+    }
+    // keep the caller's graph and split for the edge map; the new graph
+    // takes their place and is split again
+    h->c_rp = h->rp;
+    h->c_col = h->col;
+    h->c_nlow = h->nlow;
+    h->c_up = h->up_start;
+    h->rp = nrp;
+    h->col = ncol;
+    h->nlow = nullptr;
+    h->up_start = nullptr;
+    nd_release(h->mirror, st);
+    h->mirror = nullptr;
+    release_long_rows(h, st);
+    const int64_t m = h->m;
+    ND_TRY(validate_split(h, st));
+    if (h->m != m) { nd_set_error("relabelled graph lost edges (internal fault)"); return ND_E_CUDA; }
+    return ND_OK;
+}
+
+// (2,3), step 2 (after the edge ids of the new graph): the map between the
+// new canonical edge ids and the caller's, by searching each new edge's
+// caller endpoints in the caller's rows; then the caller's arrays go
+nd_status nd_relabel_truss_edges(nd_incidence* h, cudaStream_t st) {
+    if (!h->c_rp) return ND_OK;
+    const int64_t m = h->m;
+    ND_TRY(nd_alloc((void**)&h->to_new, sizeof(int32_t) * (m > 0 ? m : 1), st, h));
+    ND_TRY(nd_alloc((void**)&h->to_old, sizeof(int32_t) * (m > 0 ? m : 1), st, h));
+    nd_tmp<int> derr(st);
+    ND_TRY(derr.alloc(1));
+    ND_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
+    if (m > 0) {
+        nd_prof_scope ps("relabel", st);
+        k_edge_map<<<nd_blocks_for(m, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(
+            m, h->e_u, h->e_v, h->vto_old, h->c_rp, h->c_col, h->c_nlow, h->c_up, h->to_new, h->to_old, derr);
+        ND_CUDA(cudaGetLastError());
+    }
+    int herr = 0;
+    ND_TRY(read_flag(derr, &herr, st));
+    if (herr) { nd_set_error("an edge of the relabelled graph is missing from the caller's (internal fault)"); return ND_E_CUDA; }
+    nd_release(h->c_rp, st);
+    nd_release(h->c_col, st);
+    nd_release(h->c_nlow, st);
+    nd_release(h->c_up, st);
+    h->c_rp = h->c_up = nullptr;
+    h->c_col = h->c_nlow = nullptr;
+    return ND_OK;
+}
 
 nd_status nd_relabel_by_degree(nd_incidence* h, cudaStream_t st) {
     const int64_t n = h->n, nnz = h->nnz;
@@ -1289,30 +1388,6 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
     nd_oriented o(st);
     ND_TRY(orient_graph(h, &o, st));
     const int eblocks = nd_blocks_for(m * 32, kThreads, grid_cap(h) * 4);
-    // triangle records for the stored adjacency layout (see k_tri_oriented),
-    // when a buffer of the upper bound fits; otherwise the fill searches again
-    nd_tmp<unsigned long long> rec_ctr(st);
-    uint2* rec = nullptr;
-    unsigned long long rec_cap = 0;
-    if (h->adj && !h->otf && m < ((int64_t)1 << 31)) {
-        ND_TRY(rec_ctr.alloc(2));
-        ND_CUDA(cudaMemsetAsync(rec_ctr, 0, sizeof(unsigned long long) * 2, st));
-        {
-            nd_prof_scope ps("tri_count", st);
-            k_tri_bound<<<nd_blocks_for(m, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(m, o.out_ptr, o.out_src,
-                                                                                       o.out_col, rec_ctr.p + 1);
-            ND_CUDA(cudaGetLastError());
-        }
-        unsigned long long bound = 0;
-        ND_CUDA(cudaMemcpyAsync(&bound, rec_ctr.p + 1, sizeof(bound), cudaMemcpyDeviceToHost, st));
-        ND_TRY(nd_wait(st));
-        if (bound > 0 && cudaMallocAsync((void**)&rec, sizeof(uint2) * (size_t)bound, st) == cudaSuccess) {
-            rec_cap = bound;
-        } else {
-            cudaGetLastError();
-            rec = nullptr;
-        }
-    }
     {
         // per-edge counts fit 32 bits (d_s < n); 32-bit atomics, widened for the scan
         nd_tmp<unsigned> cnt32(st);
@@ -1321,22 +1396,13 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
         nd_prof_scope ps("tri_count", st, 2);
         k_tri_oriented<false, false, unsigned><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid,
                                                                              o.out_src, nullptr, nullptr, cnt32.p,
-                                                                             nullptr, rec, rec_ctr.p, rec_cap);
+                                                                             nullptr);
         ND_CUDA(cudaGetLastError());
         k_widen_u32<<<nd_blocks_for(m, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(m, cnt32, h->inc_ptr);
         ND_CUDA(cudaGetLastError());
     }
     ND_TRY(nd_scan_i64(h->inc_ptr, m, st));
-    unsigned long long recorded = 0;
-    if (rec) ND_CUDA(cudaMemcpyAsync(&recorded, rec_ctr.p, sizeof(recorded), cudaMemcpyDeviceToHost, st));
     ND_TRY(read_i64(h->inc_ptr + m, &h->num_inc, st));
-    // records are usable if every triangle was kept (3 incidences each)
-    const bool use_rec = rec && recorded <= rec_cap && (int64_t)recorded * 3 == h->num_inc;
-    struct rec_free {
-        uint2*& p;
-        cudaStream_t s;
-        ~rec_free() { if (p) cudaFreeAsync(p, s); }
-    } rec_guard{rec, st};
     if (h->otf) {
         // no stored incidence: the counts (d_s, tau_0 and the buckets) are all
         // that is kept; every pass finds the triangles again
@@ -1358,17 +1424,7 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
             ND_CUDA(cudaMemcpyAsync(cursor, h->inc_ptr, sizeof(int64_t) * m, cudaMemcpyDeviceToDevice, st));
         }
         nd_prof_scope ps("tri_fill", st);
-        const int rblocks = nd_blocks_for((int64_t)recorded, kThreads, grid_cap(h) * 4);
-        if (use_rec && narrow)
-            k_tri_scatter<unsigned><<<rblocks, kThreads, 0, st>>>((int64_t)recorded, rec, o.out_ptr, o.out_col,
-                                                                  o.out_eid, o.out_src, o.out_pos, o.out_mir,
-                                                                  cursor32.p, (uint2*)h->inc);
-        else if (use_rec)
-            k_tri_scatter<unsigned long long><<<rblocks, kThreads, 0, st>>>((int64_t)recorded, rec, o.out_ptr,
-                                                                            o.out_col, o.out_eid, o.out_src,
-                                                                            o.out_pos, o.out_mir, cursor.p,
-                                                                            (uint2*)h->inc);
-        else if (narrow)
+        if (narrow)
             k_tri_oriented<true, true, unsigned><<<eblocks, kThreads, 0, st>>>(
                 m, o.out_ptr, o.out_col, o.out_eid, o.out_src, o.out_pos, o.out_mir, cursor32.p, (uint2*)h->inc);
         else if (h->adj)
@@ -1379,10 +1435,6 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
                                                                       o.out_src, nullptr, nullptr, cursor.p,
                                                                       (uint2*)h->inc);
         ND_CUDA(cudaGetLastError());
-    }
-    if (rec) {  // stream-ordered: released once the fill has read it
-        cudaFreeAsync(rec, st);
-        rec = nullptr;
     }
     if (h->adj) {
         nd_release(h->mirror, st);  // build only
@@ -1539,7 +1591,10 @@ nd_status nd_write_r_cliques(const nd_incidence* h, int32_t* out_dev, cudaStream
     if (h->num_r == 0) return ND_OK;
     int blocks = nd_blocks_for(h->num_r, kThreads, grid_cap(h) * 2);
     nd_prof_scope ps("r_cliques", st);
-    k_r_cliques<<<blocks, kThreads, 0, st>>>(h->r, h->num_r, h->e_u, h->e_v, h->tri_w, h->tri_e, out_dev);
+    if (h->r == 2 && h->vto_old)
+        k_r_cliques_mapped<<<blocks, kThreads, 0, st>>>(h->num_r, h->e_u, h->e_v, h->vto_old, h->to_old, out_dev);
+    else
+        k_r_cliques<<<blocks, kThreads, 0, st>>>(h->r, h->num_r, h->e_u, h->e_v, h->tri_w, h->tri_e, out_dev);
     ND_CUDA(cudaGetLastError());
     return ND_OK;
 }

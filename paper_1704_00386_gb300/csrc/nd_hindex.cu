@@ -58,6 +58,10 @@ constexpr int kWarpChunk = ND_WARP_CHUNK;
 #define ND_NOTIFY_UNROLL 4  // notification entries in flight per lane ((2,3))
 #endif
 constexpr int kNotifyUnroll = ND_NOTIFY_UNROLL;
+#ifndef ND_RHO_CACHE
+#define ND_RHO_CACHE 1024  // rho values a warp keeps in shared memory for the search passes (0 = none)
+#endif
+constexpr int kRhoCache = ND_RHO_CACHE;
 
 // Work of one pass: rows longer than the CTA threshold are taken one per
 // block from a per-pass counter; all other rows form warp tasks that warps
@@ -241,17 +245,29 @@ __device__ __forceinline__ void kary_bin(unsigned* bins, int32_t r, int lo, int 
 
 // H({rho_j}) clipped to t by one warp, streaming the row: one pass counts
 // rho >= t; if that fails, k-ary search with 256 shared-memory bins per
-// streaming pass (at most 2 passes for t <= 65536).
+// streaming pass (at most 2 passes for t <= 65536).  The counting pass keeps
+// min(rho, t) of the row's first ncache entries in `cache` (16 bits: a warp
+// row has t <= d_s < 65536), so the search passes read them from shared
+// memory instead of gathering them again; only entries past ncache are
+// streamed again.
 template <typename F>
-__device__ __forceinline__ int32_t warp_hindex(const F& rho, int64_t jb, int64_t je, int32_t t, unsigned* bins) {
+__device__ __forceinline__ int32_t warp_hindex(const F& rho, int64_t jb, int64_t je, int32_t t, unsigned* bins,
+                                               uint16_t* cache = nullptr, int ncache = 0) {
     const int lane = threadIdx.x & 31;
     if (t <= 0) return 0;
     int cnt = 0;
+    if (!cache || t > 65535) ncache = 0;
+    const int64_t jc = jb + ncache;  // entries [jb, jc) go to the cache
 #pragma unroll kWarpUnroll
-    for (int64_t j = jb + lane; j < je; j += 32) cnt += (rho(j) >= t);
+    for (int64_t j = jb + lane; j < je; j += 32) {
+        const int32_t r = rho(j);
+        cnt += (r >= t);
+        if (j < jc) cache[j - jb] = (uint16_t)min(r, t);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     if (cnt >= t) return t;
+    __syncwarp();  // the cache is complete
     int lo = cnt, hi = t;
     while (hi - lo > 1) {
         const int span = hi - lo;
@@ -259,7 +275,8 @@ __device__ __forceinline__ int32_t warp_hindex(const F& rho, int64_t jb, int64_t
         const int width = (span + nb - 1) / nb;
         for (int i = lane; i <= 256; i += 32) bins[i] = 0;
         __syncwarp();
-        for (int64_t j = jb + lane; j < je; j += 32) kary_bin(bins, rho(j), lo, hi, width);
+        for (int64_t j = jb + lane; j < jc && j < je; j += 32) kary_bin(bins, (int32_t)cache[j - jb], lo, hi, width);
+        for (int64_t j = jc + lane; j < je; j += 32) kary_bin(bins, rho(j), lo, hi, width);
         __syncwarp();
         int nlo, nhi;
         select_bin(bins, lo, hi, width, nb, &nlo, &nhi);
@@ -271,13 +288,21 @@ __device__ __forceinline__ int32_t warp_hindex(const F& rho, int64_t jb, int64_t
 }
 
 // The same by the whole CTA (the longest rows); warp 0 selects the bin.
+// The first ncache entries are kept in `cache` as for a warp.
 template <typename F>
 __device__ __forceinline__ int32_t cta_hindex(const F& rho, int64_t jb, int64_t je, int32_t t,
-                                              unsigned* bins /* 257 */, int* bounds /* 2 */) {
+                                              unsigned* bins /* 257 */, int* bounds /* 2 */,
+                                              uint16_t* cache = nullptr, int ncache = 0) {
     if (t <= 0) return 0;
     int cnt = 0;
+    if (!cache || t > 65535) ncache = 0;
+    const int64_t jc = jb + ncache;
 #pragma unroll kWarpUnroll
-    for (int64_t j = jb + threadIdx.x; j < je; j += kThreads) cnt += (rho(j) >= t);
+    for (int64_t j = jb + threadIdx.x; j < je; j += kThreads) {
+        const int32_t r = rho(j);
+        cnt += (r >= t);
+        if (j < jc) cache[j - jb] = (uint16_t)min(r, t);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     if ((threadIdx.x & 31) == 0) bins[threadIdx.x >> 5] = (unsigned)cnt;
@@ -298,7 +323,9 @@ __device__ __forceinline__ int32_t cta_hindex(const F& rho, int64_t jb, int64_t 
         const int width = (span + nb - 1) / nb;
         for (int i = threadIdx.x; i <= 256; i += kThreads) bins[i] = 0;
         __syncthreads();
-        for (int64_t j = jb + threadIdx.x; j < je; j += kThreads)
+        for (int64_t j = jb + threadIdx.x; j < jc && j < je; j += kThreads)
+            kary_bin(bins, (int32_t)cache[j - jb], lo, hi, width);
+        for (int64_t j = jc + threadIdx.x; j < je; j += kThreads)
             kary_bin(bins, rho(j), lo, hi, width);
         __syncthreads();
         if (threadIdx.x < 32) {
@@ -500,7 +527,7 @@ __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, 
 // the frontier here (false when the caller has already selected active rows)
 template <int Q, bool AND, bool NOTIFY, bool CHECK = true>
 __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item& it, unsigned* bins,
-                                             unsigned long long& changed, unsigned long long& evals,
+                                             uint16_t* cache, unsigned long long& changed, unsigned long long& evals,
                                              unsigned long long& incs) {
     const int lane = threadIdx.x & 31;
     const uint32_t R = it.R;
@@ -510,7 +537,7 @@ __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item
     // valid tau, which is <= d_s); changes are detected against the stored value
     const int32_t t = min(t0, (int32_t)it.d);
     const int64_t jb = it.jb, je = it.jb + it.d;
-    const int32_t h = warp_hindex(make_rho<Q, !AND>(P), jb, je, t, bins);
+    const int32_t h = warp_hindex(make_rho<Q, !AND>(P), jb, je, t, bins, cache, kRhoCache);
     if (lane == 0) {
         evals++;
         incs += it.d;
@@ -523,7 +550,7 @@ __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item
 // one r-clique per CTA (rows longer than 2048 incidences)
 template <int Q, bool AND, bool NOTIFY>
 __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int64_t last,
-                                        unsigned* bins, int* bounds, unsigned long long& changed,
+                                        unsigned* bins, int* bounds, uint16_t* cache, unsigned long long& changed,
                                         unsigned long long& evals, unsigned long long& incs) {
     for (int64_t i = first; i < last; ++i) {
         const nd_item it = load_item(P.items, i);
@@ -540,7 +567,7 @@ __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int
         else if (Q == 1 && t > kTau16Max)
             h = cta_hindex(Rho<Q, !AND, int32_t>{P.inc, P.tin}, jb, je, t, bins, bounds);
         else
-            h = cta_hindex(make_rho<Q, !AND>(P), jb, je, t, bins, bounds);
+            h = cta_hindex(make_rho<Q, !AND>(P), jb, je, t, bins, bounds, cache, (kThreads / 32) * kRhoCache);
         if (threadIdx.x == 0) {
             evals++;
             incs += it.d;
@@ -675,6 +702,9 @@ __global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS 
     k_pass(SweepParams P) {
     if (P.prev != nullptr && *(volatile const unsigned long long*)P.prev == 0ull) return;  // converged
     __shared__ unsigned bins[kThreads / 32][260];  // k-ary search bins, one set per warp
+    __shared__ uint16_t rho_cache[kThreads / 32][kRhoCache > 0 ? kRhoCache : 1];  // per warp; a CTA row uses all
+    uint16_t* const wcache = kRhoCache > 0 ? rho_cache[threadIdx.x >> 5] : nullptr;
+    uint16_t* const bcache = kRhoCache > 0 ? &rho_cache[0][0] : nullptr;
     __shared__ int bounds[2];
     __shared__ unsigned long long s_chunk;
     unsigned long long changed = 0, evals = 0, incs = 0;
@@ -689,7 +719,7 @@ __global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS 
             const int64_t c = (int64_t)s_chunk;
             __syncthreads();
             if (c >= n3) break;
-            run_cta<Q, AND, NOTIFY>(P, P.lo[3] + c, P.lo[3] + c + 1, bins[0], bounds, changed, evals, incs);
+            run_cta<Q, AND, NOTIFY>(P, P.lo[3] + c, P.lo[3] + c + 1, bins[0], bounds, bcache, changed, evals, incs);
         }
     };
     // AND updates in place, so a row evaluated later in a pass already sees
@@ -733,7 +763,7 @@ __global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS 
                     const int b = __ffs(mm) - 1;
                     mm &= mm - 1;
                     const nd_item it = load_item(P.items, P.lo[2] + t + b);
-                    run_warp_row<Q, AND, NOTIFY, false>(P, it, bins[threadIdx.x >> 5], changed, evals, incs);
+                    run_warp_row<Q, AND, NOTIFY, false>(P, it, bins[threadIdx.x >> 5], wcache, changed, evals, incs);
                 }
             }
             const int64_t t1_lo = max(t, n2), t1_hi = min(te, n2 + t1);
@@ -765,7 +795,7 @@ __global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS 
             while (t < e2) {
                 nd_item nx;
                 if (t + 1 < e2) nx = load_item(P.items, P.lo[2] + t + 1);
-                run_warp_row<Q, AND, NOTIFY>(P, it, bins[threadIdx.x >> 5], changed, evals, incs);
+                run_warp_row<Q, AND, NOTIFY>(P, it, bins[threadIdx.x >> 5], wcache, changed, evals, incs);
                 it = nx;
                 ++t;
             }

@@ -91,8 +91,15 @@ struct nd_incidence {
     // (1,2): vertices relabelled by degree class (nd_relabel_by_degree); rp and
     // col hold the relabelled graph, and results are permuted back at the
     // boundary.  Null when the handle keeps the caller's ids.
-    int32_t* to_new = nullptr;  // [n] caller's id -> internal id
-    int32_t* to_old = nullptr;  // [n] internal id -> caller's id
+    // (2,3): edges relabelled the same way (nd_relabel_truss_graph); to_new /
+    // to_old then map the caller's edge ids to the internal ones and back
+    // (num_r each), and vto_old maps internal vertex ids to the caller's.
+    // c_*: the caller's CSR and split, kept during the build only.
+    int32_t* to_new = nullptr;  // [num_r] caller's r-clique id -> internal id
+    int32_t* to_old = nullptr;  // [num_r] internal r-clique id -> caller's id
+    int32_t* vto_old = nullptr;
+    int64_t *c_rp = nullptr, *c_up = nullptr;
+    int32_t *c_col = nullptr, *c_nlow = nullptr;
     bool adj = false;
     uint32_t* mirror = nullptr;    // [nnz] build only: P(v,u) for the entry P(u,v)
     uint2* e_pos = nullptr;        // [m] (P(x,y), P(y,x)) of edge (x,y), x<y
@@ -189,6 +196,13 @@ void nd_release(void* p, cudaStream_t st);
 // becomes the total).  Uses stream-ordered scratch.
 nd_status nd_scan_i64(int64_t* data, int64_t count, cudaStream_t st);
 
+// stable LSD radix sort (8-bit digits) of keys[0, count) over their low
+// `bits` bits, ping-ponging with alt; *result is whichever holds the sorted
+// keys (nd_normalize.cu).  nd_id_bits(n): bits of the ids 0..n-1 (at least 1).
+nd_status nd_sort_u64(unsigned long long* keys, unsigned long long* alt, int64_t count, int bits,
+                      unsigned long long** result, cudaStream_t st);
+int nd_id_bits(int64_t n);
+
 // build steps (nd_build.cu)
 nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st);
 nd_status nd_build_edges(nd_incidence* h, cudaStream_t st);
@@ -197,6 +211,8 @@ nd_status nd_build_triangles(nd_incidence* h, cudaStream_t st);
 nd_status nd_build_k4_incidence(nd_incidence* h, cudaStream_t st);
 nd_status nd_build_buckets(nd_incidence* h, cudaStream_t st);
 nd_status nd_relabel_by_degree(nd_incidence* h, cudaStream_t st);
+nd_status nd_relabel_truss_graph(nd_incidence* h, cudaStream_t st);
+nd_status nd_relabel_truss_edges(nd_incidence* h, cudaStream_t st);
 // out[idx[i]] = in[i] (scatter) or out[i] = in[idx[i]] (gather), n int32 values on st
 nd_status nd_permute_i32(const int32_t* idx, const int32_t* in, int32_t* out, int64_t n, bool scatter,
                          cudaStream_t st);

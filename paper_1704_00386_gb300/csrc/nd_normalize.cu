@@ -196,7 +196,9 @@ __global__ void k_row_ptr(const unsigned long long* __restrict__ ukeys, int64_t 
     }
 }
 
-int bits_for(int64_t n) {
+}  // namespace
+
+int nd_id_bits(int64_t n) {
     int b = 1;
     while (b < 63 && ((int64_t)1 << b) < n) ++b;
     return b;
@@ -204,8 +206,8 @@ int bits_for(int64_t n) {
 
 // stable LSD radix sort of keys[0, count) over their low `bits` bits; the
 // result is in *result (keys or alt)
-nd_status radix_sort(unsigned long long* keys, unsigned long long* alt, int64_t count, int bits, int sm_count,
-                     unsigned long long** result, cudaStream_t st) {
+nd_status nd_sort_u64(unsigned long long* keys, unsigned long long* alt, int64_t count, int bits,
+                      unsigned long long** result, cudaStream_t st) {
     *result = keys;
     if (count <= 1) return ND_OK;
     const int64_t tiles = (count + kTile - 1) / kTile;
@@ -229,12 +231,9 @@ nd_status radix_sort(unsigned long long* keys, unsigned long long* alt, int64_t 
         a = b;
         b = t;
     }
-    (void)sm_count;
     *result = a;
     return ND_OK;
 }
-
-}  // namespace
 
 extern "C" nd_status nd_normalize(const int64_t* src, const int64_t* dst, int64_t m, int64_t n, int on_device,
                                   int64_t* row_ptr_out, int32_t* col_out, int64_t col_capacity, int64_t* nnz_out,
@@ -248,7 +247,7 @@ extern "C" nd_status nd_normalize(const int64_t* src, const int64_t* dst, int64_
     int dev = 0, sms = 152;
     ND_CUDA(cudaGetDevice(&dev));
     ND_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int bits = bits_for(n);  // ids need `bits` bits; keys 2 * bits
+    const int bits = nd_id_bits(n);  // ids need `bits` bits; keys 2 * bits
     // device copies of host input
     const int64_t *dsrc = src, *ddst = dst;
     nd_tmp<int64_t> hsrc(st), hdst(st);
@@ -282,7 +281,7 @@ extern "C" nd_status nd_normalize(const int64_t* src, const int64_t* dst, int64_
     if (herr) { nd_set_error("a vertex id is outside [0, n)"); return ND_E_INVAL; }
     const int64_t count = (int64_t)hcount;
     unsigned long long* sorted = keys;
-    ND_TRY(radix_sort(keys, alt, count, 2 * bits, sms, &sorted, st));
+    ND_TRY(nd_sort_u64(keys, alt, count, 2 * bits, &sorted, st));
     unsigned long long* ukeys = (sorted == keys) ? (unsigned long long*)alt : (unsigned long long*)keys;
     // first copies -> positions (exclusive scan; pos[count] = number of unique keys)
     nd_tmp<int64_t> pos(st);

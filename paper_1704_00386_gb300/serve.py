@@ -22,12 +22,16 @@ import numpy as np
 from . import nd
 
 
+RELABEL_MIN_VERTICES = 1 << 16   # graphs from this size are renumbered by degree class in the build
+
+
 def footprint_bytes(row_ptr: np.ndarray, col: np.ndarray, r: int) -> int:
     """Upper bound on the device bytes a request needs (graph copy, edge
     arrays, incidence, work items, two tau buffers and frontiers), at the
     build's peak: for (2,3) the incidence is written once and ranked into a
-    second buffer, next to the CSR-slot arrays; for large (1,2) graphs the
-    relabelled CSR sits next to the caller's copy.
+    second buffer, next to the CSR-slot arrays; for large (1,2) and (2,3)
+    graphs the relabelled CSR sits next to the caller's copy, and a large
+    (2,3) graph also sorts 8-byte keys (two buffers) and keeps edge-id maps.
 
     The incidence size is bounded by sum over edges of min(d_u, d_v) (common
     neighbours of an edge) for (2,3), and by that bound times the largest
@@ -49,6 +53,9 @@ def footprint_bytes(row_ptr: np.ndarray, col: np.ndarray, r: int) -> int:
             num_r, inc, q = nnz // 2, tri_bound, 2
             copies = 2
             base += 8 * (nnz // 2) + 4 * nnz + 4 * nnz + nnz // 4  # e_pos, 16-bit copies, reverse slots, frontier
+            if n >= RELABEL_MIN_VERTICES:
+                # relabelled CSR, sort keys and their ping-pong buffer, edge-id maps, vertex map
+                base += 8 * (n + 1) + 4 * nnz + 16 * nnz + nnz // 2 + 8 * (nnz // 2) + 4 * n
         else:
             num_r = tri_bound // 3 + 1
             inc = tri_bound * int(deg.max() if n else 0) // 3
