@@ -47,10 +47,10 @@ UNIT = "updates/s"
 PEEL_SAMPLE_SCALE = 14    # the single-threaded peeling oracle, timed on a bounded sample
 CPU_SND_SECONDS = 10.0    # time budget of the multi-threaded SND passes of the CPU baseline
 # ncu DRAM bytes per incidence of the SND pass (k-truss, q = 2), measured on the
-# current kernel on R-MAT scale 18 (dram__bytes_read.sum + dram__bytes_write.sum
-# = 2.685 GB + 59.1 MB per pass over 247,767,033 incidences); None once the
+# current kernel on R-MAT scale 18, pass 12 (dram__bytes_read.sum + dram__bytes_write.sum
+# = 2.197118 GB + 32.99328 MB per pass over 247,767,033 incidences); None once the
 # kernel changes until it is measured again.
-NCU_SND_TRAFFIC_PER_INCIDENCE = (2.684543e9 + 59.060736e6) / 247767033
+NCU_SND_TRAFFIC_PER_INCIDENCE = (2.197118e9 + 32.99328e6) / 247767033
 
 
 def parse():
@@ -62,11 +62,12 @@ def parse():
     p.add_argument("--workload", default="rmat_s20_ef16")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--mode", choices=["single", "batch", "serve", "otf", "quality"], default="single",
+    p.add_argument("--mode", choices=["single", "batch", "serve", "otf", "quality", "noalloc"], default="single",
                    help="single: one graph per step (default); batch: many graphs as one disjoint "
                         "union vs one graph per launch; serve: Poisson request stream, p50/p99; "
                         "otf: stored incidence vs no-storage passes; quality: Kendall-Tau and "
-                        "accuracy of the early-stopped iterates against kappa")
+                        "accuracy of the early-stopped iterates against kappa; noalloc: the "
+                        "allocation-free k-core entry point against build + SND")
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--requests", type=int, default=192)
     p.add_argument("--no-extras", action="store_true",
@@ -794,8 +795,57 @@ def run_quality(args):
     return 0
 
 
+def run_noalloc(args):
+    """The allocation-free k-core entry point (nd_core_snd_noalloc) against
+    nd_build_incidence(1,2) + nd_snd on the largest graph it accepts, R-MAT
+    scale 20 EF16 (1,048,576 vertices): time per run and per pass."""
+    import torch
+    from paper_1704_00386_gb300 import graphs as G
+    from paper_1704_00386_gb300 import nd
+    torch.cuda.set_device(0)
+    nd.load(build_if_missing=False)
+    n, s, d = G.rmat(20, 16, seed=2)
+    rp, col = G.to_csr(n, s, d)
+    rp_d, col_d = torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=3):
+        best, res = None, None
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        return res, best
+
+    nd.core_snd_noalloc(rp_d[:1], col_d[:0])  # the set-up call (n = 0)
+    (core_a, it_a), ms_a = timed(lambda: nd.core_snd_noalloc(rp_d, col_d))
+
+    def alloc_path():
+        inc = nd.build_incidence(rp_d, col_d, 1, 2)
+        t, it = inc.snd()
+        inc.free()
+        return t, it
+
+    (core_b, it_b), ms_b = timed(alloc_path)
+    inc = nd.build_incidence(rp_d, col_d, 1, 2)
+    _, ms_snd = timed(lambda: inc.snd())
+    inc.free()
+    print(json.dumps({"mode": "noalloc", "n": n, "nnz": int(rp[-1]), "max_degree": int(np.diff(rp).max()),
+                      "passes": it_a, "noalloc_ms": ms_a, "build_plus_snd_ms": ms_b, "snd_only_ms": ms_snd,
+                      "noalloc_ms_per_pass": ms_a / (it_a + 1), "snd_ms_per_pass": ms_snd / (it_b + 1),
+                      "results_identical": bool(torch.equal(core_a, core_b)) and it_a == it_b}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.mode == "noalloc":
+        return run_noalloc(args)
     if args.mode == "otf":
         return run_otf(args)
     if args.mode == "quality":
