@@ -108,6 +108,8 @@ def test_active_ratio_rule(nd, rs):
         if stopped:
             _, evals = inc.last_passes()
             assert evals[-1] < ratio * inc.num_r + (ds == 0).sum() + 1
+        else:  # the run ended by converging: the result is kappa itself
+            np.testing.assert_array_equal(tau, kap)
     tau0, _, _, stopped0 = inc.and_until(0.0)
     assert not stopped0
     np.testing.assert_array_equal(tau0, kap)
