@@ -465,18 +465,12 @@ __global__ void k_orient(int64_t n, const int64_t* __restrict__ rp, const int32_
 #ifndef ND_TRI_MIN_BLOCKS
 #define ND_TRI_MIN_BLOCKS 6  // resident blocks per SM for the triangle count / fill
 #endif
-// nxt (ADJ fill, may be null): the three entries S0 (row uv), S1 (row uw)
-// and S2 (row vw) of a triangle hold each other's edges.  They are linked in
-// a cycle S0 -> S1 -> S2 -> S0: nxt[S] = the next entry, with bit 31 = the
-// half of that entry (0: .x, 1: .y) that refers to S's own edge.  An edge
-// that changes can then reach, from each entry of its own row, the two
-// entries that hold its value (see the inline SND pass).
 template <bool FILL, bool ADJ, typename C = unsigned long long>
 __global__ void __launch_bounds__(kThreads, ND_TRI_MIN_BLOCKS) k_tri_oriented(int64_t m, const int64_t* __restrict__ out_ptr,
                                const int32_t* __restrict__ out_col, const uint32_t* __restrict__ out_eid,
                                const int32_t* __restrict__ out_src, const uint32_t* __restrict__ out_pos,
                                const uint32_t* __restrict__ out_mir, C* __restrict__ ctr,
-                               uint2* __restrict__ inc, uint32_t* __restrict__ nxt = nullptr) {
+                               uint2* __restrict__ inc) {
     const int lane = threadIdx.x & 31;
     for (int64_t k = warp_id_global(); k < m; k += warp_count_global()) {
         const int32_t u = out_src[k], v = out_col[k];
@@ -558,17 +552,9 @@ __global__ void __launch_bounds__(kThreads, ND_TRI_MIN_BLOCKS) k_tri_oriented(in
                             r_uw = make_uint2(e_uv, e_vw);
                             r_vw = make_uint2(e_uv, e_uw);
                         }
-                        const C S0 = s0 + (C)__popc(bal & lanemask_lt());
-                        inc[S0] = r_uv;
+                        inc[s0 + __popc(bal & lanemask_lt())] = r_uv;
                         inc[s_uw] = r_uw;
                         inc[s_vw] = r_vw;
-                        if (ADJ && nxt) {
-                            // S1's .x is P(u,v) iff u < x; S2's .y is P(x,u) iff v < x;
-                            // S0's .y is P(v,w) iff u < v
-                            nxt[S0] = (uint32_t)s_uw | ((u < x ? 0u : 1u) << 31);
-                            nxt[s_uw] = (uint32_t)s_vw | ((v < x ? 1u : 0u) << 31);
-                            nxt[s_vw] = (uint32_t)S0 | ((u < v ? 1u : 0u) << 31);
-                        }
                     }
                 }
             }
@@ -605,23 +591,9 @@ constexpr int kRankWarps = 8;
 #endif
 constexpr int kRankWords = ND_RANK_WORDS;
 
-// with nxt: also move each entry's cycle pointer with it (nxt_dst) and
-// record its new position (perm), for the remapping that follows
-__device__ __forceinline__ void move_entry(const uint2& e, uint2* __restrict__ dst, int64_t from, int64_t to,
-                                           const uint32_t* __restrict__ nxt, uint32_t* __restrict__ nxt_dst,
-                                           uint32_t* __restrict__ perm) {
-    dst[to] = e;
-    if (nxt) {
-        nxt_dst[to] = nxt[from];
-        perm[from] = (uint32_t)to;
-    }
-}
-
 __device__ __forceinline__ void rank_row(const uint2* __restrict__ src, uint2* __restrict__ dst, int64_t jb,
                                          int64_t d, int comp, uint32_t base, int64_t nw,
-                                         uint32_t* __restrict__ bm, uint32_t* __restrict__ pre,
-                                         const uint32_t* __restrict__ nxt, uint32_t* __restrict__ nxt_dst,
-                                         uint32_t* __restrict__ perm) {
+                                         uint32_t* __restrict__ bm, uint32_t* __restrict__ pre) {
     const int lane = threadIdx.x & 31;
     if (d <= 32) {
         uint2 e = make_uint2(0u, 0u);
@@ -632,7 +604,7 @@ __device__ __forceinline__ void rank_row(const uint2* __restrict__ src, uint2* _
         }
         int rank = 0;
         for (int o = 0; o < d; ++o) rank += (__shfl_sync(kFull, key, o) < key);
-        if (lane < d) move_entry(e, dst, jb + lane, jb + rank, nxt, nxt_dst, perm);
+        if (lane < d) dst[jb + rank] = e;
         return;
     }
     for (int64_t w = lane; w < nw; w += 32) bm[w] = 0u;
@@ -661,18 +633,9 @@ __device__ __forceinline__ void rank_row(const uint2* __restrict__ src, uint2* _
         const uint2 e = src[j];
         const uint32_t k = (comp ? e.y : e.x) - base;
         const uint32_t rank = pre[k >> 5] + (uint32_t)__popc(bm[k >> 5] & ((1u << (k & 31)) - 1u));
-        move_entry(e, dst, j, jb + rank, nxt, nxt_dst, perm);
+        dst[jb + rank] = e;
     }
     __syncwarp();
-}
-
-// after ranking: every cycle pointer named an entry by its old position
-__global__ void k_remap_nxt(int64_t M, uint32_t* __restrict__ nxt, const uint32_t* __restrict__ perm) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < M; k += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t w = nxt[k];
-        const uint32_t i = w & 0x7fffffffu;
-        nxt[k] = (i < M ? perm[i] : 0x7fffffffu) | (w & 0x80000000u);  // out of range only on a fault
-    }
 }
 
 // BIG = false: every row, bits in shared memory; rows that need more than
@@ -684,8 +647,7 @@ __global__ void __launch_bounds__(32 * kRankWarps)
 k_row_rank(int64_t N, const int64_t* __restrict__ inc_ptr, const int32_t* __restrict__ e_u,
            const int32_t* __restrict__ e_v, const int64_t* __restrict__ rp, const uint2* __restrict__ src,
            uint2* __restrict__ dst, uint32_t* __restrict__ over, unsigned long long* __restrict__ over_ctr,
-           uint32_t* __restrict__ scratch, int64_t scratch_words, const uint32_t* __restrict__ nxt,
-           uint32_t* __restrict__ nxt_dst, uint32_t* __restrict__ perm) {
+           uint32_t* __restrict__ scratch, int64_t scratch_words) {
     extern __shared__ uint32_t rank_smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -702,7 +664,7 @@ k_row_rank(int64_t N, const int64_t* __restrict__ inc_ptr, const int32_t* __rest
         const int64_t R = BIG ? (int64_t)over[i] : i;
         const int64_t jb = inc_ptr[R], d = inc_ptr[R + 1] - jb;
         if (d <= 1) {
-            if (d == 1 && lane == 0) move_entry(src[jb], dst, jb, jb, nxt, nxt_dst, perm);
+            if (d == 1 && lane == 0) dst[jb] = src[jb];
             continue;
         }
         const int32_t x = e_u[R], y = e_v[R];
@@ -717,7 +679,7 @@ k_row_rank(int64_t N, const int64_t* __restrict__ inc_ptr, const int32_t* __rest
             }
             continue;
         }
-        rank_row(src, dst, jb, d, comp, base, nw, bm, pre, nxt, nxt_dst, perm);
+        rank_row(src, dst, jb, d, comp, base, nw, bm, pre);
     }
 }
 
@@ -1386,21 +1348,6 @@ static nd_status sort_tri_rows(nd_incidence* h, cudaStream_t st) {
     nd_status rc = over.alloc(N);
     if (rc == ND_OK) rc = over_ctr.alloc(2);
     if (rc != ND_OK) { cudaFreeAsync(dst, st); return rc; }
-    // the triangle cycle pointers move with their entries and are renamed
-    // after; without room for that, the inline SND mode is given up
-    uint32_t* nxt_dst = nullptr;
-    nd_tmp<uint32_t> perm(st);
-    if (h->nxt) {
-        bool ok = cudaMallocAsync((void**)&nxt_dst, sizeof(uint32_t) * (size_t)M, st) == cudaSuccess;
-        if (ok) ok = perm.alloc(M) == ND_OK;
-        if (!ok) {
-            cudaGetLastError();
-            if (nxt_dst) cudaFreeAsync(nxt_dst, st);
-            nxt_dst = nullptr;
-            nd_release(h->nxt, st);
-            h->nxt = nullptr;
-        }
-    }
     ND_CUDA(cudaMemsetAsync(over_ctr, 0, sizeof(unsigned long long) * 2, st));
     const size_t smem = sizeof(uint32_t) * 2 * kRankWords * kRankWarps;
     ND_CUDA(cudaFuncSetAttribute(k_row_rank<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1409,7 +1356,7 @@ static nd_status sort_tri_rows(nd_incidence* h, cudaStream_t st) {
         const int blocks = nd_blocks_for(N * 32, 32 * kRankWarps, grid_cap(h) * 8);
         k_row_rank<false><<<blocks, 32 * kRankWarps, smem, st>>>(N, h->inc_ptr, h->e_u, h->e_v, h->rp,
                                                                   (const uint2*)h->inc, dst, over, over_ctr,
-                                                                  nullptr, 0, h->nxt, nxt_dst, perm.p);
+                                                                  nullptr, 0);
         ND_CUDA(cudaGetLastError());
     }
     unsigned long long hc[2] = {0, 0};
@@ -1423,19 +1370,12 @@ static nd_status sort_tri_rows(nd_incidence* h, cudaStream_t st) {
         nd_prof_scope ps("row_rank", st);
         k_row_rank<true><<<warps / kRankWarps, 32 * kRankWarps, 0, st>>>(
             N, h->inc_ptr, h->e_u, h->e_v, h->rp, (const uint2*)h->inc, dst, over, over_ctr, scratch,
-            (int64_t)hc[1], h->nxt, nxt_dst, perm.p);
+            (int64_t)hc[1]);
         ND_CUDA(cudaGetLastError());
     }
     nd_release(h->inc, st);
     h->inc = reinterpret_cast<uint32_t*>(dst);
     h->rows_sorted = true;
-    if (h->nxt) {
-        k_remap_nxt<<<nd_blocks_for(M, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(M, nxt_dst, perm);
-        ND_CUDA(cudaGetLastError());
-        nd_release(h->nxt, st);
-        h->nxt = nxt_dst;
-        h->bytes += (int64_t)sizeof(uint32_t) * M;
-    }
     return ND_OK;
 }
 
@@ -1471,16 +1411,6 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
         return nd_alloc((void**)&h->inc, 16, st, h);
     }
     ND_TRY(nd_alloc((void**)&h->inc, sizeof(uint32_t) * 2 * (h->num_inc > 0 ? h->num_inc : 1), st, h));
-    // the triangle cycle pointers of the inline SND mode (entry indices in 31
-    // bits); without room for them (or past 2^31 incidences) there is no
-    // inline mode, which changes no result
-    if (h->adj && h->num_inc > 0 && h->num_inc < ((int64_t)1 << 31)) {
-        if (nd_alloc((void**)&h->nxt, sizeof(uint32_t) * h->num_inc, st, h) != ND_OK) {
-            cudaGetLastError();
-            nd_set_error("");
-            h->nxt = nullptr;
-        }
-    }
     if (h->num_inc > 0) {
         nd_tmp<unsigned long long> cursor(st);
         nd_tmp<unsigned> cursor32(st);
@@ -1496,12 +1426,10 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
         nd_prof_scope ps("tri_fill", st);
         if (narrow)
             k_tri_oriented<true, true, unsigned><<<eblocks, kThreads, 0, st>>>(
-                m, o.out_ptr, o.out_col, o.out_eid, o.out_src, o.out_pos, o.out_mir, cursor32.p, (uint2*)h->inc,
-                h->nxt);
+                m, o.out_ptr, o.out_col, o.out_eid, o.out_src, o.out_pos, o.out_mir, cursor32.p, (uint2*)h->inc);
         else if (h->adj)
             k_tri_oriented<true, true><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid, o.out_src,
-                                                                     o.out_pos, o.out_mir, cursor.p, (uint2*)h->inc,
-                                                                     h->nxt);
+                                                                     o.out_pos, o.out_mir, cursor.p, (uint2*)h->inc);
         else
             k_tri_oriented<true, false><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid,
                                                                       o.out_src, nullptr, nullptr, cursor.p,

@@ -58,12 +58,6 @@ constexpr int kWarpChunk = ND_WARP_CHUNK;
 #define ND_NOTIFY_UNROLL 4  // notification entries in flight per lane ((2,3))
 #endif
 constexpr int kNotifyUnroll = ND_NOTIFY_UNROLL;
-#ifndef ND_INLINE_PROBE
-#define ND_INLINE_PROBE 8   // SND passes between checks for the switch to the inline mode
-#endif
-#ifndef ND_INLINE_PCT
-#define ND_INLINE_PCT 10    // switch once a pass's pushes would be below this % of the incidences
-#endif
 #ifndef ND_RHO_CACHE
 #define ND_RHO_CACHE 1024  // rho values a warp keeps in shared memory for the search passes (0 = none)
 #endif
@@ -97,16 +91,8 @@ struct SweepParams {
     const uint32_t* cur;  // AND + notification: frontier read in this pass
     uint32_t* next;       // and the frontier written for the next pass
     const uint32_t* members;  // PartialAnd: only members are notified (null = everyone)
-    // inline SND mode ((2,3)): vin[j] = 16-bit tau of entry j's two edges,
-    // nxt = the triangle cycle pointers, clist = the edges this pass changed
-    const uint32_t* __restrict__ vin;
-    uint16_t* vin16;  // the same array, written by the pushes
-    const uint32_t* __restrict__ nxt;
-    uint32_t* clist;
-    int64_t num_inc;
     unsigned long long* ctr;         // this pass: [0] changed, [1] evaluated, [2] next CTA row,
-                                     // [3] incidences of the evaluated rows, [4] next warp chunk,
-                                     // [5] length of clist, [6] incidences of the changed rows
+                                     // [3] incidences of the evaluated rows, [4] next warp chunk
     const unsigned long long* prev;  // previous pass (null on the first)
 };
 
@@ -176,24 +162,13 @@ struct RhoExact2 {
 
 constexpr int32_t kTau16Max = 65535;
 
-// (2,3) inline mode: rho of entry j from the copies kept in the entry itself
-// (a 4-byte stream, no gather); saturated at 65535 like the gather copy
-struct RhoInline {
-    const uint32_t* __restrict__ vin;
-    __device__ __forceinline__ int32_t operator()(int64_t j) const {
-        const uint32_t v = __ldcs(vin + j);
-        return (int32_t)min(v & 0xffffu, v >> 16);
-    }
-};
-
 // the gather of a row whose tau is at most 65535: the 16-bit copy for (1,2)
 // and (2,3).  (3,4) gathers int32 tau directly: its rows are not ordered, and
 // the 16-bit copy measured 3% slower there (config 3) against 6% faster for
-// a scale-24 k-core.  INL: the inline copies of the (2,3) entries.
-template <int Q, bool RO, bool INL = false>
+// a scale-24 k-core.
+template <int Q, bool RO>
 __device__ __forceinline__ auto make_rho(const SweepParams& P) {
-    if constexpr (INL && Q == 2) return RhoInline{P.vin};
-    else if constexpr (Q == 3) return Rho<3, RO, int32_t>{P.inc, P.tin};
+    if constexpr (Q == 3) return Rho<3, RO, int32_t>{P.inc, P.tin};
     else return Rho<Q, RO, uint16_t>{P.inc, P.gin};
 }
 
@@ -367,12 +342,9 @@ __device__ __forceinline__ int32_t cta_hindex(const F& rho, int64_t jb, int64_t 
 }
 
 // the new tau of R; (2,3) also writes it to both CSR entries of the edge
-// (not in the inline mode, which reads no gather copy: the pushes update the
-// inline copies instead)
-template <int Q, bool INL = false>
+template <int Q>
 __device__ __forceinline__ void store_tau(const SweepParams& P, uint32_t R, int32_t h) {
     P.tout[R] = h;
-    if (INL) return;
     const uint16_t v = (uint16_t)min(h, kTau16Max);
     if (Q == 2) {
         const uint2 ep = __ldg(P.epos + R);
@@ -513,21 +485,6 @@ __device__ __forceinline__ void notify_entry(const SweepParams& P, int64_t j, in
     }
 }
 
-// bookkeeping of one evaluated row (by one lane): counters, and in the
-// inline mode the list of changed edges that the push step walks
-template <bool INL>
-__device__ __forceinline__ void count_row(const SweepParams& P, uint32_t R, uint32_t d, bool chg,
-                                          unsigned long long& changed, unsigned long long& evals,
-                                          unsigned long long& incs, unsigned long long& chincs) {
-    evals++;
-    incs += d;
-    if (chg) {
-        changed++;
-        chincs += d;
-        if (INL) P.clist[atomicAdd(P.ctr + 5, 1ull)] = R;
-    }
-}
-
 __device__ __forceinline__ nd_item load_item(const nd_item* __restrict__ items, int64_t i) {
     longlong2 v = __ldg(reinterpret_cast<const longlong2*>(items) + i);
     nd_item it;
@@ -539,10 +496,10 @@ __device__ __forceinline__ nd_item load_item(const nd_item* __restrict__ items, 
 
 // work items [first, first + 32/G): one r-clique per group of G lanes of the
 // calling warp
-template <int Q, int G, int C, bool AND, bool NOTIFY, bool INL = false>
+template <int Q, int G, int C, bool AND, bool NOTIFY>
 __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, int64_t last,
                                            unsigned long long& changed, unsigned long long& evals,
-                                           unsigned long long& incs, unsigned long long& chincs) {
+                                           unsigned long long& incs) {
     auto g = cg::tiled_partition<G>(cg::this_thread_block());
     const int lane = g.thread_rank();
     // the group's index inside its warp, from the lane id (G divides 32)
@@ -556,20 +513,22 @@ __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, 
     // H <= d_s, so tau is clipped at d_s for the search (a no-op for every
     // valid tau, which is <= d_s); changes are detected against the stored value
     const int32_t t = min(t0, (int32_t)it.d);
-    const int32_t h = group_hindex<G, C>(g, make_rho<Q, !AND, INL>(P), jb, je, t);
+    const int32_t h = group_hindex<G, C>(g, make_rho<Q, !AND>(P), jb, je, t);
     if (lane == 0) {
-        count_row<INL>(P, R, it.d, h != t0, changed, evals, incs, chincs);
-        if (!AND || h != t0) store_tau<Q, INL>(P, R, h);
+        evals++;
+        incs += it.d;
+        if (h != t0) changed++;
+        if (!AND || h != t0) store_tau<Q>(P, R, h);
     }
     if (AND && NOTIFY && h != t0) notify_row<Q>(P, jb, je, h, lane, G);
 }
 
 // one r-clique per warp (rows of the warp bucket), streamed.  CHECK: test
 // the frontier here (false when the caller has already selected active rows)
-template <int Q, bool AND, bool NOTIFY, bool CHECK = true, bool INL = false>
+template <int Q, bool AND, bool NOTIFY, bool CHECK = true>
 __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item& it, unsigned* bins,
                                              uint16_t* cache, unsigned long long& changed, unsigned long long& evals,
-                                             unsigned long long& incs, unsigned long long& chincs) {
+                                             unsigned long long& incs) {
     const int lane = threadIdx.x & 31;
     const uint32_t R = it.R;
     if (CHECK && AND && NOTIFY && !in_frontier<Q>(P, R)) return;
@@ -578,20 +537,21 @@ __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item
     // valid tau, which is <= d_s); changes are detected against the stored value
     const int32_t t = min(t0, (int32_t)it.d);
     const int64_t jb = it.jb, je = it.jb + it.d;
-    const int32_t h = warp_hindex(make_rho<Q, !AND, INL>(P), jb, je, t, bins, cache, kRhoCache);
+    const int32_t h = warp_hindex(make_rho<Q, !AND>(P), jb, je, t, bins, cache, kRhoCache);
     if (lane == 0) {
-        count_row<INL>(P, R, it.d, h != t0, changed, evals, incs, chincs);
-        if (!AND || h != t0) store_tau<Q, INL>(P, R, h);
+        evals++;
+        incs += it.d;
+        if (h != t0) changed++;
+        if (!AND || h != t0) store_tau<Q>(P, R, h);
     }
     if (AND && NOTIFY && h != t0) notify_row<Q>(P, jb, je, h, lane, 32);
 }
 
 // one r-clique per CTA (rows longer than 2048 incidences)
-template <int Q, bool AND, bool NOTIFY, bool INL = false>
+template <int Q, bool AND, bool NOTIFY>
 __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int64_t last,
                                         unsigned* bins, int* bounds, uint16_t* cache, unsigned long long& changed,
-                                        unsigned long long& evals, unsigned long long& incs,
-                                        unsigned long long& chincs) {
+                                        unsigned long long& evals, unsigned long long& incs) {
     for (int64_t i = first; i < last; ++i) {
         const nd_item it = load_item(P.items, i);
         const uint32_t R = it.R;
@@ -607,10 +567,12 @@ __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int
         else if (Q == 1 && t > kTau16Max)
             h = cta_hindex(Rho<Q, !AND, int32_t>{P.inc, P.tin}, jb, je, t, bins, bounds);
         else
-            h = cta_hindex(make_rho<Q, !AND, INL>(P), jb, je, t, bins, bounds, cache, (kThreads / 32) * kRhoCache);
+            h = cta_hindex(make_rho<Q, !AND>(P), jb, je, t, bins, bounds, cache, (kThreads / 32) * kRhoCache);
         if (threadIdx.x == 0) {
-            count_row<INL>(P, R, it.d, h != t0, changed, evals, incs, chincs);
-            if (!AND || h != t0) store_tau<Q, INL>(P, R, h);
+            evals++;
+            incs += it.d;
+            if (h != t0) changed++;
+            if (!AND || h != t0) store_tau<Q>(P, R, h);
         }
         if (AND && NOTIFY && h != t0) notify_row<Q>(P, jb, je, h, threadIdx.x, kThreads);
         __syncthreads();
@@ -680,7 +642,7 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int k) {
 template <int Q, int G, int C>
 __device__ __forceinline__ void run_groups_active(const SweepParams& P, int64_t a, unsigned mask,
                                                   unsigned long long& changed, unsigned long long& evals,
-                                                  unsigned long long& incs, unsigned long long& chincs) {
+                                                  unsigned long long& incs) {
     constexpr int NG = 32 / G;
     auto g = cg::tiled_partition<G>(cg::this_thread_block());
     const int lane = threadIdx.x & 31;
@@ -698,8 +660,12 @@ __device__ __forceinline__ void run_groups_active(const SweepParams& P, int64_t 
             jb = it.jb;
             h = group_hindex<G, C>(g, make_rho<Q, false>(P), jb, jb + it.d, t);
             if (g.thread_rank() == 0) {
-                count_row<false>(P, it.R, it.d, h != t0, changed, evals, incs, chincs);
-                if (h != t0) store_tau<Q>(P, it.R, h);
+                evals++;
+                incs += it.d;
+                if (h != t0) {
+                    changed++;
+                    store_tau<Q>(P, it.R, h);
+                }
             }
             dn = (h != t0) ? (int32_t)it.d : 0;
         }
@@ -731,8 +697,7 @@ __device__ __forceinline__ void run_groups_active(const SweepParams& P, int64_t 
 #ifndef ND_AND_MIN_BLOCKS
 #define ND_AND_MIN_BLOCKS 6   // the same for the AND pass with notification
 #endif
-// INL: the (2,3) SND pass that reads the inline copies instead of gathering
-template <int Q, bool AND, bool NOTIFY, bool INL = false>
+template <int Q, bool AND, bool NOTIFY>
 __global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS : ND_PASS_MIN_BLOCKS)
     k_pass(SweepParams P) {
     if (P.prev != nullptr && *(volatile const unsigned long long*)P.prev == 0ull) return;  // converged
@@ -742,7 +707,7 @@ __global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS 
     uint16_t* const bcache = kRhoCache > 0 ? &rho_cache[0][0] : nullptr;
     __shared__ int bounds[2];
     __shared__ unsigned long long s_chunk;
-    unsigned long long changed = 0, evals = 0, incs = 0, chincs = 0;
+    unsigned long long changed = 0, evals = 0, incs = 0;
     // phase 1: rows longer than the CTA threshold, one per block at a time,
     // taken from a per-pass counter (longest rows first)
     const int64_t n3 = P.hi[3] - P.lo[3];
@@ -754,8 +719,7 @@ __global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS 
             const int64_t c = (int64_t)s_chunk;
             __syncthreads();
             if (c >= n3) break;
-            run_cta<Q, AND, NOTIFY, INL>(P, P.lo[3] + c, P.lo[3] + c + 1, bins[0], bounds, bcache, changed, evals, incs,
-                                         chincs);
+            run_cta<Q, AND, NOTIFY>(P, P.lo[3] + c, P.lo[3] + c + 1, bins[0], bounds, bcache, changed, evals, incs);
         }
     };
     // AND updates in place, so a row evaluated later in a pass already sees
@@ -799,8 +763,7 @@ __global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS 
                     const int b = __ffs(mm) - 1;
                     mm &= mm - 1;
                     const nd_item it = load_item(P.items, P.lo[2] + t + b);
-                    run_warp_row<Q, AND, NOTIFY, false>(P, it, bins[threadIdx.x >> 5], wcache, changed, evals, incs,
-                                                        chincs);
+                    run_warp_row<Q, AND, NOTIFY, false>(P, it, bins[threadIdx.x >> 5], wcache, changed, evals, incs);
                 }
             }
             const int64_t t1_lo = max(t, n2), t1_hi = min(te, n2 + t1);
@@ -811,7 +774,7 @@ __global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS 
                 active_masks<Q, W1>(P, a, b, mk);
 #pragma unroll
                 for (int w = 0; w < W1; ++w)
-                    if (mk[w]) run_groups_active<Q, 8, 8>(P, a + 32 * w, mk[w], changed, evals, incs, chincs);
+                    if (mk[w]) run_groups_active<Q, 8, 8>(P, a + 32 * w, mk[w], changed, evals, incs);
             }
             const int64_t t0_lo = max(t, n2 + t1);
             if (t0_lo < te) {
@@ -821,7 +784,7 @@ __global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS 
                 active_masks<Q, W0>(P, a, b, mk);
 #pragma unroll
                 for (int w = 0; w < W0; ++w)
-                    if (mk[w]) run_groups_active<Q, 4, 2>(P, a + 32 * w, mk[w], changed, evals, incs, chincs);
+                    if (mk[w]) run_groups_active<Q, 4, 2>(P, a + 32 * w, mk[w], changed, evals, incs);
             }
             continue;
         }
@@ -832,8 +795,7 @@ __global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS 
             while (t < e2) {
                 nd_item nx;
                 if (t + 1 < e2) nx = load_item(P.items, P.lo[2] + t + 1);
-                run_warp_row<Q, AND, NOTIFY, true, INL>(P, it, bins[threadIdx.x >> 5], wcache, changed, evals, incs,
-                                                        chincs);
+                run_warp_row<Q, AND, NOTIFY>(P, it, bins[threadIdx.x >> 5], wcache, changed, evals, incs);
                 it = nx;
                 ++t;
             }
@@ -841,71 +803,30 @@ __global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS 
         for (; t < te; ++t) {
             if (t < n2 + t1) {
                 const int64_t first = P.lo[1] + 4 * (t - n2);
-                run_groups<Q, 8, 8, AND, NOTIFY, INL>(P, first, min(first + 4, P.hi[1]), changed, evals, incs, chincs);
+                run_groups<Q, 8, 8, AND, NOTIFY>(P, first, min(first + 4, P.hi[1]), changed, evals, incs);
             } else {
                 const int64_t first = P.lo[0] + 8 * (t - n2 - t1);
-                run_groups<Q, 4, 2, AND, NOTIFY, INL>(P, first, min(first + 8, P.hi[0]), changed, evals, incs, chincs);
+                run_groups<Q, 4, 2, AND, NOTIFY>(P, first, min(first + 8, P.hi[0]), changed, evals, incs);
             }
         }
     }
     if (kShortFirst) cta_phase();
-    __shared__ unsigned long long s_ch[kThreads / 32], s_ev[kThreads / 32], s_in[kThreads / 32],
-        s_ci[kThreads / 32];
+    __shared__ unsigned long long s_ch[kThreads / 32], s_ev[kThreads / 32], s_in[kThreads / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         changed += __shfl_xor_sync(0xffffffffu, changed, o);
         evals += __shfl_xor_sync(0xffffffffu, evals, o);
         incs += __shfl_xor_sync(0xffffffffu, incs, o);
-        chincs += __shfl_xor_sync(0xffffffffu, chincs, o);
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) { s_ch[wid] = changed; s_ev[wid] = evals; s_in[wid] = incs; s_ci[wid] = chincs; }
+    if (lane == 0) { s_ch[wid] = changed; s_ev[wid] = evals; s_in[wid] = incs; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long a = 0, e = 0, c = 0, ci = 0;
-        for (int w = 0; w < kThreads / 32; ++w) { a += s_ch[w]; e += s_ev[w]; c += s_in[w]; ci += s_ci[w]; }
+        unsigned long long a = 0, e = 0, c = 0;
+        for (int w = 0; w < kThreads / 32; ++w) { a += s_ch[w]; e += s_ev[w]; c += s_in[w]; }
         if (a) atomicAdd(P.ctr, a);
         if (e) atomicAdd(P.ctr + 1, e);
         if (c) atomicAdd(P.ctr + 3, c);
-        if (ci) atomicAdd(P.ctr + 6, ci);
-    }
-}
-
-// Inline SND mode, after pass t: every edge R the pass changed writes its new
-// value (saturated to 16 bits) into the two inline copies held by each of
-// its triangles' other entries.  From entry j of R's own row, the cycle
-// pointer gives the next entry t1 of the triangle and the half of it that
-// refers to R; t1's pointer gives the third entry t2, whose other half (the
-// one not referring to t1's edge) refers to R.  One warp per changed edge;
-// the next pass reads the copies, so they hold tau_t as Alg. 2 needs.
-__global__ void __launch_bounds__(kThreads) k_push(SweepParams P) {
-    if (P.prev != nullptr && *(volatile const unsigned long long*)P.prev == 0ull) return;  // converged
-    const unsigned long long count = *(volatile const unsigned long long*)(P.ctr + 5);
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = warp; i < (int64_t)count; i += warps) {
-        const uint32_t R = P.clist[i];
-        const int64_t jb = P.inc_ptr[R], je = P.inc_ptr[R + 1];
-        const uint16_t v = (uint16_t)min(P.tout[R], kTau16Max);
-        for (int64_t j = jb + lane; j < je; j += 32) {
-            const uint32_t w1 = __ldg(P.nxt + j);
-            const uint32_t t1 = w1 & 0x7fffffffu;
-            if ((int64_t)t1 >= P.num_inc) continue;  // cannot happen for a built handle
-            const uint32_t w2 = __ldg(P.nxt + t1);
-            const uint32_t t2 = w2 & 0x7fffffffu;
-            P.vin16[2 * (int64_t)t1 + (w1 >> 31)] = v;
-            if ((int64_t)t2 < P.num_inc) P.vin16[2 * (int64_t)t2 + (1u - (w2 >> 31))] = v;
-        }
-    }
-}
-
-// switch to the inline mode: every entry's copies from the gather copy
-__global__ void k_init_inline(int64_t M, const uint2* __restrict__ inc, const uint16_t* __restrict__ tg,
-                              uint32_t* __restrict__ vin) {
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M; j += (int64_t)gridDim.x * blockDim.x) {
-        const uint2 id = inc[j];
-        vin[j] = (uint32_t)tg[id.x] | ((uint32_t)tg[id.y] << 16);
     }
 }
 
@@ -1190,7 +1111,7 @@ SweepParams pass_params(const nd_incidence* h, int mode, const SweepParams& P0, 
 // capture) so that it also serves the legacy default stream.  On any
 // failure the handle falls back to ordinary launches for this kind.
 void make_batch_graph(nd_incidence* h, int mode, int kind, const SweepParams& P0, int grid, pass_fn fn,
-                      int64_t words, int gi, pass_fn push = nullptr, int push_grid = 0) {
+                      int64_t words) {
     const int base = (kind == 2) ? ND_BATCH : 0;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ex = nullptr;
@@ -1232,14 +1153,6 @@ void make_batch_graph(nd_incidence* h, int mode, int kind, const SweepParams& P0
         cudaGraphNode_t n = nullptr;
         ok = cudaGraphAddKernelNode(&n, g, &last, 1, &kp) == cudaSuccess;
         last = n;
-        if (ok && push) {
-            cudaKernelNodeParams pp = kp;
-            pp.func = (void*)push;
-            pp.gridDim = dim3(push_grid);
-            cudaGraphNode_t n2 = nullptr;
-            ok = cudaGraphAddKernelNode(&n2, g, &last, 1, &pp) == cudaSuccess;
-            last = n2;
-        }
     }
     if (ok) {
         cudaGraphNode_t n = nullptr;
@@ -1251,10 +1164,10 @@ void make_batch_graph(nd_incidence* h, int mode, int kind, const SweepParams& P0
     if (g) cudaGraphDestroy(g);
     if (!ok) {
         cudaGetLastError();  // clear, and use ordinary launches instead
-        h->pass_graph_failed[gi][kind] = true;
+        h->pass_graph_failed[mode][kind] = true;
         return;
     }
-    h->pass_graph[gi][kind] = ex;
+    h->pass_graph[mode][kind] = ex;
 }
 
 }  // namespace
@@ -1369,11 +1282,6 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
     P.ev = h->e_v;
     P.items = h->items;
     P.members = members;
-    P.vin = nullptr;
-    P.vin16 = nullptr;
-    P.nxt = h->nxt;
-    P.clist = nullptr;
-    P.num_inc = h->num_inc;
     plan_buckets(h, P);
     pass_fn fn = pick(h, mode);
     const int64_t units = pass_units(h, P);
@@ -1387,18 +1295,6 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
     bool over_bound = false;
     if ((int64_t)max_passes > bound) { max_passes = (int32_t)bound; over_bound = true; }
     const char* pname = mode == ND_SND ? "snd_pass" : (mode == ND_AND ? "and_pass" : "and_nn_pass");
-    // SND of a stored (2,3) handle may switch to the inline mode once few
-    // edges change: it runs batches of kProbe passes until the pushes the
-    // last pass would have needed (2 per incidence of a changed edge) fall
-    // below kInlineFrac of the incidences, then fills the inline copies and
-    // runs full batches of inline passes, each followed by its push
-    constexpr int kProbe = ND_INLINE_PROBE;
-    constexpr double kInlineFrac = ND_INLINE_PCT / 100.0;
-    const bool may_inline = mode == ND_SND && h->nxt && h->q == 2 && !h->otf && h->num_inc > 0 && !h->inline_failed;
-    bool inl = false;
-    pass_fn fn_inl = k_pass<2, false, false, true>;
-    const int grid_inl = may_inline ? pass_grid(h, (const void*)fn_inl, units) : 0;
-    const int grid_push = (h->sm_count > 0 ? h->sm_count : 152) * 4;
     int32_t pass = 0;
     int64_t batch = 0;
     int last_slot = -1;  // counter slot of the last pass enqueued
@@ -1406,32 +1302,28 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
     int32_t last_written = 0;  // SND: index of the buffer holding the newest tau
     while (!done && pass < max_passes) {
         // batch b uses counter slots [base, base + nb) of one half of the
-        // ring; its first pass reads the counters of the pass before it.
-        // Every batch starts at an even pass (all batch lengths but the last
-        // are even), which the graphs' buffer parities rely on.
+        // ring; its first pass reads the counters of the pass enqueued before
+        // it, and every pass takes its buffers by the parity of its index in
+        // the run (batches of one pass, for the stopping rule, included)
         const int32_t start = pass;
         const int base = (int)(batch & 1) * kBatch;
         int nb = kBatch;
-        if (may_inline && !inl) nb = kProbe;
         if (nb > max_passes - pass) nb = max_passes - pass;
         if (stop_active > 0.0) nb = 1;  // the stopping rule looks at every pass
         const int kind = batch == 0 ? 0 : ((batch & 1) ? 2 : 1);
-        const int gi = inl ? 3 : mode;
-        pass_fn f = inl ? fn_inl : fn;
-        const int g = inl ? grid_inl : grid;
         bool launched = false;
         // graphs hold the plain parameters; runs with members or a stopping rule launch directly
-        if (nb == kBatch && g > 0 && !members && (start & 1) == 0 && !h->pass_graph_failed[gi][kind]) {
-            if (!h->pass_graph[gi][kind])
-                make_batch_graph(h, mode, kind, P, g, f, words, gi, inl ? k_push : nullptr, grid_push);
-            if (h->pass_graph[gi][kind]) {
+        if (nb == kBatch && grid > 0 && !members && (start & 1) == 0 && !h->pass_graph_failed[mode][kind]) {
+            if (!h->pass_graph[mode][kind])
+                make_batch_graph(h, mode, kind, P, grid, fn, words);
+            if (h->pass_graph[mode][kind]) {
                 // the graph's first pass reads the last slot of the other half
                 const int want = (base ^ ND_BATCH) + ND_BATCH - 1;
                 if (kind != 0 && last_slot != want)
                     ND_CUDA(cudaMemcpyAsync(h->counters + ND_SLOT * want, h->counters + ND_SLOT * last_slot,
                                             sizeof(unsigned long long) * ND_SLOT, cudaMemcpyDeviceToDevice, st));
                 nd_prof_scope ps(pname, st, kBatch);
-                ND_CUDA(cudaGraphLaunch(h->pass_graph[gi][kind], st));
+                ND_CUDA(cudaGraphLaunch(h->pass_graph[mode][kind], st));
                 launched = true;
                 pass += kBatch;
             }
@@ -1442,14 +1334,10 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
                 SweepParams Pk = pass_params(h, mode, P, base + k, k > 0 ? base + k - 1 : last_slot, pass & 1);
                 if (mode == ND_AND)
                     ND_CUDA(cudaMemsetAsync(Pk.next, 0, sizeof(uint32_t) * words, st));
-                if (g > 0) {
+                if (grid > 0) {
                     nd_prof_scope ps(pname, st);
-                    f<<<g, kThreads, 0, st>>>(Pk);
+                    fn<<<grid, kThreads, 0, st>>>(Pk);
                     ND_CUDA(cudaGetLastError());
-                    if (inl) {
-                        k_push<<<grid_push, kThreads, 0, st>>>(Pk);
-                        ND_CUDA(cudaGetLastError());
-                    }
                 }
             }
             ND_CUDA(cudaMemcpyAsync(h->h_counters + ND_SLOT * base, h->counters + ND_SLOT * base,
@@ -1479,31 +1367,6 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
                 opts->stopped = true;
                 done = true;
                 break;
-            }
-        }
-        if (may_inline && !inl && !done && pass < max_passes) {
-            const double pushes = 2.0 * (double)h->h_counters[ND_SLOT * last_slot + 6];
-            if (pushes < kInlineFrac * (double)h->num_inc) {
-                // the copies are filled from the gather copy the next pass would
-                // read (it holds tau of the pass just done); without room for
-                // them the run stays in the gather mode
-                const int64_t M = h->num_inc;
-                bool ok = true;
-                if (!h->vin) ok = nd_alloc((void**)&h->vin, sizeof(uint32_t) * M, st, h) == ND_OK;
-                if (ok && !h->clist) ok = nd_alloc((void**)&h->clist, sizeof(uint32_t) * N, st, h) == ND_OK;
-                if (ok) {
-                    nd_prof_scope ps("init_inline", st);
-                    k_init_inline<<<nd_blocks_for(M, kThreads, h->sm_count * 8), kThreads, 0, st>>>(
-                        M, reinterpret_cast<const uint2*>(h->inc), h->tg[pass & 1], h->vin);
-                    ND_CUDA(cudaGetLastError());
-                    P.vin = h->vin;
-                    P.vin16 = reinterpret_cast<uint16_t*>(h->vin);
-                    P.clist = h->clist;
-                    inl = true;
-                } else {
-                    cudaGetLastError();
-                    h->inline_failed = true;
-                }
             }
         }
         ++batch;

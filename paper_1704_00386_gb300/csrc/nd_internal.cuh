@@ -105,13 +105,6 @@ struct nd_incidence {
     uint2* e_pos = nullptr;        // [m] (P(x,y), P(y,x)) of edge (x,y), x<y
     uint16_t* tg[2] = {nullptr, nullptr};  // [nnz] gather copies of tau by CSR position
     bool rows_sorted = false;      // rows ordered by w (else in fill order)
-    // inline SND mode ((2,3), stored): nxt[M] links the three entries of each
-    // triangle (see k_tri_oriented); vin[M] holds, per entry, 16-bit copies of
-    // the tau of its two edges; clist[N_R] lists the edges a pass changed
-    uint32_t* nxt = nullptr;
-    uint32_t* vin = nullptr;
-    uint32_t* clist = nullptr;
-    bool inline_failed = false;  // no room for the inline copies: gather mode only
     // (2,3) with no stored incidence (ND_BUILD_ON_THE_FLY): inc is empty and
     // every pass finds the triangles of each edge again
     bool otf = false;
@@ -132,11 +125,9 @@ struct nd_incidence {
     cudaStream_t last_stream = 0;  // stream of the latest call on this handle
     // instantiated CUDA graphs of a full batch of passes, per mode (SND, AND,
     // AND-nn) and batch kind (first, even, odd); built on first use
-    // (index 3: SND in the inline mode, each pass followed by its push)
-    cudaGraphExec_t pass_graph[4][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr},
-                                        {nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
-    bool pass_graph_failed[4][3] = {{false, false, false}, {false, false, false}, {false, false, false},
-                                    {false, false, false}};
+    cudaGraphExec_t pass_graph[3][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr},
+                                        {nullptr, nullptr, nullptr}};
+    bool pass_graph_failed[3][3] = {{false, false, false}, {false, false, false}, {false, false, false}};
     // set while a call uses the iteration state (nd_claim); a second call
     // meanwhile gets ND_E_BUSY
     std::atomic<int> busy{0};
@@ -167,7 +158,7 @@ struct nd_claim {
 
 // passes are enqueued in batches of ND_BATCH; the per-pass counters (ND_SLOT
 // u64 each) live in two halves of ND_BATCH slots used by alternate batches
-enum { ND_BATCH = 16, ND_RING = 2 * ND_BATCH, ND_SLOT = 8 };
+enum { ND_BATCH = 16, ND_RING = 2 * ND_BATCH, ND_SLOT = 6 };
 
 // wait for a stream with a time limit (ND_E_TIMEOUT past it)
 nd_status nd_wait(cudaStream_t st);
