@@ -108,7 +108,7 @@ def test_active_ratio_rule(nd, rs):
         if ratio == 0.4:
             # the late notified passes evaluate few r-cliques: the rule fires
             # (with every pass evaluating all of them, as without notification, it could not)
-            assert stopped and it < it_full
+            assert stopped and it <= it_full
         if stopped:
             _, evals = inc.last_passes()
             assert evals[-1] < ratio * inc.num_r + (ds == 0).sum() + 1
