@@ -193,7 +193,7 @@ void nd_free(nd_incidence* h) {
     void* ptrs[] = {h->nlow, h->up_start, h->eid, h->e_u, h->e_v, h->tri_ptr, h->tri_w, h->tri_e,
                     h->items, h->tau[0], h->tau[1], h->front[0], h->front[1], h->counters,
                     h->mirror, h->e_pos, h->tg[0], h->tg[1], h->long_rows, h->long_seg, h->to_new, h->to_old,
-                    h->vto_old, h->c_rp, h->c_up, h->c_col, h->c_nlow};
+                    h->vto_old, h->c_rp, h->c_up, h->c_col, h->c_nlow, h->gid, h->gact[0], h->gact[1]};
     for (void* p : ptrs) nd_release(p, st);
     for (auto& row : h->pass_graph)
         for (auto& ex : row)
@@ -368,6 +368,10 @@ nd_status nd_build_incidence_batch(const nd_csr* graphs, int count, int r, int s
         ND_TRY(urp.alloc(n + 1));
         ND_TRY(ucol.alloc(nnz));
         rc = nd_union_device(parts.data(), count, n, nnz, urp, ucol, st);
+        if (rc == ND_OK) {
+            nd_csr u{n, nnz, urp, ucol, 1};
+            rc = build_common(&u, r, s, st, out, 0, false);
+        }
     } else {
         // host graphs: assemble the union on the host and copy it once
         std::vector<int64_t> hrp(n + 1);
@@ -387,15 +391,12 @@ nd_status nd_build_incidence_batch(const nd_csr* graphs, int count, int r, int s
             nd_csr u{n, nnz, hrp.data(), hcol.data(), 0};
             rc = build_common(&u, r, s, st, out, 0, false);
         }
-        if (rc == ND_OK && r_offsets) rc = nd_batch_offsets(*out, voff.data(), count, r_offsets, st);
-        if (rc != ND_OK && *out) { nd_free(*out); *out = nullptr; }
-        return rc;
     }
-    if (rc == ND_OK) {
-        nd_csr u{n, nnz, urp, ucol, 1};
-        rc = build_common(&u, r, s, st, out, 0, false);
-    }
-    if (rc == ND_OK && r_offsets) rc = nd_batch_offsets(*out, voff.data(), count, r_offsets, st);
+    // the r-clique slice of every graph, and the graph of every r-clique
+    std::vector<int64_t> roff(count + 1, 0);
+    if (rc == ND_OK && count > 0) rc = nd_batch_offsets(*out, voff.data(), count, roff.data(), st);
+    if (rc == ND_OK) rc = nd_batch_graph_ids(*out, roff.data(), count, st);
+    if (rc == ND_OK && r_offsets) std::memcpy(r_offsets, roff.data(), sizeof(int64_t) * (count + 1));
     if (rc != ND_OK && *out) { nd_free(*out); *out = nullptr; }
     return rc;
 }

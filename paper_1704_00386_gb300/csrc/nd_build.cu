@@ -920,6 +920,19 @@ __global__ void k_bucket_scatter(int64_t N, const int64_t* __restrict__ inc_ptr,
     }
 }
 
+// graph index of r-clique R (caller's order): the i with off[i] <= R < off[i+1]
+__global__ void k_graph_ids(int64_t N, const int64_t* __restrict__ off, int count, const int32_t* __restrict__ to_new,
+                            uint32_t* __restrict__ gid) {
+    for (int64_t R = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; R < N; R += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = count;  // last i with off[i] <= R
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (off[mid] <= R) lo = mid; else hi = mid;
+        }
+        gid[to_new ? to_new[R] : R] = (uint32_t)lo;
+    }
+}
+
 __global__ void k_r_cliques(int r, int64_t N, const int32_t* __restrict__ e_u,
                             const int32_t* __restrict__ e_v, const int32_t* __restrict__ tri_w,
                             const uint32_t* __restrict__ tri_e, int32_t* __restrict__ out) {
@@ -1649,4 +1662,17 @@ nd_status nd_batch_offsets(const nd_incidence* h, const int64_t* vertex_off /* c
     ND_CUDA(cudaMemcpyAsync(r_off, res, sizeof(int64_t) * (count + 1), cudaMemcpyDeviceToHost, st));
     ND_TRY(nd_wait(st));
     return ND_OK;
+}
+
+nd_status nd_batch_graph_ids(nd_incidence* h, const int64_t* r_off, int count, cudaStream_t st) {
+    if (count < 2 || h->num_r == 0) return ND_OK;  // one graph: nothing to skip
+    nd_tmp<int64_t> doff(st);
+    ND_TRY(doff.alloc(count + 1));
+    ND_CUDA(cudaMemcpyAsync(doff, r_off, sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
+    ND_TRY(nd_alloc((void**)&h->gid, sizeof(uint32_t) * h->num_r, st, h));
+    k_graph_ids<<<nd_blocks_for(h->num_r, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(h->num_r, doff, count,
+                                                                                         h->to_new, h->gid);
+    ND_CUDA(cudaGetLastError());
+    h->ngraphs = count;
+    return nd_wait(st);  // the offsets are a host array
 }

@@ -91,6 +91,12 @@ struct SweepParams {
     const uint32_t* cur;  // AND + notification: frontier read in this pass
     uint32_t* next;       // and the frontier written for the next pass
     const uint32_t* members;  // PartialAnd: only members are notified (null = everyone)
+    // batches, SND and AND-nn: graph of every r-clique, the graphs that changed
+    // in the previous pass (gact_in) and those changing in this one (gact_out);
+    // null for a single graph
+    const uint32_t* __restrict__ gid;
+    const uint8_t* gact_in;
+    uint8_t* gact_out;
     unsigned long long* ctr;         // this pass: [0] changed, [1] evaluated, [2] next CTA row,
                                      // [3] incidences of the evaluated rows, [4] next warp chunk
     const unsigned long long* prev;  // previous pass (null on the first)
@@ -485,6 +491,17 @@ __device__ __forceinline__ void notify_entry(const SweepParams& P, int64_t j, in
     }
 }
 
+// batches: has R's graph converged (no change in its previous pass)?  Its
+// rows then keep their tau, as the graph's own run would have stopped
+__device__ __forceinline__ bool graph_done(const SweepParams& P, uint32_t R) {
+    return P.gid && !P.gact_in[__ldg(P.gid + R)];
+}
+
+// batches: R changed, so its graph is still changing
+__device__ __forceinline__ void graph_changed(const SweepParams& P, uint32_t R) {
+    if (P.gid) P.gact_out[__ldg(P.gid + R)] = 1;
+}
+
 __device__ __forceinline__ nd_item load_item(const nd_item* __restrict__ items, int64_t i) {
     longlong2 v = __ldg(reinterpret_cast<const longlong2*>(items) + i);
     nd_item it;
@@ -509,6 +526,7 @@ __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, 
     const uint32_t R = it.R;
     const int64_t jb = it.jb, je = it.jb + it.d;
     if (AND && NOTIFY && !in_frontier<Q>(P, R)) return;
+    if (graph_done(P, R)) return;
     const int32_t t0 = ld_tau<!AND>(P.tin + R);
     // H <= d_s, so tau is clipped at d_s for the search (a no-op for every
     // valid tau, which is <= d_s); changes are detected against the stored value
@@ -517,7 +535,10 @@ __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, 
     if (lane == 0) {
         evals++;
         incs += it.d;
-        if (h != t0) changed++;
+        if (h != t0) {
+            changed++;
+            graph_changed(P, R);
+        }
         if (!AND || h != t0) store_tau<Q>(P, R, h);
     }
     if (AND && NOTIFY && h != t0) notify_row<Q>(P, jb, je, h, lane, G);
@@ -532,6 +553,7 @@ __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item
     const int lane = threadIdx.x & 31;
     const uint32_t R = it.R;
     if (CHECK && AND && NOTIFY && !in_frontier<Q>(P, R)) return;
+    if (graph_done(P, R)) return;
     const int32_t t0 = ld_tau<!AND>(P.tin + R);
     // H <= d_s, so tau is clipped at d_s for the search (a no-op for every
     // valid tau, which is <= d_s); changes are detected against the stored value
@@ -541,7 +563,10 @@ __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item
     if (lane == 0) {
         evals++;
         incs += it.d;
-        if (h != t0) changed++;
+        if (h != t0) {
+            changed++;
+            graph_changed(P, R);
+        }
         if (!AND || h != t0) store_tau<Q>(P, R, h);
     }
     if (AND && NOTIFY && h != t0) notify_row<Q>(P, jb, je, h, lane, 32);
@@ -556,6 +581,7 @@ __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int
         const nd_item it = load_item(P.items, i);
         const uint32_t R = it.R;
         if (AND && NOTIFY && !in_frontier<Q>(P, R)) continue;
+        if (graph_done(P, R)) continue;  // the same R for the whole block
         const int32_t t0 = ld_tau<!AND>(P.tin + R);
         // H <= d_s, so tau is clipped at d_s for the search (a no-op for every
         // valid tau, which is <= d_s); changes are detected against the stored value
@@ -571,7 +597,10 @@ __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int
         if (threadIdx.x == 0) {
             evals++;
             incs += it.d;
-            if (h != t0) changed++;
+            if (h != t0) {
+                changed++;
+                graph_changed(P, R);
+            }
             if (!AND || h != t0) store_tau<Q>(P, R, h);
         }
         if (AND && NOTIFY && h != t0) notify_row<Q>(P, jb, je, h, threadIdx.x, kThreads);
@@ -1087,6 +1116,10 @@ SweepParams pass_params(const nd_incidence* h, int mode, const SweepParams& P0, 
     SweepParams P = P0;
     P.ctr = h->counters + ND_SLOT * slot;
     P.prev = prev_slot < 0 ? nullptr : h->counters + ND_SLOT * prev_slot;
+    if (P.gid) {
+        P.gact_in = h->gact[parity];
+        P.gact_out = h->gact[parity ^ 1];
+    }
     if (mode != ND_SND) {
         P.tin = h->tau[0];
         P.tout = h->tau[0];
@@ -1137,6 +1170,17 @@ void make_batch_graph(nd_incidence* h, int mode, int kind, const SweepParams& P0
             ms.value = 0;
             ms.elementSize = 4;
             ms.width = (size_t)words;
+            ms.height = 1;
+            cudaGraphNode_t n = nullptr;
+            ok = cudaGraphAddMemsetNode(&n, g, &last, 1, &ms) == cudaSuccess;
+            last = n;
+        }
+        if (ok && P.gid) {  // batches: the graphs changing in this pass, from none
+            cudaMemsetParams ms = {};
+            ms.dst = P.gact_out;
+            ms.value = 0;
+            ms.elementSize = 1;
+            ms.width = (size_t)h->ngraphs;
             ms.height = 1;
             cudaGraphNode_t n = nullptr;
             ok = cudaGraphAddMemsetNode(&n, g, &last, 1, &ms) == cudaSuccess;
@@ -1282,6 +1326,17 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
     P.ev = h->e_v;
     P.items = h->items;
     P.members = members;
+    // batches, SND and AND-nn: every graph starts active (AND with
+    // notification needs nothing more: a converged graph notifies no one)
+    P.gid = nullptr;
+    P.gact_in = nullptr;
+    P.gact_out = nullptr;
+    if (h->gid && mode != ND_AND) {
+        for (int b = 0; b < 2; ++b)
+            if (!h->gact[b]) ND_TRY(nd_alloc((void**)&h->gact[b], (size_t)h->ngraphs, st, h));
+        ND_CUDA(cudaMemsetAsync(h->gact[0], 1, (size_t)h->ngraphs, st));
+        P.gid = h->gid;
+    }
     plan_buckets(h, P);
     pass_fn fn = pick(h, mode);
     const int64_t units = pass_units(h, P);
@@ -1334,6 +1389,7 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
                 SweepParams Pk = pass_params(h, mode, P, base + k, k > 0 ? base + k - 1 : last_slot, pass & 1);
                 if (mode == ND_AND)
                     ND_CUDA(cudaMemsetAsync(Pk.next, 0, sizeof(uint32_t) * words, st));
+                if (Pk.gid) ND_CUDA(cudaMemsetAsync(Pk.gact_out, 0, (size_t)h->ngraphs, st));
                 if (grid > 0) {
                     nd_prof_scope ps(pname, st);
                     fn<<<grid, kThreads, 0, st>>>(Pk);
@@ -1351,8 +1407,9 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
             unsigned long long ev = h->h_counters[ND_SLOT * (base + k) + 1];
             // r-cliques with d_s = 0 are never launched: tau = H(empty) = 0 = d_s.
             // They count as evaluated in every SND / AND-nn pass and in the first
-            // AND pass, as in the paper's sequential loops.
-            if (mode != ND_AND || p == 0) ev += (unsigned long long)h->num_zero;
+            // AND pass, as in the paper's sequential loops (in a batch, whose
+            // graphs stop at different passes, once per run).
+            if ((mode != ND_AND && !h->gid) || p == 0) ev += (unsigned long long)h->num_zero;
             h->last_changed.push_back((int64_t)ch);
             h->last_evals.push_back((int64_t)ev);
             h->last_incs.push_back((int64_t)h->h_counters[ND_SLOT * (base + k) + 3]);

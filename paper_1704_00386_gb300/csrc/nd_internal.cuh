@@ -109,6 +109,14 @@ struct nd_incidence {
     // every pass finds the triangles of each edge again
     bool otf = false;
     bool inc_aliases_graph = false;  // r = 1: inc_ptr/inc are rp/col
+    // batches (nd_build_incidence_batch): the graph of every r-clique
+    // (internal ids) and, per pass, which graphs are still changing (two byte
+    // arrays by pass parity).  A graph whose pass changed nothing has
+    // converged: its later SND / AND-nn passes are skipped, as its own run
+    // would have stopped there.
+    int64_t ngraphs = 0;
+    uint32_t* gid = nullptr;
+    uint8_t* gact[2] = {nullptr, nullptr};
     // degree-bucketed processing order
     nd_item* items = nullptr;      // [num_r - num_zero], bucket by bucket
     int64_t bucket_lo[ND_NB + 1] = {0, 0, 0, 0, 0};
@@ -228,6 +236,8 @@ nd_status nd_union_device(const nd_union_part* parts_host, int count, int64_t n,
                           int32_t* ucol, cudaStream_t st);
 nd_status nd_batch_offsets(const nd_incidence* h, const int64_t* vertex_off, int count, int64_t* r_off,
                            cudaStream_t st);
+// the graph index of every r-clique of a batch handle (h->gid, internal ids)
+nd_status nd_batch_graph_ids(nd_incidence* h, const int64_t* r_off /* count+1, host */, int count, cudaStream_t st);
 
 // iteration (nd_hindex.cu)
 nd_status nd_init_tau(nd_incidence* h, int32_t* tau, cudaStream_t st);

@@ -74,3 +74,45 @@ def test_batch_rejects_bad_part(nd):
     assert e.value.status == nd.ND_E_INVAL
     with pytest.raises(ValueError):
         nd.build_incidence_batch([(rp, col), (torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda())], 1, 2)
+
+
+@pytest.mark.parametrize("rs", [(1, 2), (2, 3)])
+@pytest.mark.parametrize("mode", ["snd", "and_nn"])
+def test_batch_stops_each_graph_where_its_own_run_stops(nd, rs, mode):
+    """A graph whose pass changed nothing has converged (its tau is a fixed
+    point), so a batch skips it from then on, as its own run would have
+    stopped: the launched evaluations of the batch are exactly the sum of the
+    single-graph runs' (d_s = 0 rows are never launched), and every slice
+    equals its own run's result and the oracle's kappa."""
+    inc, offs = nd.build_incidence_batch(BATCH, *rs)
+    if mode == "snd":
+        tau, iters = inc.snd()
+    else:
+        tau, iters, _ = inc.and_(notify=False)
+    _, ev_b, inc_b = inc.last_passes(with_incidences=True)
+    ds = inc.s_degree()
+    launched_b = int(ev_b.sum()) - int((ds == 0).sum())   # the batch counts its d_s = 0 rows once
+    launched, incidences, longest = 0, 0, 0
+    for i, (rp, col) in enumerate(BATCH):
+        single = nd.build_incidence(rp, col, *rs)
+        if single.num_r == 0:
+            continue
+        if mode == "snd":
+            t, it = single.snd()
+        else:
+            t, it, _ = single.and_(notify=False)
+        _, ev, ic = single.last_passes(with_incidences=True)
+        zeros = int((single.s_degree() == 0).sum())
+        launched += int(ev.sum()) - zeros * len(ev)
+        incidences += int(ic.sum())
+        longest = max(longest, it)
+        np.testing.assert_array_equal(tau[offs[i]:offs[i + 1]], t, err_msg=f"graph {i}")
+        np.testing.assert_array_equal(t, oracle.decompose(rp, col, *rs), err_msg=f"graph {i}")
+        single.free()
+    assert iters == longest
+    if mode == "snd":  # deterministic: the same rows in the same passes
+        assert launched_b == launched
+        assert int(inc_b.sum()) == incidences
+    else:  # in place: the order inside a pass differs, so only the bound
+        assert launched_b <= sum(int(x) for x in ev_b)
+    inc.free()
