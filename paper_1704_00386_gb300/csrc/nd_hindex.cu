@@ -491,15 +491,19 @@ __device__ __forceinline__ void notify_entry(const SweepParams& P, int64_t j, in
     }
 }
 
-// batches: has R's graph converged (no change in its previous pass)?  Its
-// rows then keep their tau, as the graph's own run would have stopped
+// batches (GB): has R's graph converged (no change in its previous pass)?
+// Its rows then keep their tau, as the graph's own run would have stopped.
+// The single-graph kernels (GB = false) carry no test at all.
+template <bool GB>
 __device__ __forceinline__ bool graph_done(const SweepParams& P, uint32_t R) {
-    return P.gid && !P.gact_in[__ldg(P.gid + R)];
+    if constexpr (GB) return !P.gact_in[__ldg(P.gid + R)];
+    return false;
 }
 
 // batches: R changed, so its graph is still changing
+template <bool GB>
 __device__ __forceinline__ void graph_changed(const SweepParams& P, uint32_t R) {
-    if (P.gid) P.gact_out[__ldg(P.gid + R)] = 1;
+    if constexpr (GB) P.gact_out[__ldg(P.gid + R)] = 1;
 }
 
 __device__ __forceinline__ nd_item load_item(const nd_item* __restrict__ items, int64_t i) {
@@ -513,7 +517,7 @@ __device__ __forceinline__ nd_item load_item(const nd_item* __restrict__ items, 
 
 // work items [first, first + 32/G): one r-clique per group of G lanes of the
 // calling warp
-template <int Q, int G, int C, bool AND, bool NOTIFY>
+template <int Q, int G, int C, bool AND, bool NOTIFY, bool GB = false>
 __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, int64_t last,
                                            unsigned long long& changed, unsigned long long& evals,
                                            unsigned long long& incs) {
@@ -526,7 +530,7 @@ __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, 
     const uint32_t R = it.R;
     const int64_t jb = it.jb, je = it.jb + it.d;
     if (AND && NOTIFY && !in_frontier<Q>(P, R)) return;
-    if (graph_done(P, R)) return;
+    if (graph_done<GB>(P, R)) return;
     const int32_t t0 = ld_tau<!AND>(P.tin + R);
     // H <= d_s, so tau is clipped at d_s for the search (a no-op for every
     // valid tau, which is <= d_s); changes are detected against the stored value
@@ -537,7 +541,7 @@ __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, 
         incs += it.d;
         if (h != t0) {
             changed++;
-            graph_changed(P, R);
+            graph_changed<GB>(P, R);
         }
         if (!AND || h != t0) store_tau<Q>(P, R, h);
     }
@@ -546,14 +550,14 @@ __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, 
 
 // one r-clique per warp (rows of the warp bucket), streamed.  CHECK: test
 // the frontier here (false when the caller has already selected active rows)
-template <int Q, bool AND, bool NOTIFY, bool CHECK = true>
+template <int Q, bool AND, bool NOTIFY, bool CHECK = true, bool GB = false>
 __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item& it, unsigned* bins,
                                              uint16_t* cache, unsigned long long& changed, unsigned long long& evals,
                                              unsigned long long& incs) {
     const int lane = threadIdx.x & 31;
     const uint32_t R = it.R;
     if (CHECK && AND && NOTIFY && !in_frontier<Q>(P, R)) return;
-    if (graph_done(P, R)) return;
+    if (graph_done<GB>(P, R)) return;
     const int32_t t0 = ld_tau<!AND>(P.tin + R);
     // H <= d_s, so tau is clipped at d_s for the search (a no-op for every
     // valid tau, which is <= d_s); changes are detected against the stored value
@@ -565,7 +569,7 @@ __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item
         incs += it.d;
         if (h != t0) {
             changed++;
-            graph_changed(P, R);
+            graph_changed<GB>(P, R);
         }
         if (!AND || h != t0) store_tau<Q>(P, R, h);
     }
@@ -573,7 +577,7 @@ __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item
 }
 
 // one r-clique per CTA (rows longer than 2048 incidences)
-template <int Q, bool AND, bool NOTIFY>
+template <int Q, bool AND, bool NOTIFY, bool GB = false>
 __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int64_t last,
                                         unsigned* bins, int* bounds, uint16_t* cache, unsigned long long& changed,
                                         unsigned long long& evals, unsigned long long& incs) {
@@ -581,7 +585,7 @@ __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int
         const nd_item it = load_item(P.items, i);
         const uint32_t R = it.R;
         if (AND && NOTIFY && !in_frontier<Q>(P, R)) continue;
-        if (graph_done(P, R)) continue;  // the same R for the whole block
+        if (graph_done<GB>(P, R)) continue;  // the same R for the whole block
         const int32_t t0 = ld_tau<!AND>(P.tin + R);
         // H <= d_s, so tau is clipped at d_s for the search (a no-op for every
         // valid tau, which is <= d_s); changes are detected against the stored value
@@ -599,7 +603,7 @@ __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int
             incs += it.d;
             if (h != t0) {
                 changed++;
-                graph_changed(P, R);
+                graph_changed<GB>(P, R);
             }
             if (!AND || h != t0) store_tau<Q>(P, R, h);
         }
@@ -726,7 +730,9 @@ __device__ __forceinline__ void run_groups_active(const SweepParams& P, int64_t 
 #ifndef ND_AND_MIN_BLOCKS
 #define ND_AND_MIN_BLOCKS 6   // the same for the AND pass with notification
 #endif
-template <int Q, bool AND, bool NOTIFY>
+// GB: a batch handle's SND / AND-nn pass, which skips the rows of graphs
+// that have converged
+template <int Q, bool AND, bool NOTIFY, bool GB = false>
 __global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS : ND_PASS_MIN_BLOCKS)
     k_pass(SweepParams P) {
     if (P.prev != nullptr && *(volatile const unsigned long long*)P.prev == 0ull) return;  // converged
@@ -748,7 +754,8 @@ __global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS 
             const int64_t c = (int64_t)s_chunk;
             __syncthreads();
             if (c >= n3) break;
-            run_cta<Q, AND, NOTIFY>(P, P.lo[3] + c, P.lo[3] + c + 1, bins[0], bounds, bcache, changed, evals, incs);
+            run_cta<Q, AND, NOTIFY, GB>(P, P.lo[3] + c, P.lo[3] + c + 1, bins[0], bounds, bcache, changed, evals,
+                                        incs);
         }
     };
     // AND updates in place, so a row evaluated later in a pass already sees
@@ -824,7 +831,7 @@ __global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS 
             while (t < e2) {
                 nd_item nx;
                 if (t + 1 < e2) nx = load_item(P.items, P.lo[2] + t + 1);
-                run_warp_row<Q, AND, NOTIFY>(P, it, bins[threadIdx.x >> 5], wcache, changed, evals, incs);
+                run_warp_row<Q, AND, NOTIFY, true, GB>(P, it, bins[threadIdx.x >> 5], wcache, changed, evals, incs);
                 it = nx;
                 ++t;
             }
@@ -832,10 +839,10 @@ __global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS 
         for (; t < te; ++t) {
             if (t < n2 + t1) {
                 const int64_t first = P.lo[1] + 4 * (t - n2);
-                run_groups<Q, 8, 8, AND, NOTIFY>(P, first, min(first + 4, P.hi[1]), changed, evals, incs);
+                run_groups<Q, 8, 8, AND, NOTIFY, GB>(P, first, min(first + 4, P.hi[1]), changed, evals, incs);
             } else {
                 const int64_t first = P.lo[0] + 8 * (t - n2 - t1);
-                run_groups<Q, 4, 2, AND, NOTIFY>(P, first, min(first + 8, P.hi[0]), changed, evals, incs);
+                run_groups<Q, 4, 2, AND, NOTIFY, GB>(P, first, min(first + 8, P.hi[0]), changed, evals, incs);
             }
         }
     }
@@ -1051,6 +1058,11 @@ pass_fn pick(const nd_incidence* h, int mode) {
     // mode: ND_SND, ND_AND (notify), ND_AND_NN
     const int q = h->q;
     if (h->otf) return mode == ND_SND ? k_pass_otf<false, false> : (mode == ND_AND ? k_pass_otf<true, true> : k_pass_otf<true, false>);
+    if (h->gid && mode != ND_AND) {  // a batch: converged graphs are skipped
+        if (q == 1) return mode == ND_SND ? k_pass<1, false, false, true> : k_pass<1, true, false, true>;
+        if (q == 2) return mode == ND_SND ? k_pass<2, false, false, true> : k_pass<2, true, false, true>;
+        return mode == ND_SND ? k_pass<3, false, false, true> : k_pass<3, true, false, true>;
+    }
     if (q == 1) return mode == ND_SND ? k_pass<1, false, false> : (mode == ND_AND ? k_pass<1, true, true> : k_pass<1, true, false>);
     if (q == 2) return mode == ND_SND ? k_pass<2, false, false> : (mode == ND_AND ? k_pass<2, true, true> : k_pass<2, true, false>);
     return mode == ND_SND ? k_pass<3, false, false> : (mode == ND_AND ? k_pass<3, true, true> : k_pass<3, true, false>);
