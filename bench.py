@@ -645,7 +645,10 @@ def batch_measure(count: int, steps: int = 1, autotune: bool = False):
             thr, _ = inc.autotune(passes=2)
             inc.free()
         batched()                                 # warm-up
+        nd.prof_enable(True)
         (ev_b, (tb, offs)), ms_b = timed(batched)
+        prof = nd.prof_read()
+        nd.prof_enable(False)
         ms_bs = [ms_b]
         for _ in range(max(0, steps - 1)):
             _, ms = timed(batched)
@@ -660,7 +663,8 @@ def batch_measure(count: int, steps: int = 1, autotune: bool = False):
             "plain_ms": ms_p, "plain_updates_per_s": ev_p / (ms_p / 1e3),
             "plain_graphs_per_s": len(dev) / (ms_p / 1e3),
             "speedup": ms_p / ms_b, "results_identical": bool(same),
-            "thresholds": list(thr) if thr else None}
+            "thresholds": list(thr) if thr else None,
+            "batched_kernels_ms": {k: round(v[1], 2) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]}}
     return out
 
 
