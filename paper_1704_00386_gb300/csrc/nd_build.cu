@@ -56,19 +56,15 @@ __device__ __forceinline__ int64_t warp_count_global() {
 // search.
 // the checks of entries [pb, pe) of row u (which starts at b), one entry per
 // lane: the count of entries below the diagonal and whether any check failed
-// search = 0: the symmetry is checked afterwards by a sort (large k-core
-// graphs, which need no reverse entries), so no entry searches
 __device__ __forceinline__ void validate_entries(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
                                                  const int32_t* __restrict__ col, int64_t u, int64_t b, int64_t pb,
-                                                 int64_t pe, uint32_t* __restrict__ mirror, int& low, bool& rowbad,
-                                                 int search) {
+                                                 int64_t pe, uint32_t* __restrict__ mirror, int& low, bool& rowbad) {
     const int lane = threadIdx.x & 31;
     for (int64_t p = pb + lane; p < pe; p += 32) {
         int32_t v = col[p];
         if (v < 0 || v >= n || v == u) { rowbad = true; continue; }
         if (p > b && col[p - 1] >= v) rowbad = true;
         low += (v < u);
-        if (!search) continue;
         // only entries above the diagonal look for their reverse: the host
         // then checks 2m == nnz, i.e. as many entries below the diagonal
         // as above, so with every one above matched (injectively, distinct
@@ -136,7 +132,7 @@ __device__ __forceinline__ void long_segment(int64_t s, const int32_t* __restric
 __global__ void k_validate_split(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
                                  const int32_t* __restrict__ col, int32_t* __restrict__ nlow,
                                  int64_t* __restrict__ upcnt, int* __restrict__ err,
-                                 uint32_t* __restrict__ mirror, int search) {
+                                 uint32_t* __restrict__ mirror) {
     const int lane = threadIdx.x & 31;
     for (int64_t u = warp_id_global(); u < n; u += warp_count_global()) {
         int64_t b = rp[u], e = rp[u + 1];
@@ -151,7 +147,7 @@ __global__ void k_validate_split(int64_t n, int64_t nnz, const int64_t* __restri
         }
         int low = 0;
         bool rowbad = false;
-        validate_entries(n, nnz, rp, col, u, b, b, e, mirror, low, rowbad, search);
+        validate_entries(n, nnz, rp, col, u, b, b, e, mirror, low, rowbad);
         if (lane == 0) {
             nlow[u] = low;
             upcnt[u] = (e - b) - low;
@@ -165,14 +161,14 @@ __global__ void k_validate_long(int64_t n, int64_t nnz, const int64_t* __restric
                                 const int32_t* __restrict__ col, const int32_t* __restrict__ rows,
                                 const int64_t* __restrict__ seg_off, int64_t count, int64_t segs,
                                 int32_t* __restrict__ nlow, int64_t* __restrict__ upcnt, int* __restrict__ err,
-                                uint32_t* __restrict__ mirror, int search) {
+                                uint32_t* __restrict__ mirror) {
     const int lane = threadIdx.x & 31;
     for (int64_t sg = warp_id_global(); sg < segs; sg += warp_count_global()) {
         int64_t u, b, pb, pe;
         long_segment(sg, rows, seg_off, count, rp, u, b, pb, pe);
         int low = 0;
         bool rowbad = false;
-        validate_entries(n, nnz, rp, col, u, b, pb, pe, mirror, low, rowbad, search);
+        validate_entries(n, nnz, rp, col, u, b, pb, pe, mirror, low, rowbad);
         if (lane == 0) {
             atomicAdd(nlow + u, low);
             atomicAdd(reinterpret_cast<unsigned long long*>(upcnt + u), (unsigned long long)((pe - pb) - low));
@@ -350,65 +346,6 @@ __global__ void k_r_cliques_mapped(int64_t N, const int32_t* __restrict__ e_u, c
         const int64_t c = to_old[e];
         out[2 * c] = a < b ? a : b;
         out[2 * c + 1] = a < b ? b : a;
-    }
-}
-
-// ---- symmetry by sorting (large k-core graphs) ------------------------------
-// The CSR, read row by row, is the ascending sequence of keys (u << B) | v.
-// The graph is symmetric iff its transposed keys (v << B) | u, sorted, are
-// that same sequence: both are sets of distinct pairs of the same size.
-__device__ __forceinline__ void transpose_key_entries(const int32_t* __restrict__ col, int bits,
-                                                      unsigned long long* __restrict__ keys, int64_t u, int64_t pb,
-                                                      int64_t pe) {
-    for (int64_t p = pb + (threadIdx.x & 31); p < pe; p += 32)
-        keys[p] = ((unsigned long long)col[p] << bits) | (unsigned long long)u;
-}
-
-__global__ void k_transpose_keys(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int bits,
-                                 unsigned long long* __restrict__ keys) {
-    for (int64_t u = warp_id_global(); u < n; u += warp_count_global()) {
-        const int64_t b = rp[u], e = rp[u + 1];
-        if (is_long_row(b, e)) continue;  // k_transpose_keys_long
-        transpose_key_entries(col, bits, keys, u, b, e);
-    }
-}
-
-__global__ void k_transpose_keys_long(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int bits,
-                                      unsigned long long* __restrict__ keys, const int32_t* __restrict__ rows,
-                                      const int64_t* __restrict__ seg_off, int64_t count, int64_t segs) {
-    for (int64_t sg = warp_id_global(); sg < segs; sg += warp_count_global()) {
-        int64_t u, b, pb, pe;
-        long_segment(sg, rows, seg_off, count, rp, u, b, pb, pe);
-        transpose_key_entries(col, bits, keys, u, pb, pe);
-    }
-}
-
-__device__ __forceinline__ void compare_key_entries(const int32_t* __restrict__ col, int bits,
-                                                    const unsigned long long* __restrict__ sorted, int64_t u,
-                                                    int64_t pb, int64_t pe, int* __restrict__ err) {
-    bool bad = false;
-    for (int64_t p = pb + (threadIdx.x & 31); p < pe; p += 32)
-        bad |= sorted[p] != (((unsigned long long)u << bits) | (unsigned long long)col[p]);
-    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, 2);
-}
-
-__global__ void k_compare_keys(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int bits,
-                               const unsigned long long* __restrict__ sorted, int* __restrict__ err) {
-    for (int64_t u = warp_id_global(); u < n; u += warp_count_global()) {
-        const int64_t b = rp[u], e = rp[u + 1];
-        if (is_long_row(b, e)) continue;  // k_compare_keys_long
-        compare_key_entries(col, bits, sorted, u, b, e, err);
-    }
-}
-
-__global__ void k_compare_keys_long(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int bits,
-                                    const unsigned long long* __restrict__ sorted, int* __restrict__ err,
-                                    const int32_t* __restrict__ rows, const int64_t* __restrict__ seg_off,
-                                    int64_t count, int64_t segs) {
-    for (int64_t sg = warp_id_global(); sg < segs; sg += warp_count_global()) {
-        int64_t u, b, pb, pe;
-        long_segment(sg, rows, seg_off, count, rp, u, b, pb, pe);
-        compare_key_entries(col, bits, sorted, u, pb, pe, err);
     }
 }
 
@@ -1106,10 +1043,6 @@ static void release_long_rows(nd_incidence* h, cudaStream_t st) {
 
 // validation and degree split of the handle's CSR (h->rp, h->col): nlow,
 // up_start, the long rows, for r >= 2 the reverse entries, and h->m
-// k-core graphs with at least this many CSR entries check their symmetry by
-// a sort (the per-entry search costs more there)
-constexpr int64_t kSortSymmetryMin = (int64_t)1 << 26;
-
 static nd_status validate_split(nd_incidence* h, cudaStream_t st) {
     const nd_csr gg{h->n, h->nnz, h->rp, h->col, 1};
     const nd_csr* g = &gg;
@@ -1123,55 +1056,21 @@ static nd_status validate_split(nd_incidence* h, cudaStream_t st) {
     ND_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
     ND_CUDA(cudaMemsetAsync(h->up_start, 0, sizeof(int64_t) * (g->n + 1), st));
     ND_TRY(find_long_rows(h, st));
-    // a large k-core graph needs no reverse entries: its symmetry is checked
-    // by sorting the transposed pairs (below) instead of one search per entry
-    // (253 against about 60 ms on R-MAT scale 26), when the two key buffers fit
-    nd_tmp<unsigned long long> keys(st), alt(st);
-    bool by_sort = h->r == 1 && g->nnz >= kSortSymmetryMin;
-    if (by_sort && (keys.alloc(g->nnz) != ND_OK || alt.alloc(g->nnz) != ND_OK)) {
-        cudaGetLastError();
-        by_sort = false;
-    }
     if (g->n > 0) {
         nd_prof_scope ps("validate_split", st);
         int blocks = nd_blocks_for(g->n * 32, kThreads, grid_cap(h) * 4);
         k_validate_split<<<blocks, kThreads, 0, st>>>(g->n, g->nnz, h->rp, h->col, h->nlow,
-                                                      h->up_start, derr, h->mirror, by_sort ? 0 : 1);
+                                                      h->up_start, derr, h->mirror);
         ND_CUDA(cudaGetLastError());
         if (h->long_segs > 0) {
             k_validate_long<<<nd_blocks_for(h->long_segs * 32, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(
                 g->n, g->nnz, h->rp, h->col, h->long_rows, h->long_seg, h->long_count, h->long_segs, h->nlow,
-                h->up_start, derr, h->mirror, by_sort ? 0 : 1);
+                h->up_start, derr, h->mirror);
             ND_CUDA(cudaGetLastError());
         }
     }
     int herr = 0;
     ND_TRY(read_flag(derr, &herr, st));
-    if (!herr && by_sort) {
-        // the rows are in range and strictly increasing: the transposed keys,
-        // sorted, must equal the CSR's own keys position by position
-        nd_prof_scope ps("validate_split", st);
-        const int bits = nd_id_bits(g->n);
-        const int vblocks = nd_blocks_for(g->n * 32, kThreads, grid_cap(h) * 4);
-        const int lblocks = nd_blocks_for(h->long_segs * 32, kThreads, grid_cap(h) * 4);
-        k_transpose_keys<<<vblocks, kThreads, 0, st>>>(g->n, h->rp, h->col, bits, keys);
-        ND_CUDA(cudaGetLastError());
-        if (h->long_segs > 0) {
-            k_transpose_keys_long<<<lblocks, kThreads, 0, st>>>(h->rp, h->col, bits, keys, h->long_rows, h->long_seg,
-                                                                h->long_count, h->long_segs);
-            ND_CUDA(cudaGetLastError());
-        }
-        unsigned long long* sorted = nullptr;
-        ND_TRY(nd_sort_u64(keys, alt, g->nnz, 2 * bits, &sorted, st));
-        k_compare_keys<<<vblocks, kThreads, 0, st>>>(g->n, h->rp, h->col, bits, sorted, derr);
-        ND_CUDA(cudaGetLastError());
-        if (h->long_segs > 0) {
-            k_compare_keys_long<<<lblocks, kThreads, 0, st>>>(h->rp, h->col, bits, sorted, derr, h->long_rows,
-                                                              h->long_seg, h->long_count, h->long_segs);
-            ND_CUDA(cudaGetLastError());
-        }
-        ND_TRY(read_flag(derr, &herr, st));
-    }
     if (herr) {
         nd_set_error(herr & 1 ? "row_ptr is not a valid offset array"
                               : "col is not simple, sorted and symmetric");
