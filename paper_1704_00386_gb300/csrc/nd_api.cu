@@ -193,7 +193,7 @@ void nd_free(nd_incidence* h) {
     void* ptrs[] = {h->nlow, h->up_start, h->eid, h->e_u, h->e_v, h->tri_ptr, h->tri_w, h->tri_e,
                     h->items, h->tau[0], h->tau[1], h->front[0], h->front[1], h->counters,
                     h->mirror, h->e_pos, h->tg[0], h->tg[1], h->long_rows, h->long_seg, h->to_new, h->to_old,
-                    h->vto_old, h->c_rp, h->c_up, h->c_col, h->c_nlow, h->gid, h->gact[0], h->gact[1], h->tg8[0], h->tg8[1]};
+                    h->vto_old, h->c_rp, h->c_up, h->c_col, h->c_nlow, h->gid, h->gact[0], h->gact[1]};
     for (void* p : ptrs) nd_release(p, st);
     for (auto& row : h->pass_graph)
         for (auto& ex : row)

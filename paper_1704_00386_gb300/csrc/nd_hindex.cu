@@ -79,9 +79,6 @@ struct SweepParams {
     // vertex for (1,2); (3,4) gathers tin.
     const uint16_t* gin;
     uint16_t* gout;
-    // (1,2): the 8-bit copy (saturated at 255), gathered by rows with tau <= 255
-    const uint8_t* gin8;
-    uint8_t* gout8;
     const uint2* __restrict__ epos;
     const uint32_t* __restrict__ eid;  // CSR position -> edge id (notification)
     // (2,3) without a stored incidence: the graph and the edge endpoints
@@ -119,12 +116,6 @@ __device__ __forceinline__ int32_t ld_tau(const int32_t* p) {
 
 template <bool RO>
 __device__ __forceinline__ int32_t ld_tau(const uint16_t* p) {
-    if (RO) return (int32_t)__ldg(p);
-    return (int32_t)*p;
-}
-
-template <bool RO>
-__device__ __forceinline__ int32_t ld_tau(const uint8_t* p) {
     if (RO) return (int32_t)__ldg(p);
     return (int32_t)*p;
 }
@@ -176,7 +167,6 @@ struct RhoExact2 {
 };
 
 constexpr int32_t kTau16Max = 65535;
-constexpr int32_t kTau8Max = 255;
 
 // the gather of a row whose tau is at most 65535: the 16-bit copy for (1,2)
 // and (2,3).  (3,4) gathers int32 tau directly: its rows are not ordered, and
@@ -368,7 +358,6 @@ __device__ __forceinline__ void store_tau(const SweepParams& P, uint32_t R, int3
         P.gout[ep.y] = v;
     } else if (Q == 1) {
         P.gout[R] = v;
-        P.gout8[R] = (uint8_t)min(h, kTau8Max);
     }
 }
 
@@ -546,11 +535,7 @@ __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, 
     // H <= d_s, so tau is clipped at d_s for the search (a no-op for every
     // valid tau, which is <= d_s); changes are detected against the stored value
     const int32_t t = min(t0, (int32_t)it.d);
-    int32_t h;
-    if (Q == 1 && t <= kTau8Max)  // the 8-bit copy is exact below 256 (the row looks at min(rho, t))
-        h = group_hindex<G, C>(g, Rho<1, !AND, uint8_t>{P.inc, P.gin8}, jb, je, t);
-    else
-        h = group_hindex<G, C>(g, make_rho<Q, !AND>(P), jb, je, t);
+    const int32_t h = group_hindex<G, C>(g, make_rho<Q, !AND>(P), jb, je, t);
     if (lane == 0) {
         evals++;
         incs += it.d;
@@ -578,11 +563,7 @@ __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item
     // valid tau, which is <= d_s); changes are detected against the stored value
     const int32_t t = min(t0, (int32_t)it.d);
     const int64_t jb = it.jb, je = it.jb + it.d;
-    int32_t h;
-    if (Q == 1 && t <= kTau8Max)
-        h = warp_hindex(Rho<1, !AND, uint8_t>{P.inc, P.gin8}, jb, je, t, bins, cache, kRhoCache);
-    else
-        h = warp_hindex(make_rho<Q, !AND>(P), jb, je, t, bins, cache, kRhoCache);
+    const int32_t h = warp_hindex(make_rho<Q, !AND>(P), jb, je, t, bins, cache, kRhoCache);
     if (lane == 0) {
         evals++;
         incs += it.d;
@@ -710,10 +691,7 @@ __device__ __forceinline__ void run_groups_active(const SweepParams& P, int64_t 
             const int32_t t0 = ld_tau<false>(P.tin + it.R);
             const int32_t t = min(t0, (int32_t)it.d);
             jb = it.jb;
-            if (Q == 1 && t <= kTau8Max)
-                h = group_hindex<G, C>(g, Rho<1, false, uint8_t>{P.inc, P.gin8}, jb, jb + it.d, t);
-            else
-                h = group_hindex<G, C>(g, make_rho<Q, false>(P), jb, jb + it.d, t);
+            h = group_hindex<G, C>(g, make_rho<Q, false>(P), jb, jb + it.d, t);
             if (g.thread_rank() == 0) {
                 evals++;
                 incs += it.d;
@@ -916,18 +894,12 @@ __global__ void k_tau_to_adj(int64_t N, const uint2* __restrict__ epos, const in
 
 // tau -> its 16-bit gather copies indexed by r-clique id ((1,2), (3,4))
 __global__ void k_tau_to_16(int64_t N, const int32_t* __restrict__ tau, uint16_t* __restrict__ a,
-                            uint16_t* __restrict__ b, uint8_t* __restrict__ a8, uint8_t* __restrict__ b8) {
+                            uint16_t* __restrict__ b) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t t = max(tau[i], 0);
-        const uint16_t v = (uint16_t)min(t, kTau16Max);
+        const uint16_t v = (uint16_t)min(max(tau[i], 0), kTau16Max);
         a[i] = v;
         if (b) b[i] = v;
-        if (a8) {
-            const uint8_t v8 = (uint8_t)min(t, kTau8Max);
-            a8[i] = v8;
-            if (b8) b8[i] = v8;
-        }
     }
 }
 
@@ -1132,10 +1104,6 @@ nd_status ensure_state(nd_incidence* h, bool and_mode, cudaStream_t st) {
         const int64_t E = h->adj ? (h->nnz > 0 ? h->nnz : 1) : N;
         if (!h->tg[0]) ND_TRY(nd_alloc((void**)&h->tg[0], sizeof(uint16_t) * E, st, h));
         if (!and_mode && !h->tg[1]) ND_TRY(nd_alloc((void**)&h->tg[1], sizeof(uint16_t) * E, st, h));
-        if (h->q == 1) {
-            if (!h->tg8[0]) ND_TRY(nd_alloc((void**)&h->tg8[0], E, st, h));
-            if (!and_mode && !h->tg8[1]) ND_TRY(nd_alloc((void**)&h->tg8[1], E, st, h));
-        }
     }
     // (2,3): one frontier bit per CSR position (notification sets the bit of
     // the slot it has just read); otherwise one per r-clique
@@ -1169,8 +1137,6 @@ SweepParams pass_params(const nd_incidence* h, int mode, const SweepParams& P0, 
         P.tout = h->tau[0];
         P.gin = h->tg[0];
         P.gout = h->tg[0];
-        P.gin8 = h->tg8[0];
-        P.gout8 = h->tg8[0];
         P.cur = h->front[parity];
         P.next = h->front[parity ^ 1];
     } else {
@@ -1178,8 +1144,6 @@ SweepParams pass_params(const nd_incidence* h, int mode, const SweepParams& P0, 
         P.tout = h->tau[parity ^ 1];
         P.gin = h->tg[parity];
         P.gout = h->tg[parity ^ 1];
-        P.gin8 = h->tg8[parity];
-        P.gout8 = h->tg8[parity ^ 1];
         P.cur = nullptr;
         P.next = nullptr;
     }
@@ -1337,8 +1301,7 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
                 k_tau_to_adj<<<blocks, kThreads, 0, st>>>(N, h->e_pos, h->tau[0], h->tg[0],
                                                           and_mode ? nullptr : h->tg[1]);
             else
-                k_tau_to_16<<<blocks, kThreads, 0, st>>>(N, h->tau[0], h->tg[0], and_mode ? nullptr : h->tg[1],
-                                                         h->tg8[0], and_mode ? nullptr : h->tg8[1]);
+                k_tau_to_16<<<blocks, kThreads, 0, st>>>(N, h->tau[0], h->tg[0], and_mode ? nullptr : h->tg[1]);
             ND_CUDA(cudaGetLastError());
         }
     }

@@ -104,10 +104,6 @@ struct nd_incidence {
     uint32_t* mirror = nullptr;    // [nnz] build only: P(v,u) for the entry P(u,v)
     uint2* e_pos = nullptr;        // [m] (P(x,y), P(y,x)) of edge (x,y), x<y
     uint16_t* tg[2] = {nullptr, nullptr};  // [nnz] gather copies of tau by CSR position
-    // (1,2): a second gather copy in 8 bits, saturated at 255, for the rows
-    // with tau <= 255 (half the footprint of the 16-bit copy, so that a large
-    // graph's copy fits in L2)
-    uint8_t* tg8[2] = {nullptr, nullptr};
     bool rows_sorted = false;      // rows ordered by w (else in fill order)
     // (2,3) with no stored incidence (ND_BUILD_ON_THE_FLY): inc is empty and
     // every pass finds the triangles of each edge again
