@@ -58,6 +58,20 @@ constexpr int kWarpChunk = ND_WARP_CHUNK;
 #define ND_NOTIFY_UNROLL 4  // notification entries in flight per lane ((2,3))
 #endif
 constexpr int kNotifyUnroll = ND_NOTIFY_UNROLL;
+#ifndef ND_FRONT_L1
+#define ND_FRONT_L1 0  // 1: read the next frontier's words through L1 (a stale clear bit costs an atomic)
+#endif
+
+// a word of the next frontier, which this pass only sets bits in: read from
+// L2 (fresh), or through L1 with ND_FRONT_L1, where a stale clear bit only
+// costs a redundant, idempotent atomic
+__device__ __forceinline__ uint32_t ld_front(const uint32_t* p) {
+#if ND_FRONT_L1
+    return __ldca(p);
+#else
+    return __ldcg(p);
+#endif
+}
 #ifndef ND_RHO_CACHE
 #define ND_RHO_CACHE 1024  // rho values a warp keeps in shared memory for the search passes (0 = none)
 #endif
@@ -378,7 +392,7 @@ __device__ __forceinline__ void notify_clear(const SweepParams& P, uint32_t pos,
 
 // the same, testing the bit first and reading tau only if it is clear
 __device__ __forceinline__ void notify_pos(const SweepParams& P, uint32_t pos, int32_t h) {
-    if ((__ldcg(P.next + (pos >> 5)) >> (pos & 31)) & 1u) return;
+    if ((ld_front(P.next + (pos >> 5)) >> (pos & 31)) & 1u) return;
     notify_clear(P, pos, h, ld_tau<false>(P.gin + pos));
 }
 
@@ -422,8 +436,8 @@ __device__ __forceinline__ void notify_row(const SweepParams& P, int64_t jb, int
 #pragma unroll
             for (int u = 0; u < kNotifyUnroll; ++u) {
                 const bool ok = j0 + (int64_t)u * step < je;
-                wx[u] = ok ? __ldcg(P.next + (id[u].x >> 5)) : 0xffffffffu;
-                wy[u] = ok ? __ldcg(P.next + (id[u].y >> 5)) : 0xffffffffu;
+                wx[u] = ok ? ld_front(P.next + (id[u].x >> 5)) : 0xffffffffu;
+                wy[u] = ok ? ld_front(P.next + (id[u].y >> 5)) : 0xffffffffu;
             }
 #pragma unroll
             for (int u = 0; u < kNotifyUnroll; ++u) {
@@ -447,7 +461,7 @@ __device__ __forceinline__ void notify_row(const SweepParams& P, int64_t jb, int
             for (int u = 0; u < U; ++u) {
                 const bool ok = j0 + (int64_t)u * step < je;
 #pragma unroll
-                for (int k = 0; k < Q; ++k) wd[u][k] = ok ? __ldcg(P.next + (id[u][k] >> 5)) : 0xffffffffu;
+                for (int k = 0; k < Q; ++k) wd[u][k] = ok ? ld_front(P.next + (id[u][k] >> 5)) : 0xffffffffu;
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -471,7 +485,7 @@ template <int Q>
 __device__ __forceinline__ void notify_entry(const SweepParams& P, int64_t j, int32_t h) {
     if constexpr (Q == 2) {
         const uint2 id = __ldg(reinterpret_cast<const uint2*>(P.inc) + j);
-        const uint32_t wx = __ldcg(P.next + (id.x >> 5)), wy = __ldcg(P.next + (id.y >> 5));
+        const uint32_t wx = ld_front(P.next + (id.x >> 5)), wy = ld_front(P.next + (id.y >> 5));
         if (!((wx >> (id.x & 31)) & 1u)) notify_clear(P, id.x, h, ld_tau<false>(P.gin + id.x));
         if (!((wy >> (id.y & 31)) & 1u)) notify_clear(P, id.y, h, ld_tau<false>(P.gin + id.y));
     } else {
@@ -479,7 +493,7 @@ __device__ __forceinline__ void notify_entry(const SweepParams& P, int64_t j, in
 #pragma unroll
         for (int k = 0; k < Q; ++k) id[k] = __ldg(P.inc + Q * j + k);
 #pragma unroll
-        for (int k = 0; k < Q; ++k) wd[k] = __ldcg(P.next + (id[k] >> 5));
+        for (int k = 0; k < Q; ++k) wd[k] = ld_front(P.next + (id[k] >> 5));
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             const uint32_t Rp = id[k];
