@@ -59,12 +59,15 @@ constexpr int kWarpChunk = ND_WARP_CHUNK;
 #endif
 constexpr int kNotifyUnroll = ND_NOTIFY_UNROLL;
 #ifndef ND_FRONT_L1
-#define ND_FRONT_L1 0  // 1: read the next frontier's words through L1 (a stale clear bit costs an atomic)
+#define ND_FRONT_L1 1  // 0: read the next frontier's words from L2 only
 #endif
 
-// a word of the next frontier, which this pass only sets bits in: read from
-// L2 (fresh), or through L1 with ND_FRONT_L1, where a stale clear bit only
-// costs a redundant, idempotent atomic
+// a word of the next frontier, which this pass only sets bits in: read
+// through L1, where a stale clear bit only costs a redundant, idempotent
+// atomic (a set bit is never stale).  Measured against L2-only reads: the
+// k-core AND of R-MAT scale 24 took 73.8 against 89.9 ms, where the frontier
+// words of the hub vertices are read again and again; the truss and (3,4)
+// AND did not change.
 __device__ __forceinline__ uint32_t ld_front(const uint32_t* p) {
 #if ND_FRONT_L1
     return __ldca(p);
