@@ -58,9 +58,6 @@ constexpr int kWarpChunk = ND_WARP_CHUNK;
 #define ND_NOTIFY_UNROLL 4  // notification entries in flight per lane ((2,3))
 #endif
 constexpr int kNotifyUnroll = ND_NOTIFY_UNROLL;
-#ifndef ND_GROUP_KARY
-#define ND_GROUP_KARY 0  // 1: 4-ary search steps in the 4- and 8-lane groups (one packed reduction each)
-#endif
 #ifndef ND_FRONT_L1
 #define ND_FRONT_L1 1  // 0: read the next frontier's words from L2 only
 #endif
@@ -205,7 +202,6 @@ template <int G, int C, typename F>
 __device__ __forceinline__ int32_t group_hindex(const cg::thread_block_tile<G>& g, const F& rho,
                                                 int64_t jb, int64_t je, int32_t t) {
     static_assert(C % 2 == 0, "values are packed in pairs");
-    static_assert(G * C < 1024, "4-ary step counts are packed in 10-bit fields");
     const int lane = g.thread_rank();
     if (t <= 0) return 0;
     uint32_t pk[C / 2];
@@ -221,25 +217,6 @@ __device__ __forceinline__ int32_t group_hindex(const cg::thread_block_tile<G>& 
     cnt = cg::reduce(g, cnt, cg::plus<int>());
     if (cnt >= t) return t;
     int lo = cnt, hi = t;  // #{rho >= lo} >= lo holds; at hi it fails
-#if ND_GROUP_KARY
-    // 4-ary steps: three thresholds at once, their counts (at most G*C <= 64
-    // each) packed into 10-bit fields of one reduction
-    while (hi - lo > 3) {
-        const int q = (hi - lo) >> 2;  // lo < m1 < m2 < m3 < hi
-        const int m1 = lo + q, m2 = lo + 2 * q, m3 = lo + 3 * q;
-        int pc = 0;
-#pragma unroll
-        for (int c = 0; c < C / 2; ++c) {
-            const int a = (int)(pk[c] & 0xffffu), b = (int)(pk[c] >> 16);
-            pc += (a >= m1) + (b >= m1) + (((a >= m2) + (b >= m2)) << 10) + (((a >= m3) + (b >= m3)) << 20);
-        }
-        pc = cg::reduce(g, pc, cg::plus<int>());
-        if ((pc >> 20) >= m3) lo = m3;
-        else if (((pc >> 10) & 1023) >= m2) { lo = m2; hi = m3; }
-        else if ((pc & 1023) >= m1) { lo = m1; hi = m2; }
-        else hi = m1;
-    }
-#endif
     while (hi - lo > 1) {
         const int mid = lo + ((hi - lo) >> 1);
         int c2 = 0;
