@@ -278,7 +278,7 @@ static nd_status build_common(const nd_csr* g, int r, int s, cudaStream_t st, nd
     if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         h->sm_count = 152;
     h->last_stream = st;
-    nd_status rc = nd_build_graph(h, g, st);
+    nd_status rc = nd_build_graph(h, g, st, r == 2 && !h->otf && relabel);
     if (rc == ND_OK && r == 2 && !h->otf && relabel) rc = nd_relabel_truss_graph(h, st);
     if (rc == ND_OK && r >= 2) rc = nd_build_edges(h, st);
     if (rc == ND_OK && r == 2) rc = nd_relabel_truss_edges(h, st);

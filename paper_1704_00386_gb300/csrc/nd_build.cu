@@ -46,42 +46,60 @@ __device__ __forceinline__ int64_t warp_count_global() {
 }
 
 // ---- validation and degree split (one warp per vertex) -------------------
-// A row must lie inside [0, nnz], be strictly increasing, hold ids in [0, n)
-// other than its own, and every entry v of row u needs u in row v (checked
-// for v > u here, and for v < u by the count 2m == nnz that follows).  Writes
-// nlow[u] = #neighbours < u and upcnt[u] = #neighbours > u.  Reads only
-// inside the bounds it has checked, so a malformed graph cannot fault.
-// With mirror (builds with r >= 2), it also records for every entry p of
-// row u the position of u in row v: the reverse entry, found by the same
+// A row must lie inside [0, nnz], be strictly increasing and hold ids in
+// [0, n) other than its own, and every entry v of row u needs u in row v.
+// Writes nlow[u] = #neighbours < u and upcnt[u] = #neighbours > u.  Reads
+// only inside the bounds it has checked, so a malformed graph cannot fault.
+//
+// Symmetry: vertices are ordered by the key (row length, id).  An entry
+// (u, v) whose row u has the larger key searches the shorter row v for u;
+// the others are not searched.  The reverse of a searching entry is a
+// non-searching one, and distinct entries have distinct reverses, so if
+// every searching entry finds its reverse and the searching entries are
+// exactly half of nnz (counted in *searched, checked by the host), the two
+// halves are in one-to-one correspondence: the graph is symmetric.  A hub
+// row is thus never binary-searched, whatever the order of the caller's ids.
+// BY_LENGTH = false: the key is the id alone, so the entries above the
+// diagonal search (the same argument holds).  That is for graphs whose ids
+// the build itself assigned by degree class, high degree first, where the
+// entry above the diagonal already points at the shorter row (or one of its
+// class) and nothing needs gathering to decide it.
+// With mirror (builds with r >= 2), it also records for both entries of
+// every pair the position of the other: the reverse entry, found by the same
 // search.
-// the checks of entries [pb, pe) of row u (which starts at b), one entry per
-// lane: the count of entries below the diagonal and whether any check failed
+
+// the checks of entries [pb, pe) of row u (which spans [b, e)), one entry
+// per lane: the count of entries below the diagonal, of searching entries,
+// and whether any check failed
+template <bool BY_LENGTH>
 __device__ __forceinline__ void validate_entries(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
-                                                 const int32_t* __restrict__ col, int64_t u, int64_t b, int64_t pb,
-                                                 int64_t pe, uint32_t* __restrict__ mirror, int& low, bool& rowbad) {
+                                                 const int32_t* __restrict__ col, int64_t u, int64_t b, int64_t e,
+                                                 int64_t pb, int64_t pe, uint32_t* __restrict__ mirror, int& low,
+                                                 int& found, bool& rowbad) {
     const int lane = threadIdx.x & 31;
     for (int64_t p = pb + lane; p < pe; p += 32) {
         int32_t v = col[p];
         if (v < 0 || v >= n || v == u) { rowbad = true; continue; }
         if (p > b && col[p - 1] >= v) rowbad = true;
         low += (v < u);
-        // only entries above the diagonal look for their reverse: the host
-        // then checks 2m == nnz, i.e. as many entries below the diagonal
-        // as above, so with every one above matched (injectively, distinct
-        // u in one row) every entry below is matched too
-        if (v < u) continue;
+        if (!BY_LENGTH && v < u) continue;
         int64_t vb = rp[v], ve = rp[v + 1];
         // a row longer than n - 1 cannot be simple (and would not fit the 32-bit search)
         if (vb < 0 || ve < vb || ve > nnz || ve - vb >= n) { rowbad = true; continue; }
+        if (BY_LENGTH && (e - b < ve - vb || (e - b == ve - vb && u < v))) continue;
         const int64_t pos = vb + nd_lower_bound_n(col + vb, (int)(ve - vb), (int32_t)u);
         if (pos >= ve || col[pos] != (int32_t)u) { rowbad = true; continue; }
+        ++found;
         if (mirror) {
             mirror[p] = (uint32_t)pos;
             mirror[pos] = (uint32_t)p;
         }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) low += __shfl_xor_sync(kFull, low, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        low += __shfl_xor_sync(kFull, low, o);
+        found += __shfl_xor_sync(kFull, found, o);
+    }
     rowbad = __any_sync(kFull, rowbad);
 }
 
@@ -129,10 +147,11 @@ __device__ __forceinline__ void long_segment(int64_t s, const int32_t* __restric
     pe = min(pb + kLongSeg, e);
 }
 
+template <bool BY_LENGTH>
 __global__ void k_validate_split(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
                                  const int32_t* __restrict__ col, int32_t* __restrict__ nlow,
                                  int64_t* __restrict__ upcnt, int* __restrict__ err,
-                                 uint32_t* __restrict__ mirror) {
+                                 unsigned long long* __restrict__ searched, uint32_t* __restrict__ mirror) {
     const int lane = threadIdx.x & 31;
     for (int64_t u = warp_id_global(); u < n; u += warp_count_global()) {
         int64_t b = rp[u], e = rp[u + 1];
@@ -145,33 +164,36 @@ __global__ void k_validate_split(int64_t n, int64_t nnz, const int64_t* __restri
             if (lane == 0) { nlow[u] = 0; upcnt[u] = 0; }
             continue;
         }
-        int low = 0;
+        int low = 0, found = 0;
         bool rowbad = false;
-        validate_entries(n, nnz, rp, col, u, b, b, e, mirror, low, rowbad);
+        validate_entries<BY_LENGTH>(n, nnz, rp, col, u, b, e, b, e, mirror, low, found, rowbad);
         if (lane == 0) {
             nlow[u] = low;
             upcnt[u] = (e - b) - low;
+            if (found) atomicAdd(searched, (unsigned long long)found);
             if (rowbad) atomicOr(err, 2);
         }
     }
 }
 
 // the long rows, one warp per segment; the counts add up per row
+template <bool BY_LENGTH>
 __global__ void k_validate_long(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
                                 const int32_t* __restrict__ col, const int32_t* __restrict__ rows,
                                 const int64_t* __restrict__ seg_off, int64_t count, int64_t segs,
                                 int32_t* __restrict__ nlow, int64_t* __restrict__ upcnt, int* __restrict__ err,
-                                uint32_t* __restrict__ mirror) {
+                                unsigned long long* __restrict__ searched, uint32_t* __restrict__ mirror) {
     const int lane = threadIdx.x & 31;
     for (int64_t sg = warp_id_global(); sg < segs; sg += warp_count_global()) {
         int64_t u, b, pb, pe;
         long_segment(sg, rows, seg_off, count, rp, u, b, pb, pe);
-        int low = 0;
+        int low = 0, found = 0;
         bool rowbad = false;
-        validate_entries(n, nnz, rp, col, u, b, pb, pe, mirror, low, rowbad);
+        validate_entries<BY_LENGTH>(n, nnz, rp, col, u, b, rp[u + 1], pb, pe, mirror, low, found, rowbad);
         if (lane == 0) {
             atomicAdd(nlow + u, low);
             atomicAdd(reinterpret_cast<unsigned long long*>(upcnt + u), (unsigned long long)((pe - pb) - low));
+            if (found) atomicAdd(searched, (unsigned long long)found);
             if (rowbad) atomicOr(err, 2);
         }
     }
@@ -1043,29 +1065,35 @@ static void release_long_rows(nd_incidence* h, cudaStream_t st) {
 
 // validation and degree split of the handle's CSR (h->rp, h->col): nlow,
 // up_start, the long rows, for r >= 2 the reverse entries, and h->m
-static nd_status validate_split(nd_incidence* h, cudaStream_t st) {
+// by_length: the symmetry key of k_validate_split (false only for ids that
+// the build assigned by degree class); mirror: record the reverse entries
+static nd_status validate_split(nd_incidence* h, cudaStream_t st, bool by_length, bool mirror) {
     const nd_csr gg{h->n, h->nnz, h->rp, h->col, 1};
     const nd_csr* g = &gg;
     ND_TRY(nd_alloc((void**)&h->nlow, sizeof(int32_t) * (g->n > 0 ? g->n : 1), st, h));
     ND_TRY(nd_alloc((void**)&h->up_start, sizeof(int64_t) * (g->n + 1), st, h));
     // reverse entries for the edge ids and the (2,3) adjacency layout (build only)
-    if (h->r >= 2 && g->nnz > 0 && g->nnz < (int64_t)UINT32_MAX)
+    if (mirror && h->r >= 2 && g->nnz > 0 && g->nnz < (int64_t)UINT32_MAX)
         ND_TRY(nd_alloc((void**)&h->mirror, sizeof(uint32_t) * g->nnz, st, h));
     nd_tmp<int> derr(st);
     ND_TRY(derr.alloc(1));
     ND_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
+    nd_tmp<unsigned long long> dsearched(st);
+    ND_TRY(dsearched.alloc(1));
+    ND_CUDA(cudaMemsetAsync(dsearched, 0, sizeof(unsigned long long), st));
     ND_CUDA(cudaMemsetAsync(h->up_start, 0, sizeof(int64_t) * (g->n + 1), st));
     ND_TRY(find_long_rows(h, st));
     if (g->n > 0) {
         nd_prof_scope ps("validate_split", st);
         int blocks = nd_blocks_for(g->n * 32, kThreads, grid_cap(h) * 4);
-        k_validate_split<<<blocks, kThreads, 0, st>>>(g->n, g->nnz, h->rp, h->col, h->nlow,
-                                                      h->up_start, derr, h->mirror);
+        (by_length ? k_validate_split<true> : k_validate_split<false>)<<<blocks, kThreads, 0, st>>>(
+            g->n, g->nnz, h->rp, h->col, h->nlow, h->up_start, derr, dsearched, h->mirror);
         ND_CUDA(cudaGetLastError());
         if (h->long_segs > 0) {
-            k_validate_long<<<nd_blocks_for(h->long_segs * 32, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(
+            (by_length ? k_validate_long<true> : k_validate_long<false>)<<<
+                nd_blocks_for(h->long_segs * 32, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(
                 g->n, g->nnz, h->rp, h->col, h->long_rows, h->long_seg, h->long_count, h->long_segs, h->nlow,
-                h->up_start, derr, h->mirror);
+                h->up_start, derr, dsearched, h->mirror);
             ND_CUDA(cudaGetLastError());
         }
     }
@@ -1077,19 +1105,24 @@ static nd_status validate_split(nd_incidence* h, cudaStream_t st) {
         return ND_E_INVAL;
     }
     ND_TRY(nd_scan_i64(h->up_start, g->n, st));
-    int64_t m = 0;
+    int64_t m = 0, found = 0;
     ND_TRY(read_i64(h->up_start + g->n, &m, st));
-    if (2 * m != g->nnz) {
-        // every entry above the diagonal has its reverse; a surplus below it
-        // is an entry without one
-        nd_set_error("col is not symmetric (more entries below the diagonal than above)");
+    ND_TRY(read_i64(reinterpret_cast<int64_t*>(dsearched.p), &found, st));
+    if (2 * found != g->nnz || 2 * m != g->nnz) {
+        // every searching entry has its reverse; a surplus of the others is
+        // an entry without one
+        nd_set_error("col is not symmetric (an entry without its reverse)");
         return ND_E_INVAL;
     }
     h->m = m;
     return ND_OK;
 }
 
-nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st) {
+// graphs smaller than this keep their ids: their tau fits in cache anyway,
+// and the few launches of a relabelling would dominate their build
+constexpr int64_t kRelabelMinVertices = 1 << 16;
+
+nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st, bool truss_relabel) {
     h->n = g->n;
     h->nnz = g->nnz;
     ND_TRY(nd_alloc((void**)&h->rp, sizeof(int64_t) * (g->n + 1), st, h));
@@ -1097,12 +1130,11 @@ nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st) {
     cudaMemcpyKind kind = g->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     ND_CUDA(cudaMemcpyAsync(h->rp, g->row_ptr, sizeof(int64_t) * (g->n + 1), kind, st));
     if (g->nnz > 0) ND_CUDA(cudaMemcpyAsync(h->col, g->col, sizeof(int32_t) * g->nnz, kind, st));
-    return validate_split(h, st);
+    // a (2,3) graph that the relabelling will rewrite is validated again
+    // under its new ids, and only that second pass records reverse entries
+    const bool rewritten = truss_relabel && h->r == 2 && g->n >= kRelabelMinVertices;
+    return validate_split(h, st, true, !rewritten);
 }
-
-// graphs smaller than this keep their ids: their tau fits in cache anyway,
-// and the few launches of a relabelling would dominate their build
-constexpr int64_t kRelabelMinVertices = 1 << 16;
 
 // vertex ids by degree class (k_class_count / k_class_scatter) for the graph
 // in h->rp: to_new[caller id] = new id, to_old[new id] = caller id
@@ -1187,7 +1219,7 @@ nd_status nd_relabel_truss_graph(nd_incidence* h, cudaStream_t st) {
     h->mirror = nullptr;
     release_long_rows(h, st);
     const int64_t m = h->m;
-    ND_TRY(validate_split(h, st));
+    ND_TRY(validate_split(h, st, false, true));
     if (h->m != m) { nd_set_error("relabelled graph lost edges (internal fault)"); return ND_E_CUDA; }
     return ND_OK;
 }

@@ -212,7 +212,9 @@ nd_status nd_sort_u64(unsigned long long* keys, unsigned long long* alt, int64_t
 int nd_id_bits(int64_t n);
 
 // build steps (nd_build.cu)
-nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st);
+// the handle's CSR copy, validated and split; truss_relabel: a (2,3) build
+// that will renumber the graph (nd_relabel_truss_graph) next
+nd_status nd_build_graph(nd_incidence* h, const nd_csr* g, cudaStream_t st, bool truss_relabel);
 nd_status nd_build_edges(nd_incidence* h, cudaStream_t st);
 nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st);
 nd_status nd_build_triangles(nd_incidence* h, cudaStream_t st);
