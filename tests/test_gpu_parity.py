@@ -195,6 +195,35 @@ def test_malformed_graph_rejected(nd, bad):
     assert e.value.status == nd.ND_E_INVAL
 
 
+def test_truss_with_high_out_degree_sources(nd):
+    """Long oriented lists next to short ones.  A K_530 (every vertex 529
+    neighbours: ids break the ties of the degree orientation, so the first
+    vertices have out-degree above 512, and every edge lies in 528
+    triangles) disjoint from a Chung-Lu graph of 3,000 vertices.  Closed
+    form on the clique (truss number 528 for every edge), the oracle on the
+    rest."""
+    k = 530
+    rest_rp, rest_col = G.to_csr(3000, *G.chung_lu(3000, 2.2, 10.0, seed=111))
+    a, b = np.triu_indices(k, 1)
+    src = np.concatenate([a, k + np.repeat(np.arange(3000), np.diff(rest_rp))])
+    dst = np.concatenate([b, k + rest_col.astype(np.int64)])
+    rp, col = G.to_csr(k + 3000, src, dst)
+    want_rest = oracle.decompose(rest_rp, rest_col, 2, 3)
+    m_clique = k * (k - 1) // 2
+    for on_device in (False, True):
+        args = (torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda()) if on_device else (rp, col)
+        inc = nd.build_incidence(*args, 2, 3)
+        assert inc.num_r == m_clique + len(want_rest)
+        ds = inc.s_degree()
+        ds = ds.cpu().numpy() if on_device else ds
+        assert (ds[:m_clique] == k - 2).all()
+        for tau in (inc.snd()[0], inc.and_(notify=True)[0]):
+            tau = tau.cpu().numpy() if on_device else tau
+            assert (tau[:m_clique] == k - 2).all()      # edges (u, v), u < v < 530 come first
+            np.testing.assert_array_equal(tau[m_clique:], want_rest)
+        inc.free()
+
+
 @pytest.mark.parametrize("rs", RS)
 def test_overlapping_long_rows_rejected(nd, rs):
     """Long rows are listed before validation into arrays sized for disjoint
