@@ -75,6 +75,9 @@ __device__ __forceinline__ uint32_t ld_front(const uint32_t* p) {
     return __ldcg(p);
 #endif
 }
+#ifndef ND_CORE_AND_CTA_FIRST
+#define ND_CORE_AND_CTA_FIRST 1  // (1,2) AND: the CTA rows (hub vertices) before the warp tasks
+#endif
 #ifndef ND_RHO_CACHE
 #define ND_RHO_CACHE 1024  // rho values a warp keeps in shared memory for the search passes (0 = none)
 #endif
@@ -779,9 +782,14 @@ __global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS 
     // what earlier rows lowered: AND takes the shortest rows first and the
     // CTA rows last (measured 3% faster than longest first on R-MAT scale 20
     // k-truss).  SND, whose pass reads only the previous pass, takes the
-    // longest rows first, for balance.
+    // longest rows first, for balance.  A k-core's CTA rows are the hub
+    // vertices, up to hundreds of thousands of entries each, and one block
+    // streams a row: taken last, they kept a few blocks busy long after the
+    // rest of the pass had finished (18% of the AND time of an R-MAT scale
+    // 26 k-core in ncu), so (1,2) AND takes them first.
     constexpr bool kShortFirst = AND;
-    if (!kShortFirst) cta_phase();
+    constexpr bool kCtaFirst = !AND || (Q == 1 && ND_CORE_AND_CTA_FIRST);
+    if (kCtaFirst) cta_phase();
     // phase 2: warp tasks (one warp row, four 8-lane rows or eight 4-lane
     // rows), longest first (SND) or shortest first (AND).  Each warp takes
     // chunks of kWarpChunk
@@ -863,7 +871,7 @@ __global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS 
             }
         }
     }
-    if (kShortFirst) cta_phase();
+    if (!kCtaFirst) cta_phase();
     __shared__ unsigned long long s_ch[kThreads / 32], s_ev[kThreads / 32], s_in[kThreads / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
