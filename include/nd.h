@@ -102,7 +102,14 @@ nd_status nd_normalize(const int64_t* src, const int64_t* dst, int64_t m, int64_
  * internal: every call takes and returns r-cliques in the canonical order
  * of nd_r_cliques.
  * The graph is validated first; a malformed graph returns ND_E_INVAL and
- * builds nothing.  Synchronises `stream` (sizes are read back to allocate).
+ * builds nothing.  Bounds, ids, self-loops and row order are checked
+ * exactly.  Symmetry is checked exactly for r >= 2, where the build finds
+ * every entry's reverse anyway.  For r = 1 it is checked by a fingerprint:
+ * two 64-bit sums, over all entries (u, v), of a hash of (u, v) minus the
+ * same hash of (v, u).  A symmetric graph always passes.  An asymmetric one
+ * passes only if both sums vanish by coincidence, about 2^-128 for inputs
+ * not built to collide.  A k-core of such an input reads only inside its
+ * arrays.  Synchronises `stream` (sizes are read back to allocate).
  * On success *out owns device memory until nd_free(*out). */
 nd_status nd_build_incidence(const nd_csr* g, int r, int s, void* stream, nd_incidence** out);
 

@@ -68,20 +68,45 @@ __device__ __forceinline__ int64_t warp_count_global() {
 // every pair the position of the other: the reverse entry, found by the same
 // search.
 
+// FP (k-core builds, which need no reverse entries): symmetry by
+// fingerprint instead of searches.  Every entry (u, v) adds
+// f(u, v) - f(v, u) to two 64-bit sums, each with its own mixing function f
+// (the splitmix64 finalizer, after Steele, Lea and Flood, on different
+// inputs).  A symmetric graph sums to zero exactly.  Otherwise the sums are
+// those of f over the entries without a reverse minus f over the missing
+// reverses, and both are zero only by a coincidence of two 64-bit hashes.
+// It streams col once and gathers nothing.
+__device__ __forceinline__ unsigned long long fp_mix(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ void fp_add(unsigned long long (&fp)[2], int64_t u, int32_t v) {
+    const unsigned long long k = ((unsigned long long)u << 32) | (uint32_t)v;
+    const unsigned long long r = ((unsigned long long)(uint32_t)v << 32) | (unsigned long long)u;
+    fp[0] += fp_mix(k ^ 0x9e3779b97f4a7c15ull) - fp_mix(r ^ 0x9e3779b97f4a7c15ull);
+    fp[1] += fp_mix(fp_mix(k) + 0x632be59bd9b4e019ull) - fp_mix(fp_mix(r) + 0x632be59bd9b4e019ull);
+}
+
 // the checks of entries [pb, pe) of row u (which spans [b, e)), one entry
 // per lane: the count of entries below the diagonal, of searching entries,
-// and whether any check failed
-template <bool BY_LENGTH>
+// and whether any check failed (FP: fp collects this lane's fingerprint
+// terms, summed over the warp by the caller)
+template <bool BY_LENGTH, bool FP = false>
 __device__ __forceinline__ void validate_entries(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
                                                  const int32_t* __restrict__ col, int64_t u, int64_t b, int64_t e,
                                                  int64_t pb, int64_t pe, uint32_t* __restrict__ mirror, int& low,
-                                                 int& found, bool& rowbad) {
+                                                 int& found, bool& rowbad, unsigned long long (&fp)[2]) {
     const int lane = threadIdx.x & 31;
     for (int64_t p = pb + lane; p < pe; p += 32) {
         int32_t v = col[p];
         if (v < 0 || v >= n || v == u) { rowbad = true; continue; }
         if (p > b && col[p - 1] >= v) rowbad = true;
         low += (v < u);
+        if constexpr (FP) {
+            fp_add(fp, u, v);
+            continue;
+        }
         if (!BY_LENGTH && v < u) continue;
         int64_t vb = rp[v], ve = rp[v + 1];
         // a row longer than n - 1 cannot be simple (and would not fit the 32-bit search)
@@ -147,12 +172,27 @@ __device__ __forceinline__ void long_segment(int64_t s, const int32_t* __restric
     pe = min(pb + kLongSeg, e);
 }
 
-template <bool BY_LENGTH>
+// the two fingerprint sums of a warp's lanes, added to fp_out[0..1]
+__device__ __forceinline__ void fp_flush(unsigned long long (&fp)[2], unsigned long long* fp_out) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fp[0] += __shfl_xor_sync(kFull, fp[0], o);
+        fp[1] += __shfl_xor_sync(kFull, fp[1], o);
+    }
+    if ((threadIdx.x & 31) == 0 && (fp[0] | fp[1])) {
+        atomicAdd(fp_out, fp[0]);
+        atomicAdd(fp_out + 1, fp[1]);
+    }
+}
+
+template <bool BY_LENGTH, bool FP = false>
 __global__ void k_validate_split(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
                                  const int32_t* __restrict__ col, int32_t* __restrict__ nlow,
                                  int64_t* __restrict__ upcnt, int* __restrict__ err,
-                                 unsigned long long* __restrict__ searched, uint32_t* __restrict__ mirror) {
+                                 unsigned long long* __restrict__ searched, uint32_t* __restrict__ mirror,
+                                 unsigned long long* __restrict__ fp_out) {
     const int lane = threadIdx.x & 31;
+    unsigned long long fp[2] = {0ull, 0ull};
     for (int64_t u = warp_id_global(); u < n; u += warp_count_global()) {
         int64_t b = rp[u], e = rp[u + 1];
         bool bad = (b < 0) || (e < b) || (e > nnz) || (u == 0 && b != 0) || (u == n - 1 && e != nnz);
@@ -166,7 +206,7 @@ __global__ void k_validate_split(int64_t n, int64_t nnz, const int64_t* __restri
         }
         int low = 0, found = 0;
         bool rowbad = false;
-        validate_entries<BY_LENGTH>(n, nnz, rp, col, u, b, e, b, e, mirror, low, found, rowbad);
+        validate_entries<BY_LENGTH, FP>(n, nnz, rp, col, u, b, e, b, e, mirror, low, found, rowbad, fp);
         if (lane == 0) {
             nlow[u] = low;
             upcnt[u] = (e - b) - low;
@@ -174,22 +214,25 @@ __global__ void k_validate_split(int64_t n, int64_t nnz, const int64_t* __restri
             if (rowbad) atomicOr(err, 2);
         }
     }
+    if constexpr (FP) fp_flush(fp, fp_out);
 }
 
 // the long rows, one warp per segment; the counts add up per row
-template <bool BY_LENGTH>
+template <bool BY_LENGTH, bool FP = false>
 __global__ void k_validate_long(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
                                 const int32_t* __restrict__ col, const int32_t* __restrict__ rows,
                                 const int64_t* __restrict__ seg_off, int64_t count, int64_t segs,
                                 int32_t* __restrict__ nlow, int64_t* __restrict__ upcnt, int* __restrict__ err,
-                                unsigned long long* __restrict__ searched, uint32_t* __restrict__ mirror) {
+                                unsigned long long* __restrict__ searched, uint32_t* __restrict__ mirror,
+                                unsigned long long* __restrict__ fp_out) {
     const int lane = threadIdx.x & 31;
+    unsigned long long fp[2] = {0ull, 0ull};
     for (int64_t sg = warp_id_global(); sg < segs; sg += warp_count_global()) {
         int64_t u, b, pb, pe;
         long_segment(sg, rows, seg_off, count, rp, u, b, pb, pe);
         int low = 0, found = 0;
         bool rowbad = false;
-        validate_entries<BY_LENGTH>(n, nnz, rp, col, u, b, rp[u + 1], pb, pe, mirror, low, found, rowbad);
+        validate_entries<BY_LENGTH, FP>(n, nnz, rp, col, u, b, rp[u + 1], pb, pe, mirror, low, found, rowbad, fp);
         if (lane == 0) {
             atomicAdd(nlow + u, low);
             atomicAdd(reinterpret_cast<unsigned long long*>(upcnt + u), (unsigned long long)((pe - pb) - low));
@@ -197,6 +240,7 @@ __global__ void k_validate_long(int64_t n, int64_t nnz, const int64_t* __restric
             if (rowbad) atomicOr(err, 2);
         }
     }
+    if constexpr (FP) fp_flush(fp, fp_out);
 }
 
 // ---- (1,2): vertices relabelled by degree class ----------------------------
@@ -1078,22 +1122,25 @@ static nd_status validate_split(nd_incidence* h, cudaStream_t st, bool by_length
     nd_tmp<int> derr(st);
     ND_TRY(derr.alloc(1));
     ND_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
+    // k-core builds (no reverse entries needed) decide symmetry by fingerprint
+    const bool fp = h->r == 1;
     nd_tmp<unsigned long long> dsearched(st);
-    ND_TRY(dsearched.alloc(1));
-    ND_CUDA(cudaMemsetAsync(dsearched, 0, sizeof(unsigned long long), st));
+    ND_TRY(dsearched.alloc(3));  // [0] searching entries found, [1..2] fingerprint sums
+    ND_CUDA(cudaMemsetAsync(dsearched, 0, 3 * sizeof(unsigned long long), st));
     ND_CUDA(cudaMemsetAsync(h->up_start, 0, sizeof(int64_t) * (g->n + 1), st));
     ND_TRY(find_long_rows(h, st));
     if (g->n > 0) {
         nd_prof_scope ps("validate_split", st);
         int blocks = nd_blocks_for(g->n * 32, kThreads, grid_cap(h) * 4);
-        (by_length ? k_validate_split<true> : k_validate_split<false>)<<<blocks, kThreads, 0, st>>>(
-            g->n, g->nnz, h->rp, h->col, h->nlow, h->up_start, derr, dsearched, h->mirror);
+        auto split = fp ? k_validate_split<true, true> : (by_length ? k_validate_split<true> : k_validate_split<false>);
+        split<<<blocks, kThreads, 0, st>>>(g->n, g->nnz, h->rp, h->col, h->nlow, h->up_start, derr, dsearched,
+                                           h->mirror, dsearched.p + 1);
         ND_CUDA(cudaGetLastError());
         if (h->long_segs > 0) {
-            (by_length ? k_validate_long<true> : k_validate_long<false>)<<<
-                nd_blocks_for(h->long_segs * 32, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(
+            auto lng = fp ? k_validate_long<true, true> : (by_length ? k_validate_long<true> : k_validate_long<false>);
+            lng<<<nd_blocks_for(h->long_segs * 32, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(
                 g->n, g->nnz, h->rp, h->col, h->long_rows, h->long_seg, h->long_count, h->long_segs, h->nlow,
-                h->up_start, derr, dsearched, h->mirror);
+                h->up_start, derr, dsearched, h->mirror, dsearched.p + 1);
             ND_CUDA(cudaGetLastError());
         }
     }
@@ -1106,9 +1153,12 @@ static nd_status validate_split(nd_incidence* h, cudaStream_t st, bool by_length
     }
     ND_TRY(nd_scan_i64(h->up_start, g->n, st));
     int64_t m = 0, found = 0;
+    unsigned long long hs[3] = {0, 0, 0};
     ND_TRY(read_i64(h->up_start + g->n, &m, st));
-    ND_TRY(read_i64(reinterpret_cast<int64_t*>(dsearched.p), &found, st));
-    if (2 * found != g->nnz || 2 * m != g->nnz) {
+    ND_CUDA(cudaMemcpyAsync(hs, dsearched.p, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    ND_TRY(nd_wait(st));
+    found = (int64_t)hs[0];
+    if (fp ? (hs[1] != 0 || hs[2] != 0 || 2 * m != g->nnz) : (2 * found != g->nnz || 2 * m != g->nnz)) {
         // every searching entry has its reverse; a surplus of the others is
         // an entry without one
         nd_set_error("col is not symmetric (an entry without its reverse)");
