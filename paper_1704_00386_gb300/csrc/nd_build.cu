@@ -531,14 +531,22 @@ __global__ void k_orient(int64_t n, const int64_t* __restrict__ rp, const int32_
 #ifndef ND_TRI_MIN_BLOCKS
 #define ND_TRI_MIN_BLOCKS 6  // resident blocks per SM for the triangle count / fill
 #endif
-template <bool FILL, bool ADJ, typename C = unsigned long long>
+// REC (count pass): also record every triangle found from edge k, as the
+// offsets of w in the shorter and in the longer out-list (16 bits each: an
+// out-list holds at most sqrt(2m) < 65536 entries, since each of its
+// vertices has at least the owner's degree and nnz < 2^32), at
+// rec[rec_ptr[k] + i]; rec_ptr[k] reserves min(|out(u)|, |out(v)|) slots,
+// the most edge k can find.  rec_cnt[k] = triangles found.
+template <bool FILL, bool ADJ, typename C = unsigned long long, bool REC = false>
 __global__ void __launch_bounds__(kThreads, ND_TRI_MIN_BLOCKS) k_tri_oriented(int64_t m, const int64_t* __restrict__ out_ptr,
                                const int32_t* __restrict__ out_col, const uint32_t* __restrict__ out_eid,
                                const int32_t* __restrict__ out_src, const uint32_t* __restrict__ out_pos,
                                const uint32_t* __restrict__ out_mir, C* __restrict__ ctr,
-                               uint2* __restrict__ inc) {
+                               uint2* __restrict__ inc, const int64_t* __restrict__ rec_ptr = nullptr,
+                               uint32_t* __restrict__ rec = nullptr, uint32_t* __restrict__ rec_cnt = nullptr) {
     const int lane = threadIdx.x & 31;
     for (int64_t k = warp_id_global(); k < m; k += warp_count_global()) {
+        uint32_t nrec = 0;  // REC: triangles recorded so far for edge k
         const int32_t u = out_src[k], v = out_col[k];
         const uint32_t e_uv = out_eid[k];
         uint32_t Puv = 0, Pvu = 0;
@@ -585,6 +593,12 @@ __global__ void __launch_bounds__(kThreads, ND_TRI_MIN_BLOCKS) k_tri_oriented(in
                         atomicAdd(ctr + e_uw, (C)1);
                         atomicAdd(ctr + e_vw, (C)1);
                     }
+                    if (REC) {
+                        if (found)
+                            rec[rec_ptr[k] + nrec + __popc(bal & lanemask_lt())] =
+                                (uint32_t)(p - ab) | ((uint32_t)(pb - bb) << 16);
+                        nrec += (uint32_t)nf;
+                    }
                 } else {
                     uint32_t pbp = 0, mb = 0;
                     if (found) {
@@ -627,6 +641,80 @@ __global__ void __launch_bounds__(kThreads, ND_TRI_MIN_BLOCKS) k_tri_oriented(in
             const int64_t last_pb = __shfl_sync(kFull, pb, 31);
             if (base + 32 <= ae) lo = last_pb;
         }
+        if (REC && lane == 0) rec_cnt[k] = nrec;
+    }
+}
+
+// the fill from the count pass's records: one warp per oriented edge k, one
+// recorded triangle per lane, so no search is repeated.  The six positions
+// of a triangle are read at the recorded offsets of w in the two out-lists
+// (the shorter list's reads coalesce, as in the searching fill); slots and
+// entries are as in k_tri_oriented<true, true>.
+template <typename C>
+__global__ void __launch_bounds__(kThreads, ND_TRI_MIN_BLOCKS)
+    k_tri_fill_rec(int64_t m, const int64_t* __restrict__ out_ptr, const int32_t* __restrict__ out_col,
+                   const uint32_t* __restrict__ out_eid, const int32_t* __restrict__ out_src,
+                   const uint32_t* __restrict__ out_pos, const uint32_t* __restrict__ out_mir, C* __restrict__ ctr,
+                   uint2* __restrict__ inc, const int64_t* __restrict__ rec_ptr, const uint32_t* __restrict__ rec,
+                   const uint32_t* __restrict__ rec_cnt) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t k = warp_id_global(); k < m; k += warp_count_global()) {
+        const uint32_t c = __ldg(rec_cnt + k);
+        if (c == 0) continue;
+        const int32_t u = out_src[k], v = out_col[k];
+        const uint32_t e_uv = out_eid[k];
+        const uint32_t Puv = __ldg(out_pos + k), Pvu = __ldg(out_mir + k);
+        int64_t ab = out_ptr[u], ae = out_ptr[u + 1], bb = out_ptr[v], be = out_ptr[v + 1];
+        bool a_is_u = true;
+        if (ae - ab > be - bb) {  // the same choice of the shorter list as the count pass
+            int64_t t = ab; ab = bb; bb = t; t = ae; ae = be; be = t;
+            a_is_u = false;
+        }
+        const int64_t r0 = rec_ptr[k];
+        for (uint32_t base = 0; base < c; base += 32) {
+            const uint32_t i = base + lane;
+            const bool found = i < c;
+            uint32_t ea = 0, pa = 0, ma = 0, eb = 0, pbp = 0, mb = 0;
+            int32_t x = 0;
+            if (found) {
+                const uint32_t r = __ldg(rec + r0 + i);
+                const int64_t p = ab + (r & 0xffffu), pb = bb + (r >> 16);
+                x = __ldg(out_col + p);
+                ea = __ldg(out_eid + p);
+                pa = __ldg(out_pos + p);
+                ma = __ldg(out_mir + p);
+                eb = __ldg(out_eid + pb);
+                pbp = __ldg(out_pos + pb);
+                mb = __ldg(out_mir + pb);
+            }
+            const unsigned bal = __ballot_sync(kFull, found);
+            const int nf = __popc(bal);
+            const uint32_t e_uw = a_is_u ? ea : eb, e_vw = a_is_u ? eb : ea;
+            C s0 = 0, s_uw = 0, s_vw = 0;
+            if (lane == 0) s0 = atomicAdd(ctr + e_uv, (C)nf);
+            if (found) {
+                s_uw = atomicAdd(ctr + e_uw, (C)1);
+                s_vw = atomicAdd(ctr + e_vw, (C)1);
+            }
+            s0 = __shfl_sync(kFull, s0, 0);
+            if (found) {
+                const uint32_t Puw = a_is_u ? pa : pbp, Pwu = a_is_u ? ma : mb;
+                const uint32_t Pvw = a_is_u ? pbp : pa, Pwv = a_is_u ? mb : ma;
+                inc[s0 + __popc(bal & lanemask_lt())] = u < v ? make_uint2(Puw, Pvw) : make_uint2(Pvw, Puw);
+                inc[s_uw] = u < x ? make_uint2(Puv, Pwv) : make_uint2(Pwv, Puv);
+                inc[s_vw] = v < x ? make_uint2(Pvu, Pwu) : make_uint2(Pwu, Pvu);
+            }
+        }
+    }
+}
+
+// the record slots of each oriented edge: min(|out(u)|, |out(v)|)
+__global__ void k_rec_bound(int64_t m, const int64_t* __restrict__ out_ptr, const int32_t* __restrict__ out_src,
+                            const int32_t* __restrict__ out_col, int64_t* __restrict__ rec_ptr) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = out_src[k], v = out_col[k];
+        const int64_t a = out_ptr[u + 1] - out_ptr[u], b = out_ptr[v + 1] - out_ptr[v];
+        rec_ptr[k] = a < b ? a : b;
     }
 }
 
@@ -1483,15 +1571,38 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
     nd_oriented o(st);
     ND_TRY(orient_graph(h, &o, st));
     const int eblocks = nd_blocks_for(m * 32, kThreads, grid_cap(h) * 4);
+    // the stored adjacency layout keeps the count pass's triangles as records
+    // (4 B each, min(|out(u)|, |out(v)|) slots reserved per oriented edge), so
+    // that the fill does not search again; without the memory for them the
+    // fill searches as the count pass does
+    nd_tmp<int64_t> rec_ptr(st);
+    nd_tmp<uint32_t> rec(st), rec_cnt(st);
+    bool use_rec = false;
+    if (h->adj && !h->otf && rec_ptr.alloc(m + 1) == ND_OK) {
+        k_rec_bound<<<nd_blocks_for(m, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(m, o.out_ptr, o.out_src,
+                                                                                     o.out_col, rec_ptr);
+        ND_CUDA(cudaGetLastError());
+        ND_CUDA(cudaMemsetAsync(rec_ptr.p + m, 0, sizeof(int64_t), st));
+        ND_TRY(nd_scan_i64(rec_ptr, m, st));
+        int64_t slots = 0;
+        ND_TRY(read_i64(rec_ptr.p + m, &slots, st));
+        use_rec = rec.alloc(slots) == ND_OK && rec_cnt.alloc(m) == ND_OK;
+        if (!use_rec) nd_set_error("");
+    }
     {
         // per-edge counts fit 32 bits (d_s < n); 32-bit atomics, widened for the scan
         nd_tmp<unsigned> cnt32(st);
         ND_TRY(cnt32.alloc(m));
         ND_CUDA(cudaMemsetAsync(cnt32, 0, sizeof(unsigned) * m, st));
         nd_prof_scope ps("tri_count", st, 2);
-        k_tri_oriented<false, false, unsigned><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid,
-                                                                             o.out_src, nullptr, nullptr, cnt32.p,
-                                                                             nullptr);
+        if (use_rec)
+            k_tri_oriented<false, false, unsigned, true><<<eblocks, kThreads, 0, st>>>(
+                m, o.out_ptr, o.out_col, o.out_eid, o.out_src, nullptr, nullptr, cnt32.p, nullptr, rec_ptr, rec,
+                rec_cnt);
+        else
+            k_tri_oriented<false, false, unsigned><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid,
+                                                                                 o.out_src, nullptr, nullptr, cnt32.p,
+                                                                                 nullptr);
         ND_CUDA(cudaGetLastError());
         k_widen_u32<<<nd_blocks_for(m, kThreads, grid_cap(h) * 4), kThreads, 0, st>>>(m, cnt32, h->inc_ptr);
         ND_CUDA(cudaGetLastError());
@@ -1519,7 +1630,15 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
             ND_CUDA(cudaMemcpyAsync(cursor, h->inc_ptr, sizeof(int64_t) * m, cudaMemcpyDeviceToDevice, st));
         }
         nd_prof_scope ps("tri_fill", st);
-        if (narrow)
+        if (use_rec && narrow)
+            k_tri_fill_rec<unsigned><<<eblocks, kThreads, 0, st>>>(m, o.out_ptr, o.out_col, o.out_eid, o.out_src,
+                                                                   o.out_pos, o.out_mir, cursor32.p, (uint2*)h->inc,
+                                                                   rec_ptr, rec, rec_cnt);
+        else if (use_rec)
+            k_tri_fill_rec<unsigned long long><<<eblocks, kThreads, 0, st>>>(
+                m, o.out_ptr, o.out_col, o.out_eid, o.out_src, o.out_pos, o.out_mir, cursor.p, (uint2*)h->inc, rec_ptr,
+                rec, rec_cnt);
+        else if (narrow)
             k_tri_oriented<true, true, unsigned><<<eblocks, kThreads, 0, st>>>(
                 m, o.out_ptr, o.out_col, o.out_eid, o.out_src, o.out_pos, o.out_mir, cursor32.p, (uint2*)h->inc);
         else if (h->adj)
@@ -1531,6 +1650,10 @@ nd_status nd_build_tri_incidence(nd_incidence* h, cudaStream_t st) {
                                                                       (uint2*)h->inc);
         ND_CUDA(cudaGetLastError());
     }
+    // the records are no longer needed: free them before the row ranking
+    // takes its second incidence buffer
+    nd_release(rec.p, st);
+    rec.p = nullptr;
     if (h->adj) {
         nd_release(h->mirror, st);  // build only
         h->mirror = nullptr;
