@@ -21,9 +21,10 @@ every host core, one full pass per step, the incidence built once before
 the timed steps.
 
 After the timed region the default run also measures, without touching the
-headline: the R-MAT scale-26 k-core (one step), 256 graphs of the batched
-workload (one disjoint-union batch, autotuned, against one graph per
-launch) and a short Poisson request stream (p50 / p99), under "extra".
+headline: SND, AND and AND-nn side by side on the workloads of configs 1-3,
+the R-MAT scale-26 k-core (one step), 256 graphs of the batched workload (one
+disjoint-union batch, autotuned, against one graph per launch) and a short
+Poisson request stream (p50 / p99), under "extra".
 """
 from __future__ import annotations
 
@@ -62,12 +63,14 @@ def parse():
     p.add_argument("--workload", default="rmat_s20_ef16")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--mode", choices=["single", "batch", "serve", "otf", "quality", "noalloc"], default="single",
+    p.add_argument("--mode", choices=["single", "batch", "serve", "otf", "quality", "noalloc", "sweeps"],
+                   default="single",
                    help="single: one graph per step (default); batch: many graphs as one disjoint "
                         "union vs one graph per launch; serve: Poisson request stream, p50/p99; "
                         "otf: stored incidence vs no-storage passes; quality: Kendall-Tau and "
                         "accuracy of the early-stopped iterates against kappa; noalloc: the "
-                        "allocation-free k-core entry point against build + SND")
+                        "allocation-free k-core entry point against build + SND; sweeps: SND, AND "
+                        "and AND-nn to convergence on configs 1-3 (or --workload)")
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--requests", type=int, default=192)
     p.add_argument("--no-extras", action="store_true",
@@ -710,12 +713,14 @@ def core26_measure(steps: int = 1):
 
 
 def run_extras(args, dev):
-    """After the timed region: one scale-26 k-core step, a 256-graph batch
-    (autotuned) against one graph per launch, and a 64-request stream at half
-    of its saturated rate.  Each is reported, none changes the headline."""
+    """After the timed region: SND / AND / AND-nn on configs 1-3, one
+    scale-26 k-core step, a 256-graph batch (autotuned) against one graph per
+    launch, and a 64-request stream at half of its saturated rate.  Each is
+    reported, none changes the headline."""
     import torch
     extra = {}
-    for key, fn in (("rmat_core_s26_ef16", lambda: core26_measure(1)),
+    for key, fn in (("sweeps", lambda: sweeps_measure(reps=1)),
+                    ("rmat_core_s26_ef16", lambda: core26_measure(1)),
                     ("batch_256", lambda: batch_measure(256, steps=1, autotune=True)),
                     ("serve_64", lambda: serve_measure(serve_requests(64), loads=(0.5,)))):
         t0 = time.perf_counter()
@@ -726,6 +731,69 @@ def run_extras(args, dev):
         extra[key]["wall_s"] = time.perf_counter() - t0
         torch.cuda.synchronize(dev)
     return extra
+
+
+SWEEP_WORKLOADS = ("chunglu_n2000_g2.5_d10", "rmat_s20_ef16", "chunglu_n100000_g2.1_d20_planted200")
+
+
+def sweeps_measure(names=SWEEP_WORKLOADS, reps=3):
+    """SND, AND with notification and AND without it (the paper's AND-nn),
+    each from d_s to convergence on one built incidence: updating passes,
+    evaluations and device time (median of reps), and AND-nn / AND time, the
+    ratio the paper tabulates for its CPU runs."""
+    import torch
+    from paper_1704_00386_gb300 import graphs as G
+    from paper_1704_00386_gb300 import nd
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return res, e0.elapsed_time(e1)
+
+    out = {}
+    for name in names:
+        w = G.workload(name)
+        rp = torch.from_numpy(np.asarray(w["row_ptr"])).cuda()
+        col = torch.from_numpy(np.asarray(w["col"])).cuda()
+        inc = nd.build_incidence(rp, col, w["r"], w["s"])
+        rec = {"r": w["r"], "s": w["s"], "r_cliques": inc.num_r}
+        kappa = None
+        for mode in ("snd", "and", "and_nn"):
+            runs = []
+            for _ in range(reps):
+                if mode == "snd":
+                    (tau, it), ms = timed(inc.snd)
+                    ev = _evals_of(inc, 0)
+                else:
+                    (tau, it, ev), ms = timed(lambda: inc.and_(notify=(mode == "and")))
+                runs.append((ms, it, ev))
+                if kappa is None:
+                    kappa = tau.clone()
+                elif not torch.equal(tau, kappa):
+                    rec["error"] = f"{mode} differs from SND"
+            ms = statistics.median(r[0] for r in runs)
+            rec[mode] = {"passes": runs[-1][1], "evaluations": runs[-1][2], "ms": ms,
+                         "updates_per_s": runs[-1][2] / (ms / 1e3) if ms > 0 else None}
+        rec["and_nn_over_and_time"] = rec["and_nn"]["ms"] / rec["and"]["ms"] if rec["and"]["ms"] > 0 else None
+        inc.free()
+        out[name] = rec
+    return out
+
+
+def run_sweeps(args):
+    import torch
+    from paper_1704_00386_gb300 import nd
+    torch.cuda.set_device(0)
+    nd.load(build_if_missing=False)
+    names = SWEEP_WORKLOADS if args.workload == "rmat_s20_ef16" else (args.workload,)
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "mode": "sweeps", "workloads": sweeps_measure(names)}),
+          flush=True)
+    return 0
 
 
 def run_otf(args):
@@ -848,6 +916,8 @@ def run_noalloc(args):
 
 def main():
     args = parse()
+    if args.mode == "sweeps":
+        return run_sweeps(args)
     if args.mode == "noalloc":
         return run_noalloc(args)
     if args.mode == "otf":
