@@ -528,6 +528,9 @@ __global__ void k_orient(int64_t n, const int64_t* __restrict__ rp, const int32_
 // one warp per oriented edge u -> v: the triangles {u, v, w}, w in out(u) /\ out(v).
 // ADJ: the entries are CSR positions, each pair ordered by its edge's
 // canonical endpoints (the entry of the smaller endpoint first).
+#ifndef ND_TRI_COUNT_MIN_BLOCKS
+#define ND_TRI_COUNT_MIN_BLOCKS 8  // the count pass (with its records) at full occupancy
+#endif
 #ifndef ND_TRI_MIN_BLOCKS
 #define ND_TRI_MIN_BLOCKS 6  // resident blocks per SM for the triangle count / fill
 #endif
@@ -538,7 +541,7 @@ __global__ void k_orient(int64_t n, const int64_t* __restrict__ rp, const int32_
 // rec[rec_ptr[k] + i]; rec_ptr[k] reserves min(|out(u)|, |out(v)|) slots,
 // the most edge k can find.  rec_cnt[k] = triangles found.
 template <bool FILL, bool ADJ, typename C = unsigned long long, bool REC = false>
-__global__ void __launch_bounds__(kThreads, ND_TRI_MIN_BLOCKS) k_tri_oriented(int64_t m, const int64_t* __restrict__ out_ptr,
+__global__ void __launch_bounds__(kThreads, FILL ? ND_TRI_MIN_BLOCKS : ND_TRI_COUNT_MIN_BLOCKS) k_tri_oriented(int64_t m, const int64_t* __restrict__ out_ptr,
                                const int32_t* __restrict__ out_col, const uint32_t* __restrict__ out_eid,
                                const int32_t* __restrict__ out_src, const uint32_t* __restrict__ out_pos,
                                const uint32_t* __restrict__ out_mir, C* __restrict__ ctr,
