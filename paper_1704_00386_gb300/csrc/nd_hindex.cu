@@ -752,14 +752,18 @@ __device__ __forceinline__ void run_groups_active(const SweepParams& P, int64_t 
 #endif
 // GB: a batch handle's SND / AND-nn pass, which skips the rows of graphs
 // that have converged
-template <int Q, bool AND, bool NOTIFY, bool GB = false>
+// NC: no rho cache, for the late passes of a run, where few rows search:
+// without its 16 KB per block the SM keeps more of its memory as L1 for the
+// gathers
+template <int Q, bool AND, bool NOTIFY, bool GB = false, bool NC = false>
 __global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS : ND_PASS_MIN_BLOCKS)
     k_pass(SweepParams P) {
     if (P.prev != nullptr && *(volatile const unsigned long long*)P.prev == 0ull) return;  // converged
+    constexpr int kRC = NC ? 0 : kRhoCache;
     __shared__ unsigned bins[kThreads / 32][260];  // k-ary search bins, one set per warp
-    __shared__ uint16_t rho_cache[kThreads / 32][kRhoCache > 0 ? kRhoCache : 1];  // per warp; a CTA row uses all
-    uint16_t* const wcache = kRhoCache > 0 ? rho_cache[threadIdx.x >> 5] : nullptr;
-    uint16_t* const bcache = kRhoCache > 0 ? &rho_cache[0][0] : nullptr;
+    __shared__ uint16_t rho_cache[kThreads / 32][kRC > 0 ? kRC : 1];  // per warp; a CTA row uses all
+    uint16_t* const wcache = kRC > 0 ? rho_cache[threadIdx.x >> 5] : nullptr;
+    uint16_t* const bcache = kRC > 0 ? &rho_cache[0][0] : nullptr;
     __shared__ int bounds[2];
     __shared__ unsigned long long s_chunk;
     unsigned long long changed = 0, evals = 0, incs = 0;
@@ -1079,9 +1083,20 @@ __global__ void __launch_bounds__(kThreads, ND_PASS_MIN_BLOCKS) k_pass_otf(Sweep
 
 typedef void (*pass_fn)(SweepParams);
 
-pass_fn pick(const nd_incidence* h, int mode) {
+#ifndef ND_LATE_NOCACHE
+#define ND_LATE_NOCACHE 1  // passes after the first batch without the rho cache: 0 none, 1 SND, 2 SND and AND
+#endif
+pass_fn pick(const nd_incidence* h, int mode, bool late = false) {
     // mode: ND_SND, ND_AND (notify), ND_AND_NN
     const int q = h->q;
+    if (late && !h->otf && !h->gid) {
+        if (mode == ND_SND && ND_LATE_NOCACHE >= 1)
+            return q == 1 ? k_pass<1, false, false, false, true>
+                          : (q == 2 ? k_pass<2, false, false, false, true> : k_pass<3, false, false, false, true>);
+        if (mode == ND_AND && ND_LATE_NOCACHE >= 2)
+            return q == 1 ? k_pass<1, true, true, false, true>
+                          : (q == 2 ? k_pass<2, true, true, false, true> : k_pass<3, true, true, false, true>);
+    }
     if (h->otf) return mode == ND_SND ? k_pass_otf<false, false> : (mode == ND_AND ? k_pass_otf<true, true> : k_pass_otf<true, false>);
     if (h->gid && mode != ND_AND) {  // a batch: converged graphs are skipped
         if (q == 1) return mode == ND_SND ? k_pass<1, false, false, true> : k_pass<1, true, false, true>;
@@ -1375,9 +1390,12 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
         P.gid = h->gid;
     }
     plan_buckets(h, P);
-    pass_fn fn = pick(h, mode);
+    // the first batch of passes, where rows still search, keeps the rho
+    // cache; later batches may run a kernel without it
+    pass_fn fn0 = pick(h, mode), fn1 = pick(h, mode, true);
     const int64_t units = pass_units(h, P);
-    const int grid = units > 0 ? pass_grid(h, (const void*)fn, units) : 0;
+    const int grid0 = units > 0 ? pass_grid(h, (const void*)fn0, units) : 0;
+    const int grid1 = units > 0 ? pass_grid(h, (const void*)fn1, units) : 0;
     const int kBatch = ND_BATCH;
     // Thm. 3 / Lemma 2: SND settles within the number of degree levels, at
     // most N_R, and AND never needs more passes than SND.  A run longer than
@@ -1403,6 +1421,8 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
         if (nb > max_passes - pass) nb = max_passes - pass;
         if (stop_active > 0.0) nb = 1;  // the stopping rule looks at every pass
         const int kind = batch == 0 ? 0 : ((batch & 1) ? 2 : 1);
+        const pass_fn fn = batch == 0 ? fn0 : fn1;
+        const int grid = batch == 0 ? grid0 : grid1;
         bool launched = false;
         // graphs hold the plain parameters; runs with members or a stopping rule launch directly
         if (nb == kBatch && grid > 0 && !members && (start & 1) == 0 && !h->pass_graph_failed[mode][kind]) {
