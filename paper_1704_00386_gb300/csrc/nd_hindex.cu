@@ -747,6 +747,9 @@ __device__ __forceinline__ void run_groups_active(const SweepParams& P, int64_t 
 #ifndef ND_PASS_MIN_BLOCKS
 #define ND_PASS_MIN_BLOCKS 6  // resident blocks per SM the register budget targets (6 measured best)
 #endif
+#ifndef ND_NC_MIN_BLOCKS
+#define ND_NC_MIN_BLOCKS 6  // the late-pass kernel without the rho cache
+#endif
 #ifndef ND_AND_MIN_BLOCKS
 #define ND_AND_MIN_BLOCKS 6   // the same for the AND pass with notification
 #endif
@@ -756,7 +759,8 @@ __device__ __forceinline__ void run_groups_active(const SweepParams& P, int64_t 
 // without its 16 KB per block the SM keeps more of its memory as L1 for the
 // gathers
 template <int Q, bool AND, bool NOTIFY, bool GB = false, bool NC = false>
-__global__ void __launch_bounds__(kThreads, (AND && NOTIFY) ? ND_AND_MIN_BLOCKS : ND_PASS_MIN_BLOCKS)
+__global__ void __launch_bounds__(kThreads, NC ? ND_NC_MIN_BLOCKS
+                                               : ((AND && NOTIFY) ? ND_AND_MIN_BLOCKS : ND_PASS_MIN_BLOCKS))
     k_pass(SweepParams P) {
     if (P.prev != nullptr && *(volatile const unsigned long long*)P.prev == 0ull) return;  // converged
     constexpr int kRC = NC ? 0 : kRhoCache;
@@ -1083,6 +1087,10 @@ __global__ void __launch_bounds__(kThreads, ND_PASS_MIN_BLOCKS) k_pass_otf(Sweep
 
 typedef void (*pass_fn)(SweepParams);
 
+#ifndef ND_LATE_FROM
+#define ND_LATE_FROM 16  // the first pass (0-based) of a run that takes the late-pass kernel
+#endif
+static_assert(ND_LATE_FROM >= 0 && ND_LATE_FROM <= ND_BATCH, "the late kernel starts within the first batch");
 #ifndef ND_LATE_NOCACHE
 #define ND_LATE_NOCACHE 1  // passes after the first batch without the rho cache: 0 none, 1 SND, 2 SND and AND
 #endif
@@ -1195,8 +1203,8 @@ SweepParams pass_params(const nd_incidence* h, int mode, const SweepParams& P0, 
 // the counters to the pinned host mirror.  Built explicitly (not by stream
 // capture) so that it also serves the legacy default stream.  On any
 // failure the handle falls back to ordinary launches for this kind.
-void make_batch_graph(nd_incidence* h, int mode, int kind, const SweepParams& P0, int grid, pass_fn fn,
-                      int64_t words) {
+void make_batch_graph(nd_incidence* h, int mode, int kind, const SweepParams& P0, int grid0, pass_fn fn0,
+                      int grid1, pass_fn fn1, int late_from, int64_t words) {
     const int base = (kind == 2) ? ND_BATCH : 0;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ex = nullptr;
@@ -1241,8 +1249,10 @@ void make_batch_graph(nd_incidence* h, int mode, int kind, const SweepParams& P0
         if (!ok) break;
         cudaKernelNodeParams kp = {};
         void* args[] = {&P};
-        kp.func = (void*)fn;
-        kp.gridDim = dim3(grid);
+        // passes from late_from on (in the run) take the late-pass kernel
+        const bool late = (kind == 0 ? k : ND_BATCH + k) >= late_from;
+        kp.func = (void*)(late ? fn1 : fn0);
+        kp.gridDim = dim3(late ? grid1 : grid0);
         kp.blockDim = dim3(kThreads);
         kp.sharedMemBytes = 0;
         kp.kernelParams = args;
@@ -1421,13 +1431,11 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
         if (nb > max_passes - pass) nb = max_passes - pass;
         if (stop_active > 0.0) nb = 1;  // the stopping rule looks at every pass
         const int kind = batch == 0 ? 0 : ((batch & 1) ? 2 : 1);
-        const pass_fn fn = batch == 0 ? fn0 : fn1;
-        const int grid = batch == 0 ? grid0 : grid1;
         bool launched = false;
         // graphs hold the plain parameters; runs with members or a stopping rule launch directly
-        if (nb == kBatch && grid > 0 && !members && (start & 1) == 0 && !h->pass_graph_failed[mode][kind]) {
+        if (nb == kBatch && grid0 > 0 && !members && (start & 1) == 0 && !h->pass_graph_failed[mode][kind]) {
             if (!h->pass_graph[mode][kind])
-                make_batch_graph(h, mode, kind, P, grid, fn, words);
+                make_batch_graph(h, mode, kind, P, grid0, fn0, grid1, fn1, ND_LATE_FROM, words);
             if (h->pass_graph[mode][kind]) {
                 // the graph's first pass reads the last slot of the other half
                 const int want = (base ^ ND_BATCH) + ND_BATCH - 1;
@@ -1447,9 +1455,10 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
                 if (mode == ND_AND)
                     ND_CUDA(cudaMemsetAsync(Pk.next, 0, sizeof(uint32_t) * words, st));
                 if (Pk.gid) ND_CUDA(cudaMemsetAsync(Pk.gact_out, 0, (size_t)h->ngraphs, st));
-                if (grid > 0) {
+                if (grid0 > 0) {
+                    const bool late = pass >= ND_LATE_FROM;
                     nd_prof_scope ps(pname, st);
-                    fn<<<grid, kThreads, 0, st>>>(Pk);
+                    (late ? fn1 : fn0)<<<late ? grid1 : grid0, kThreads, 0, st>>>(Pk);
                     ND_CUDA(cudaGetLastError());
                 }
             }
