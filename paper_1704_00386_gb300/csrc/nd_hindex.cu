@@ -747,6 +747,9 @@ __device__ __forceinline__ void run_groups_active(const SweepParams& P, int64_t 
 #ifndef ND_PASS_MIN_BLOCKS
 #define ND_PASS_MIN_BLOCKS 6  // resident blocks per SM the register budget targets (6 measured best)
 #endif
+#ifndef ND_NC_CARVEOUT
+#define ND_NC_CARVEOUT 1  // the late-pass kernel asks for the carve-out it needs (0: the driver's choice)
+#endif
 #ifndef ND_NC_MIN_BLOCKS
 #define ND_NC_MIN_BLOCKS 6  // the late-pass kernel without the rho cache
 #endif
@@ -1403,6 +1406,23 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
     // the first batch of passes, where rows still search, keeps the rho
     // cache; later batches may run a kernel without it
     pass_fn fn0 = pick(h, mode), fn1 = pick(h, mode, true);
+    // the late-pass kernel needs little shared memory: ask for a carve-out
+    // that just holds its resident blocks (plus the 1 KB each block reserves),
+    // leaving the rest of the SM's memory as L1.  Left to itself the driver
+    // chose 132 KB, where 64 KB suffice.
+    if (fn1 != fn0 && ND_NC_CARVEOUT) {
+        cudaFuncAttributes fa;
+        int dev = 0, max_sm = 0;
+        ND_CUDA(cudaFuncGetAttributes(&fa, (const void*)fn1));
+        ND_CUDA(cudaGetDevice(&dev));
+        ND_CUDA(cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        if (max_sm > 0) {
+            const int64_t need = (int64_t)ND_NC_MIN_BLOCKS * ((int64_t)fa.sharedSizeBytes + 1024);
+            int pct = (int)((100 * need + max_sm - 1) / max_sm) + 1;
+            if (pct > 100) pct = 100;
+            ND_CUDA(cudaFuncSetAttribute((const void*)fn1, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+        }
+    }
     const int64_t units = pass_units(h, P);
     const int grid0 = units > 0 ? pass_grid(h, (const void*)fn0, units) : 0;
     const int grid1 = units > 0 ? pass_grid(h, (const void*)fn1, units) : 0;
