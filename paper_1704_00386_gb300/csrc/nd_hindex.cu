@@ -1095,7 +1095,7 @@ typedef void (*pass_fn)(SweepParams);
 #endif
 static_assert(ND_LATE_FROM >= 0 && ND_LATE_FROM <= ND_BATCH, "the late kernel starts within the first batch");
 #ifndef ND_LATE_NOCACHE
-#define ND_LATE_NOCACHE 1  // passes after the first batch without the rho cache: 0 none, 1 SND, 2 SND and AND
+#define ND_LATE_NOCACHE 2  // passes after the first batch without the rho cache: 0 none, 1 SND, 2 SND and AND
 #endif
 pass_fn pick(const nd_incidence* h, int mode, bool late = false) {
     // mode: ND_SND, ND_AND (notify), ND_AND_NN
