@@ -1093,7 +1093,11 @@ typedef void (*pass_fn)(SweepParams);
 #ifndef ND_LATE_FROM
 #define ND_LATE_FROM 16  // the first pass (0-based) of a run that takes the late-pass kernel
 #endif
+#ifndef ND_AND_LATE_FROM
+#define ND_AND_LATE_FROM 16  // the same for AND with notification
+#endif
 static_assert(ND_LATE_FROM >= 0 && ND_LATE_FROM <= ND_BATCH, "the late kernel starts within the first batch");
+static_assert(ND_AND_LATE_FROM >= 0 && ND_AND_LATE_FROM <= ND_BATCH, "the late kernel starts within the first batch");
 #ifndef ND_LATE_NOCACHE
 #define ND_LATE_NOCACHE 2  // passes after the first batch without the rho cache: 0 none, 1 SND, 2 SND and AND
 #endif
@@ -1406,6 +1410,7 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
     // the first batch of passes, where rows still search, keeps the rho
     // cache; later batches may run a kernel without it
     pass_fn fn0 = pick(h, mode), fn1 = pick(h, mode, true);
+    const int late_from = mode == ND_AND ? ND_AND_LATE_FROM : ND_LATE_FROM;
     // the late-pass kernel needs little shared memory: ask for a carve-out
     // that just holds its resident blocks (plus the 1 KB each block reserves),
     // leaving the rest of the SM's memory as L1.  Left to itself the driver
@@ -1455,7 +1460,7 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
         // graphs hold the plain parameters; runs with members or a stopping rule launch directly
         if (nb == kBatch && grid0 > 0 && !members && (start & 1) == 0 && !h->pass_graph_failed[mode][kind]) {
             if (!h->pass_graph[mode][kind])
-                make_batch_graph(h, mode, kind, P, grid0, fn0, grid1, fn1, ND_LATE_FROM, words);
+                make_batch_graph(h, mode, kind, P, grid0, fn0, grid1, fn1, late_from, words);
             if (h->pass_graph[mode][kind]) {
                 // the graph's first pass reads the last slot of the other half
                 const int want = (base ^ ND_BATCH) + ND_BATCH - 1;
@@ -1476,7 +1481,7 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
                     ND_CUDA(cudaMemsetAsync(Pk.next, 0, sizeof(uint32_t) * words, st));
                 if (Pk.gid) ND_CUDA(cudaMemsetAsync(Pk.gact_out, 0, (size_t)h->ngraphs, st));
                 if (grid0 > 0) {
-                    const bool late = pass >= ND_LATE_FROM;
+                    const bool late = pass >= late_from;
                     nd_prof_scope ps(pname, st);
                     (late ? fn1 : fn0)<<<late ? grid1 : grid0, kThreads, 0, st>>>(Pk);
                     ND_CUDA(cudaGetLastError());
