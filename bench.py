@@ -50,7 +50,7 @@ CPU_SND_SECONDS = 10.0    # time budget of the multi-threaded SND passes of the 
 # ncu DRAM bytes per incidence of the SND pass (k-truss, q = 2), measured on the
 # current kernels on R-MAT scale 18: pass 12, with the rho cache (dram__bytes_read.sum +
 # dram__bytes_write.sum = 2.197118 GB + 32.99328 MB per pass over 247,767,033
-# incidences, 9.00 B), and pass 20 of the late-pass kernel without it (2.195024 GB +
+# incidences, 9.00 B), and pass 21 of the late-pass kernel without it (2.195024 GB +
 # 26.116608 MB, 8.96 B); None once a kernel changes until it is measured again.
 NCU_SND_TRAFFIC_PER_INCIDENCE = (2.197118e9 + 32.99328e6) / 247767033
 
