@@ -1104,13 +1104,25 @@ static_assert(ND_AND_LATE_FROM >= 0 && ND_AND_LATE_FROM <= ND_BATCH, "the late k
 pass_fn pick(const nd_incidence* h, int mode, bool late = false) {
     // mode: ND_SND, ND_AND (notify), ND_AND_NN
     const int q = h->q;
-    if (late && !h->otf && !h->gid) {
-        if (mode == ND_SND && ND_LATE_NOCACHE >= 1)
+    if (late && !h->otf) {
+        const bool gb = h->gid && mode != ND_AND;  // a batch's SND / AND-nn pass
+        if (mode == ND_SND && ND_LATE_NOCACHE >= 1) {
+            if (gb)
+                return q == 1 ? k_pass<1, false, false, true, true>
+                              : (q == 2 ? k_pass<2, false, false, true, true> : k_pass<3, false, false, true, true>);
             return q == 1 ? k_pass<1, false, false, false, true>
                           : (q == 2 ? k_pass<2, false, false, false, true> : k_pass<3, false, false, false, true>);
+        }
         if (mode == ND_AND && ND_LATE_NOCACHE >= 2)
             return q == 1 ? k_pass<1, true, true, false, true>
                           : (q == 2 ? k_pass<2, true, true, false, true> : k_pass<3, true, true, false, true>);
+        if (mode == ND_AND_NN && ND_LATE_NOCACHE >= 2) {
+            if (gb)
+                return q == 1 ? k_pass<1, true, false, true, true>
+                              : (q == 2 ? k_pass<2, true, false, true, true> : k_pass<3, true, false, true, true>);
+            return q == 1 ? k_pass<1, true, false, false, true>
+                          : (q == 2 ? k_pass<2, true, false, false, true> : k_pass<3, true, false, false, true>);
+        }
     }
     if (h->otf) return mode == ND_SND ? k_pass_otf<false, false> : (mode == ND_AND ? k_pass_otf<true, true> : k_pass_otf<true, false>);
     if (h->gid && mode != ND_AND) {  // a batch: converged graphs are skipped
@@ -1410,7 +1422,7 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
     // the first batch of passes, where rows still search, keeps the rho
     // cache; later batches may run a kernel without it
     pass_fn fn0 = pick(h, mode), fn1 = pick(h, mode, true);
-    const int late_from = mode == ND_AND ? ND_AND_LATE_FROM : ND_LATE_FROM;
+    const int late_from = mode == ND_SND ? ND_LATE_FROM : ND_AND_LATE_FROM;
     // the late-pass kernel needs little shared memory: ask for a carve-out
     // that just holds its resident blocks (plus the 1 KB each block reserves),
     // leaving the rest of the SM's memory as L1.  Left to itself the driver
