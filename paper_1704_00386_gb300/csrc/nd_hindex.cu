@@ -237,12 +237,21 @@ __device__ __forceinline__ int32_t group_hindex(const cg::thread_block_tile<G>& 
 // #{rho >= lo + b*width} is the suffix sum from b; the answer H lies in
 // [k, next edge) for the largest bin edge k whose suffix is >= k (bin 0
 // always qualifies, because #{rho >= lo} >= lo).  Each lane owns 8 bins.
+// P16: the counters are 16 bits, two to a word (bin b in word b/2), for
+// rows of fewer than 65,536 entries; 129 words instead of 257.
+template <bool P16>
+__device__ __forceinline__ unsigned bin_count(const unsigned* bins, int b) {
+    if constexpr (P16) return (bins[b >> 1] >> ((b & 1) << 4)) & 0xffffu;
+    return bins[b];
+}
+
+template <bool P16>
 __device__ __forceinline__ void select_bin(const unsigned* bins, int lo, int hi, int width, int nb,
                                            int* nlo, int* nhi) {
     const int lane = threadIdx.x & 31;
     unsigned own = 0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) own += bins[8 * lane + k];
+    for (int k = 0; k < 8; ++k) own += bin_count<P16>(bins, 8 * lane + k);
     unsigned incl = own;  // inclusive prefix over lanes
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -250,12 +259,12 @@ __device__ __forceinline__ void select_bin(const unsigned* bins, int lo, int hi,
         if (lane >= o) incl += v;
     }
     const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
-    int64_t run = (int64_t)bins[256] + (total - incl);  // rho at or above this lane's bins
+    int64_t run = (int64_t)bin_count<P16>(bins, 256) + (total - incl);  // rho at or above this lane's bins
     int best = -1;
 #pragma unroll
     for (int k = 7; k >= 0; --k) {
         const int b = 8 * lane + k;
-        run += bins[b];
+        run += bin_count<P16>(bins, b);
         if (best < 0 && run >= (int64_t)lo + (int64_t)b * width) best = b;
     }
     const unsigned hit = __ballot_sync(0xffffffffu, best >= 0);
@@ -265,9 +274,17 @@ __device__ __forceinline__ void select_bin(const unsigned* bins, int lo, int hi,
     *nhi = e < hi ? e : hi;
 }
 
+template <bool P16>
 __device__ __forceinline__ void kary_bin(unsigned* bins, int32_t r, int lo, int hi, int width) {
-    if (r >= lo) atomicAdd(&bins[r >= hi ? 256 : (r - lo) / width], 1u);
+    if (r < lo) return;
+    const int b = r >= hi ? 256 : (r - lo) / width;
+    if constexpr (P16) atomicAdd(&bins[b >> 1], 1u << ((b & 1) << 4));
+    else atomicAdd(&bins[b], 1u);
 }
+
+// words of one set of bins: 257 counters, packed or not
+template <bool P16>
+__device__ __forceinline__ int bin_words() { return P16 ? 129 : 257; }
 
 // H({rho_j}) clipped to t by one warp, streaming the row: one pass counts
 // rho >= t; if that fails, k-ary search with 256 shared-memory bins per
@@ -276,7 +293,8 @@ __device__ __forceinline__ void kary_bin(unsigned* bins, int32_t r, int lo, int 
 // row has t <= d_s < 65536), so the search passes read them from shared
 // memory instead of gathering them again; only entries past ncache are
 // streamed again.
-template <typename F>
+// P16: packed 16-bit bins, for rows of fewer than 65,536 entries
+template <bool P16 = false, typename F>
 __device__ __forceinline__ int32_t warp_hindex(const F& rho, int64_t jb, int64_t je, int32_t t, unsigned* bins,
                                                uint16_t* cache = nullptr, int ncache = 0) {
     const int lane = threadIdx.x & 31;
@@ -299,13 +317,14 @@ __device__ __forceinline__ int32_t warp_hindex(const F& rho, int64_t jb, int64_t
         const int span = hi - lo;
         const int nb = span < 256 ? span : 256;
         const int width = (span + nb - 1) / nb;
-        for (int i = lane; i <= 256; i += 32) bins[i] = 0;
+        for (int i = lane; i < bin_words<P16>(); i += 32) bins[i] = 0;
         __syncwarp();
-        for (int64_t j = jb + lane; j < jc && j < je; j += 32) kary_bin(bins, (int32_t)cache[j - jb], lo, hi, width);
-        for (int64_t j = jc + lane; j < je; j += 32) kary_bin(bins, rho(j), lo, hi, width);
+        for (int64_t j = jb + lane; j < jc && j < je; j += 32)
+            kary_bin<P16>(bins, (int32_t)cache[j - jb], lo, hi, width);
+        for (int64_t j = jc + lane; j < je; j += 32) kary_bin<P16>(bins, rho(j), lo, hi, width);
         __syncwarp();
         int nlo, nhi;
-        select_bin(bins, lo, hi, width, nb, &nlo, &nhi);
+        select_bin<P16>(bins, lo, hi, width, nb, &nlo, &nhi);
         lo = nlo;
         hi = nhi;
         __syncwarp();
@@ -350,13 +369,13 @@ __device__ __forceinline__ int32_t cta_hindex(const F& rho, int64_t jb, int64_t 
         for (int i = threadIdx.x; i <= 256; i += kThreads) bins[i] = 0;
         __syncthreads();
         for (int64_t j = jb + threadIdx.x; j < jc && j < je; j += kThreads)
-            kary_bin(bins, (int32_t)cache[j - jb], lo, hi, width);
+            kary_bin<false>(bins, (int32_t)cache[j - jb], lo, hi, width);
         for (int64_t j = jc + threadIdx.x; j < je; j += kThreads)
-            kary_bin(bins, rho(j), lo, hi, width);
+            kary_bin<false>(bins, rho(j), lo, hi, width);
         __syncthreads();
         if (threadIdx.x < 32) {
             int nlo, nhi;
-            select_bin(bins, lo, hi, width, nb, &nlo, &nhi);
+            select_bin<false>(bins, lo, hi, width, nb, &nlo, &nhi);
             if (threadIdx.x == 0) { bounds[0] = nlo; bounds[1] = nhi; }
         }
         __syncthreads();
@@ -570,7 +589,7 @@ __device__ __forceinline__ void run_groups(const SweepParams& P, int64_t first, 
 
 // one r-clique per warp (rows of the warp bucket), streamed.  CHECK: test
 // the frontier here (false when the caller has already selected active rows)
-template <int Q, bool AND, bool NOTIFY, bool CHECK = true, bool GB = false>
+template <int Q, bool AND, bool NOTIFY, bool CHECK = true, bool GB = false, bool PK = true>
 __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item& it, unsigned* bins,
                                              uint16_t* cache, unsigned long long& changed, unsigned long long& evals,
                                              unsigned long long& incs) {
@@ -583,7 +602,8 @@ __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item
     // valid tau, which is <= d_s); changes are detected against the stored value
     const int32_t t = min(t0, (int32_t)it.d);
     const int64_t jb = it.jb, je = it.jb + it.d;
-    const int32_t h = warp_hindex(make_rho<Q, !AND>(P), jb, je, t, bins, cache, kRhoCache);
+    // a warp row has d_s <= the warp threshold (at most 8,192), so 16-bit bins hold its counts
+    const int32_t h = warp_hindex<PK>(make_rho<Q, !AND>(P), jb, je, t, bins, cache, kRhoCache);
     if (lane == 0) {
         evals++;
         incs += it.d;
@@ -599,7 +619,8 @@ __device__ __forceinline__ void run_warp_row(const SweepParams& P, const nd_item
 // one r-clique per CTA (rows longer than 2048 incidences)
 template <int Q, bool AND, bool NOTIFY, bool GB = false>
 __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int64_t last,
-                                        unsigned* bins, int* bounds, uint16_t* cache, unsigned long long& changed,
+                                        unsigned* bins, int* bounds, uint16_t* cache, int ncache,
+                                        unsigned long long& changed,
                                         unsigned long long& evals, unsigned long long& incs) {
     for (int64_t i = first; i < last; ++i) {
         const nd_item it = load_item(P.items, i);
@@ -617,7 +638,7 @@ __device__ __forceinline__ void run_cta(const SweepParams& P, int64_t first, int
         else if (Q == 1 && t > kTau16Max)
             h = cta_hindex(Rho<Q, !AND, int32_t>{P.inc, P.tin}, jb, je, t, bins, bounds);
         else
-            h = cta_hindex(make_rho<Q, !AND>(P), jb, je, t, bins, bounds, cache, (kThreads / 32) * kRhoCache);
+            h = cta_hindex(make_rho<Q, !AND>(P), jb, je, t, bins, bounds, cache, ncache);
         if (threadIdx.x == 0) {
             evals++;
             incs += it.d;
@@ -747,6 +768,12 @@ __device__ __forceinline__ void run_groups_active(const SweepParams& P, int64_t 
 #ifndef ND_PASS_MIN_BLOCKS
 #define ND_PASS_MIN_BLOCKS 6  // resident blocks per SM the register budget targets (6 measured best)
 #endif
+#ifndef ND_PACKED_BINS_Q2
+#define ND_PACKED_BINS_Q2 0  // (2,3) passes with the packed bins too (measured slower on the R-MAT k-truss)
+#endif
+#ifndef ND_CARVEOUT_FN0
+#define ND_CARVEOUT_FN0 1  // request the carve-out for the first batch's kernel too
+#endif
 #ifndef ND_NC_CARVEOUT
 #define ND_NC_CARVEOUT 1  // the late-pass kernel asks for the carve-out it needs (0: the driver's choice)
 #endif
@@ -767,10 +794,27 @@ __global__ void __launch_bounds__(kThreads, NC ? ND_NC_MIN_BLOCKS
     k_pass(SweepParams P) {
     if (P.prev != nullptr && *(volatile const unsigned long long*)P.prev == 0ull) return;  // converged
     constexpr int kRC = NC ? 0 : kRhoCache;
-    __shared__ unsigned bins[kThreads / 32][260];  // k-ary search bins, one set per warp
-    __shared__ uint16_t rho_cache[kThreads / 32][kRC > 0 ? kRC : 1];  // per warp; a CTA row uses all
+    // k-ary search bins.  (1,2) and (3,4): one packed set per warp (16-bit
+    // counters), and a 32-bit set for the CTA rows in the last 1,040 bytes of
+    // the block's rho cache, which a CTA row then does not use for values;
+    // that keeps six blocks within a 132 KB shared-memory carve-out, and the
+    // rest of the SM's memory serves as L1 (R-MAT scale-26 k-core: 794 against
+    // 825 ms per step; config-3 (3,4): 121.9 against 126.8 ms).  (2,3): one
+    // 32-bit set per warp, the CTA rows using warp 0's (the packed layout
+    // measured 262.8 against 258.9 ms per step on the R-MAT scale-20 k-truss).
+    // PK: packed warp bins and the CTA bins in the cache (ND_PACKED_BINS_Q2
+    // selects it for (2,3))
+    constexpr bool PK = Q != 2 || ND_PACKED_BINS_Q2;
+    constexpr int kCtaBinWords = 260;
+    constexpr int kCtaCache = kRC > 0 ? (kThreads / 32) * kRC - (PK ? 2 * kCtaBinWords : 0) : 0;
+    static_assert(kRC == 0 || kCtaCache > 0, "the rho cache holds the CTA bins");
+    __shared__ unsigned bins[kThreads / 32][PK ? 132 : 260];
+    __shared__ __align__(16) uint16_t rho_cache[kThreads / 32][kRC > 0 ? kRC : 1];  // per warp; a CTA row uses all
+    __shared__ unsigned cta_bins_own[(kRC > 0 && PK) ? 1 : kCtaBinWords];
     uint16_t* const wcache = kRC > 0 ? rho_cache[threadIdx.x >> 5] : nullptr;
     uint16_t* const bcache = kRC > 0 ? &rho_cache[0][0] : nullptr;
+    unsigned* const cta_bins =
+        (kRC > 0 && PK) ? reinterpret_cast<unsigned*>(&rho_cache[0][0] + kCtaCache) : (PK ? cta_bins_own : bins[0]);
     __shared__ int bounds[2];
     __shared__ unsigned long long s_chunk;
     unsigned long long changed = 0, evals = 0, incs = 0;
@@ -785,8 +829,8 @@ __global__ void __launch_bounds__(kThreads, NC ? ND_NC_MIN_BLOCKS
             const int64_t c = (int64_t)s_chunk;
             __syncthreads();
             if (c >= n3) break;
-            run_cta<Q, AND, NOTIFY, GB>(P, P.lo[3] + c, P.lo[3] + c + 1, bins[0], bounds, bcache, changed, evals,
-                                        incs);
+            run_cta<Q, AND, NOTIFY, GB>(P, P.lo[3] + c, P.lo[3] + c + 1, cta_bins, bounds, bcache, kCtaCache,
+                                        changed, evals, incs);
         }
     };
     // AND updates in place, so a row evaluated later in a pass already sees
@@ -835,7 +879,8 @@ __global__ void __launch_bounds__(kThreads, NC ? ND_NC_MIN_BLOCKS
                     const int b = __ffs(mm) - 1;
                     mm &= mm - 1;
                     const nd_item it = load_item(P.items, P.lo[2] + t + b);
-                    run_warp_row<Q, AND, NOTIFY, false>(P, it, bins[threadIdx.x >> 5], wcache, changed, evals, incs);
+                    run_warp_row<Q, AND, NOTIFY, false, false, PK>(P, it, bins[threadIdx.x >> 5], wcache, changed,
+                                                                   evals, incs);
                 }
             }
             const int64_t t1_lo = max(t, n2), t1_hi = min(te, n2 + t1);
@@ -867,7 +912,8 @@ __global__ void __launch_bounds__(kThreads, NC ? ND_NC_MIN_BLOCKS
             while (t < e2) {
                 nd_item nx;
                 if (t + 1 < e2) nx = load_item(P.items, P.lo[2] + t + 1);
-                run_warp_row<Q, AND, NOTIFY, true, GB>(P, it, bins[threadIdx.x >> 5], wcache, changed, evals, incs);
+                run_warp_row<Q, AND, NOTIFY, true, GB, PK>(P, it, bins[threadIdx.x >> 5], wcache, changed, evals,
+                                                           incs);
                 it = nx;
                 ++t;
             }
@@ -1187,6 +1233,24 @@ nd_status ensure_state(nd_incidence* h, bool and_mode, cudaStream_t st) {
 }
 
 
+// the smallest shared-memory carve-out (percent of the SM's maximum) that
+// holds the resident blocks of a pass kernel (all are built for 6 per SM)
+nd_status request_carveout(const void* fn) {
+    static_assert(ND_PASS_MIN_BLOCKS == 6 && ND_AND_MIN_BLOCKS == 6 && ND_NC_MIN_BLOCKS == 6,
+                  "the carve-out is sized for six blocks per SM");
+    cudaFuncAttributes fa;
+    int dev = 0, max_sm = 0;
+    ND_CUDA(cudaFuncGetAttributes(&fa, fn));
+    ND_CUDA(cudaGetDevice(&dev));
+    ND_CUDA(cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    if (max_sm <= 0) return ND_OK;
+    const int64_t need = 6 * ((int64_t)fa.sharedSizeBytes + 1024);
+    int pct = (int)((100 * need + max_sm - 1) / max_sm);  // rounded up to a supported carve-out
+    if (pct > 100) pct = 100;
+    ND_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+    return ND_OK;
+}
+
 // parameters of one pass: its counter slot, the slot of the pass before it
 // (-1: none), and the parity of its index in the run (SND reads tau[parity]
 // and writes the other buffer; AND reads the frontier front[parity])
@@ -1423,22 +1487,13 @@ nd_status nd_run(nd_incidence* h, int mode, int32_t max_passes, const int32_t* t
     // cache; later batches may run a kernel without it
     pass_fn fn0 = pick(h, mode), fn1 = pick(h, mode, true);
     const int late_from = mode == ND_SND ? ND_LATE_FROM : ND_AND_LATE_FROM;
-    // the late-pass kernel needs little shared memory: ask for a carve-out
-    // that just holds its resident blocks (plus the 1 KB each block reserves),
-    // leaving the rest of the SM's memory as L1.  Left to itself the driver
-    // chose 132 KB, where 64 KB suffice.
-    if (fn1 != fn0 && ND_NC_CARVEOUT) {
-        cudaFuncAttributes fa;
-        int dev = 0, max_sm = 0;
-        ND_CUDA(cudaFuncGetAttributes(&fa, (const void*)fn1));
-        ND_CUDA(cudaGetDevice(&dev));
-        ND_CUDA(cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-        if (max_sm > 0) {
-            const int64_t need = (int64_t)ND_NC_MIN_BLOCKS * ((int64_t)fa.sharedSizeBytes + 1024);
-            int pct = (int)((100 * need + max_sm - 1) / max_sm) + 1;
-            if (pct > 100) pct = 100;
-            ND_CUDA(cudaFuncSetAttribute((const void*)fn1, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
-        }
+    // ask for a shared-memory carve-out that just holds each kernel's six
+    // resident blocks (plus the 1 KB each block reserves), leaving the rest
+    // of the SM's memory as L1 for the gathers.  Left to itself the driver
+    // chose 132 KB for the late-pass kernel, where 64 KB suffice.
+    if (ND_NC_CARVEOUT && !h->otf) {
+        if (ND_CARVEOUT_FN0) ND_TRY(request_carveout((const void*)fn0));
+        if (fn1 != fn0) ND_TRY(request_carveout((const void*)fn1));
     }
     const int64_t units = pass_units(h, P);
     const int grid0 = units > 0 ? pass_grid(h, (const void*)fn0, units) : 0;
