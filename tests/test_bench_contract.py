@@ -55,3 +55,19 @@ def test_our_arm_line():
     assert 0 < d["value_launched"] <= d["value"]
     ref = _run(["--impl", "reference", "--workload", "rmat_s14_ef8", "--steps", "1", "--warmup", "0"], 600)
     assert ref["config"] == d["config"]   # both arms decompose the same graph
+
+
+@pytest.mark.gpu
+def test_sweeps_line():
+    """--mode sweeps: SND, AND and AND-nn reach the same kappa (the bench
+    flags any mismatch), and notification only ever saves evaluations."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    d = _run(["--mode", "sweeps", "--workload", "rmat_s14_ef8"], 900)
+    rec = d["workloads"]["rmat_s14_ef8"]
+    assert "error" not in rec, rec.get("error")
+    for mode in ("snd", "and", "and_nn"):
+        assert rec[mode]["passes"] >= 1 and rec[mode]["ms"] > 0 and rec[mode]["evaluations"] > 0
+    assert rec["and"]["evaluations"] <= rec["and_nn"]["evaluations"]
+    assert rec["and_nn_over_and_time"] > 0
