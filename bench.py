@@ -21,8 +21,9 @@ every host core, one full pass per step, the incidence built once before
 the timed steps.
 
 After the timed region the default run also measures, without touching the
-headline: SND, AND and AND-nn side by side on the workloads of configs 1-3,
-the R-MAT scale-26 k-core (one step), 256 graphs of the batched workload (one
+headline: SND, AND and AND-nn side by side on the three single-graph
+workloads (Chung-Lu 2,000-vertex k-core, R-MAT scale-20 k-truss, Chung-Lu
+100,000-vertex (3,4) with planted cliques), the R-MAT scale-26 k-core (one step), 256 graphs of the batched workload (one
 disjoint-union batch, autotuned, against one graph per launch) and a short
 Poisson request stream (p50 / p99), under "extra".
 """
@@ -71,7 +72,8 @@ def parse():
                         "otf: stored incidence vs no-storage passes; quality: Kendall-Tau and "
                         "accuracy of the early-stopped iterates against kappa; noalloc: the "
                         "allocation-free k-core entry point against build + SND; sweeps: SND, AND "
-                        "and AND-nn to convergence on configs 1-3 (or --workload)")
+                        "and AND-nn to convergence on the Chung-Lu 2K k-core, R-MAT s20 k-truss and "
+                        "Chung-Lu 100K (3,4) workloads (or --workload)")
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--requests", type=int, default=192)
     p.add_argument("--no-extras", action="store_true",
@@ -499,7 +501,7 @@ def _evals_of(inc, and_evals):
 
 
 def run_batch(args):
-    """Config-4 shape, the whole list (default 4,096 graphs): one
+    """The batched workload, the whole list (default 4,096 graphs): one
     disjoint-union batch against one graph per launch, same GPU."""
     import torch
     from paper_1704_00386_gb300 import nd
@@ -513,7 +515,7 @@ SERVE_BUDGET = 64 << 30
 
 
 def serve_requests(count: int, seed: int = 5):
-    """Config-5a shape: graphs with 1K-2M edges (log-uniform), family uniform
+    """The served workload: graphs with 1K-2M edges (log-uniform), family uniform
     over ER / Chung-Lu / R-MAT, job uniform over (1,2) / (2,3) / (3,4) ((3,4)
     only where the footprint bound fits an eighth of the budget, else (2,3))."""
     from paper_1704_00386_gb300 import graphs as G
@@ -582,7 +584,7 @@ def serve_measure(reqs, loads=(0.5, 0.7, 0.9)):
 
 
 def run_serve(args):
-    """Config-5a shape: a Poisson stream of graphs with 1K-2M edges, mixed
+    """The served workload: a Poisson stream of graphs with 1K-2M edges, mixed
     jobs; saturated throughput, then p50/p99 latency at 0.5 / 0.7 / 0.9 of
     it; one-request-at-a-time service as the baseline."""
     import torch
@@ -594,7 +596,7 @@ def run_serve(args):
 
 
 def batch_measure(count: int, steps: int = 1, autotune: bool = False):
-    """Config-4 shape: `count` independent graphs (ER / Chung-Lu / R-MAT, n
+    """The batched workload: `count` independent graphs (ER / Chung-Lu / R-MAT, n
     in [100, 50000]), core and truss numbers for each: one disjoint-union
     batch against one graph per launch, same GPU, results compared.  With
     autotune, the batch handle's buckets are tuned (nd_autotune) first; the
@@ -673,7 +675,7 @@ def batch_measure(count: int, steps: int = 1, autotune: bool = False):
 
 
 def core26_measure(steps: int = 1):
-    """Config-5b: the k-core of R-MAT scale 26, EF 16 (67M vertices, 2.1G CSR
+    """The k-core of R-MAT scale 26, EF 16 (67M vertices, 2.1G CSR
     entries), generated on the device: build + SND + AND per step."""
     import torch
     from paper_1704_00386_gb300 import graphs as G
@@ -714,9 +716,10 @@ def core26_measure(steps: int = 1):
 
 
 def run_extras(args, dev):
-    """After the timed region: SND / AND / AND-nn on configs 1-3, one
-    scale-26 k-core step, a 256-graph batch (autotuned) against one graph per
-    launch, and a 64-request stream at half of its saturated rate.  Each is
+    """After the timed region: SND / AND / AND-nn on the three single-graph
+    workloads, one scale-26 k-core step, a 256-graph batch (autotuned)
+    against one graph per launch, and a 64-request stream at half of its
+    saturated rate.  Each is
     reported, none changes the headline."""
     import torch
     extra = {}

@@ -190,8 +190,8 @@ constexpr int32_t kTau16Max = 65535;
 
 // the gather of a row whose tau is at most 65535: the 16-bit copy for (1,2)
 // and (2,3).  (3,4) gathers int32 tau directly: its rows are not ordered, and
-// the 16-bit copy measured 3% slower there (config 3) against 6% faster for
-// a scale-24 k-core.
+// the 16-bit copy measured 3% slower there (Chung-Lu 100K (3,4) with planted
+// cliques) against 6% faster for a scale-24 k-core.
 template <int Q, bool RO>
 __device__ __forceinline__ auto make_rho(const SweepParams& P) {
     if constexpr (Q == 3) return Rho<3, RO, int32_t>{P.inc, P.tin};
@@ -799,7 +799,7 @@ __global__ void __launch_bounds__(kThreads, NC ? ND_NC_MIN_BLOCKS
     // the block's rho cache, which a CTA row then does not use for values;
     // that keeps six blocks within a 132 KB shared-memory carve-out, and the
     // rest of the SM's memory serves as L1 (R-MAT scale-26 k-core: 794 against
-    // 825 ms per step; config-3 (3,4): 121.9 against 126.8 ms).  (2,3): one
+    // 825 ms per step; Chung-Lu 100K (3,4): 121.9 against 126.8 ms).  (2,3): one
     // 32-bit set per warp, the CTA rows using warp 0's (the packed layout
     // measured 262.8 against 258.9 ms per step on the R-MAT scale-20 k-truss).
     // PK: packed warp bins and the CTA bins in the cache (ND_PACKED_BINS_Q2
