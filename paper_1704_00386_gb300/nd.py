@@ -24,11 +24,16 @@ ND_OK, ND_E_INVAL, ND_E_UNSUPPORTED_RS, ND_E_NOMEM, ND_E_CUDA, ND_E_NOT_CONVERGE
 ND_SND, ND_AND, ND_AND_NN = 0, 1, 2
 MODES = {"snd": ND_SND, "and": ND_AND, "and_nn": ND_AND_NN}
 
-SYMBOLS = ["nd_build_incidence", "nd_build_incidence_ex", "nd_build_incidence_batch", "nd_incidence_info", "nd_r_cliques", "nd_s_degree", "nd_snd",
-           "nd_and", "nd_iterate_k", "nd_truss_classic", "nd_prof_enable", "nd_prof_read",
-           "nd_last_passes", "nd_autotune", "nd_and_partial", "nd_and_until", "nd_count_equal", "nd_kendall_tau_b", "nd_incidence_bytes", "nd_free", "nd_strerror", "nd_last_error",
-           "nd_abi_version", "nd_core_snd_noalloc", "nd_normalize", "nd_set_wait_limit",
-           "nd_set_handle_memory_limit"]
+# every function include/nd.h declares (tests/test_abi.py checks the two lists agree)
+SYMBOLS = [
+    "nd_normalize", "nd_build_incidence", "nd_build_incidence_ex", "nd_build_incidence_batch",
+    "nd_incidence_info", "nd_incidence_bytes", "nd_r_cliques", "nd_s_degree",
+    "nd_snd", "nd_and", "nd_iterate_k", "nd_and_partial", "nd_and_until",
+    "nd_truss_classic", "nd_count_equal", "nd_kendall_tau_b",
+    "nd_prof_enable", "nd_prof_read", "nd_last_passes", "nd_autotune",
+    "nd_core_snd_noalloc", "nd_set_wait_limit", "nd_set_handle_memory_limit",
+    "nd_free", "nd_strerror", "nd_last_error", "nd_abi_version",
+]
 
 _lock = threading.Lock()
 _lib = None
