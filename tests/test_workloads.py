@@ -17,7 +17,7 @@ def _simple(rp, col):
     assert all((v, x) in full for x, v in fwd)  # symmetric (sampled)
 
 
-def test_config1_core_workload():
+def test_chunglu_2000_core_workload():
     w = G.workload("chunglu_n2000_g2.5_d10")
     assert (w["r"], w["s"]) == (1, 2)
     assert w["row_ptr"].size - 1 == 2000 and w["col"].size // 2 == 9753
@@ -26,7 +26,7 @@ def test_config1_core_workload():
     assert np.array_equal(w["col"], w2["col"]) and np.array_equal(w["row_ptr"], w2["row_ptr"])
 
 
-def test_config3_nucleus_workload():
+def test_chunglu_100000_planted_nucleus_workload():
     w = G.workload("chunglu_n100000_g2.1_d20_planted200")
     assert (w["r"], w["s"]) == (3, 4)
     assert w["row_ptr"].size - 1 == 100000 and w["col"].size // 2 == 1140801
