@@ -532,7 +532,7 @@ __global__ void k_orient(int64_t n, const int64_t* __restrict__ rp, const int32_
 #define ND_TRI_COUNT_MIN_BLOCKS 8  // the count pass (with its records) at full occupancy
 #endif
 #ifndef ND_TRI_MIN_BLOCKS
-#define ND_TRI_MIN_BLOCKS 6  // resident blocks per SM for the triangle count / fill
+#define ND_TRI_MIN_BLOCKS 6  // resident blocks per SM for the searching fill (used when the records do not fit)
 #endif
 // REC (count pass): also record every triangle found from edge k, as the
 // offsets of w in the shorter and in the longer out-list (16 bits each: an
